@@ -1,0 +1,214 @@
+"""PEANUT read-mapping oracle: TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline / reference arm may import
+this package.  The CUDA library and its Python binding never import it; they share no code.
+
+A ctypes wrapper over `peanut_oracle.c` (plain, slow, single-threaded C; see its header for the
+definitions, each tied to its section of Köster & Rahmann, "Massively parallel read mapping on GPUs
+with PEANUT") plus the closed-form index sizes of Section "The q-group index", paragraph "Size".
+
+Hit sets are returned as a numpy structured array with fields read (u4), strand (u1: 0 = read,
+1 = reverse complement of the read on the forward reference), end (i8: 0-based inclusive end in
+forward coordinates) and dist (i4: edit distance), sorted by (read, strand, end).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "peanut_oracle.c")
+_SO = os.path.join(_HERE, "_peanut_oracle.so")
+_lib = None
+
+HIT_DTYPE = np.dtype([("read", "<u4"), ("strand", "u1"), ("end", "<i8"), ("dist", "<i4")])
+MODES = {"all": 0, "best": 1, "ends": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into a shared object next to its source (atomic replace)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+        os.close(fd)
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        c = ctypes
+        vp = c.c_void_p
+        lib.oracle_semiglobal_column.restype = c.c_int
+        lib.oracle_semiglobal_column.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, c.c_int64, vp]
+        for f in (lib.oracle_map_bruteforce,):
+            f.restype = vp
+            f.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, vp, c.c_int64, vp, c.c_int]
+        lib.oracle_map_filter.restype = vp
+        lib.oracle_map_filter.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, vp, c.c_int64, vp,
+                                          c.c_int, c.c_int]
+        lib.oracle_hits_count.restype = c.c_int64
+        lib.oracle_hits_count.argtypes = [vp]
+        lib.oracle_hits_copy.argtypes = [vp, vp, vp, vp, vp]
+        lib.oracle_hits_free.argtypes = [vp]
+        lib.oracle_qgroup_build.restype = c.c_int64
+        lib.oracle_qgroup_build.argtypes = [vp, vp, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp]
+        lib.oracle_indexpair.argtypes = [vp, vp, vp, c.c_int, c.c_uint64, vp, vp]
+        lib.oracle_canonical_text.restype = c.c_int64
+        lib.oracle_canonical_text.argtypes = [c.c_char_p, vp, c.c_int64, c.c_int, vp, vp]
+        lib.oracle_frequent_qgrams.restype = c.c_int64
+        lib.oracle_frequent_qgrams.argtypes = [c.c_char_p, c.c_int64, c.c_int, c.c_int64, vp, vp,
+                                               c.c_int64]
+        _lib = lib
+    return _lib
+
+
+def _bytes(x) -> bytes:
+    if isinstance(x, (bytes, bytearray)):
+        return bytes(x)
+    return np.ascontiguousarray(x, dtype=np.uint8).tobytes()
+
+
+def _reads_args(seq, offsets):
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    return _bytes(seq), offs
+
+
+def _collect(h) -> np.ndarray:
+    lib = _load()
+    if not h:
+        raise ValueError("oracle rejected the input (non-ACGT base, bad q, or lemma threshold < 1)")
+    try:
+        n = lib.oracle_hits_count(h)
+        r = np.empty(n, np.uint32)
+        s = np.empty(n, np.uint8)
+        e = np.empty(n, np.int64)
+        d = np.empty(n, np.int32)
+        if n:
+            lib.oracle_hits_copy(h, r.ctypes.data, s.ctypes.data, e.ctypes.data, d.ctypes.data)
+    finally:
+        lib.oracle_hits_free(h)
+    out = np.empty(n, HIT_DTYPE)
+    out["read"], out["strand"], out["end"], out["dist"] = r, s, e, d
+    return out
+
+
+def semiglobal_column(pattern, ref) -> np.ndarray:
+    """D[j] = E[m][j] of Section "Validation" for every end position j of `ref`."""
+    P, R = _bytes(pattern), _bytes(ref)
+    D = np.empty(max(len(R), 1), np.int32)
+    if _load().oracle_semiglobal_column(P, len(P), R, len(R), D.ctypes.data) != 0:
+        raise ValueError("non-ACGT character")
+    return D[:len(R)]
+
+
+def _kvec(k, n):
+    k = np.asarray(k, dtype=np.int32)
+    if k.ndim == 0:
+        k = np.full(n, int(k), dtype=np.int32)
+    return np.ascontiguousarray(k)
+
+
+def map_bruteforce(ref, seq, offsets, k, mode: str = "all") -> np.ndarray:
+    """Hit set by the definition: full semiglobal DP of every read and strand over `ref`."""
+    R = _bytes(ref)
+    S, offs = _reads_args(seq, offsets)
+    n = offs.size - 1
+    kv = _kvec(k, n)
+    return _collect(_load().oracle_map_bruteforce(R, len(R), S, offs.ctypes.data, n, kv.ctypes.data,
+                                                  MODES[mode]))
+
+
+def map_filter(ref, seq, offsets, k, q: int, mode: str = "all") -> np.ndarray:
+    """Hit set by the q-gram filter + windowed DP (equal to map_bruteforce when every t >= 1)."""
+    R = _bytes(ref)
+    S, offs = _reads_args(seq, offsets)
+    n = offs.size - 1
+    kv = _kvec(k, n)
+    return _collect(_load().oracle_map_filter(R, len(R), S, offs.ctypes.data, n, kv.ctypes.data,
+                                              int(q), MODES[mode]))
+
+
+def qgroup_build(codes, payload, q: int, w: int = 32):
+    """Algorithm 1 over a text of q-gram codes.  Returns (I, S, Sp, O, distinct) with Sp cut to
+    distinct + 1 entries (the last one is the sentinel |T|)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint64)
+    payload = np.ascontiguousarray(payload, dtype=np.uint64)
+    T = codes.size
+    ng = ((1 << (2 * q)) + w - 1) // w
+    I = np.empty(ng, np.uint64)
+    S = np.empty(ng, np.uint64)
+    Sp = np.empty(T + 1, np.uint64)
+    O = np.empty(max(T, 1), np.uint64)
+    d = _load().oracle_qgroup_build(codes.ctypes.data, payload.ctypes.data, T, q, w, I.ctypes.data,
+                                    S.ctypes.data, Sp.ctypes.data, O.ctypes.data)
+    if d < 0:
+        raise ValueError("bad q or w")
+    return I, S, Sp[:d + 1].copy(), O[:T], int(d)
+
+
+def indexpair(I, S, Sp, w: int, g: int):
+    """INDEXPAIR(g) of Section "Filtration"; (0, 0) when g does not occur."""
+    a = ctypes.c_uint64()
+    b = ctypes.c_uint64()
+    Sp_full = np.ascontiguousarray(np.append(Sp, 0), dtype=np.uint64)
+    _load().oracle_indexpair(np.ascontiguousarray(I).ctypes.data, np.ascontiguousarray(S).ctypes.data,
+                             Sp_full.ctypes.data, w, int(g), ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)
+
+
+def canonical_text(seq, offsets, q: int):
+    """(codes, payload) of every read q-gram: canonical code min(g, revcomp g) and the label
+    (read << 9) | (g != canonical) << 8 | offset."""
+    S, offs = _reads_args(seq, offsets)
+    n = offs.size - 1
+    lens = np.diff(offs)
+    total = int(np.maximum(lens - q + 1, 0).sum())
+    codes = np.empty(max(total, 1), np.uint64)
+    payload = np.empty(max(total, 1), np.uint64)
+    got = _load().oracle_canonical_text(S, offs.ctypes.data, n, q, codes.ctypes.data, payload.ctypes.data)
+    if got < 0:
+        raise ValueError("bad input")
+    return codes[:got], payload[:got]
+
+
+def frequent_qgrams(ref, q: int, cap: int, max_out: int = 1 << 20):
+    """Canonical q-grams occurring more than `cap` times in `ref`: (codes, counts) by code."""
+    R = _bytes(ref)
+    codes = np.empty(max_out, np.uint64)
+    counts = np.empty(max_out, np.int64)
+    n = _load().oracle_frequent_qgrams(R, len(R), q, cap, codes.ctypes.data, counts.ctypes.data, max_out)
+    if n < 0:
+        raise ValueError("bad input")
+    if n > max_out:
+        return frequent_qgrams(ref, q, cap, max_out=int(n))
+    return codes[:n].copy(), counts[:n].copy()
+
+
+# ---- closed-form sizes, Section "The q-group index", paragraph "Size" (in words) ----
+
+def qgroup_index_words(q: int, T: int, w: int = 32) -> float:
+    """Upper bound on the q-group index size: 2/w * 4^q + min(4^q, |T|) + |T| words."""
+    return 2.0 / w * 4 ** q + min(4 ** q, T) + T
+
+
+def qgram_index_words(q: int, T: int) -> float:
+    """Size of a plain q-gram index (address table + position table): 4^q + |T| words."""
+    return float(4 ** q + T)
+
+
+def lemma_threshold(m: int, q: int, k: int) -> int:
+    """q-gram lemma: an alignment with at most k errors keeps at least m + 1 - q(k + 1) of the
+    read's q-grams intact (Section "The q-group index", paragraph on the choice of q)."""
+    return m + 1 - q * (k + 1)
+
+
+def sort_hits(h: np.ndarray) -> np.ndarray:
+    """Hits in (read, strand, end) order."""
+    return h[np.lexsort((h["end"], h["strand"], h["read"]))]

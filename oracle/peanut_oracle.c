@@ -1,0 +1,559 @@
+/* PEANUT read-mapping oracle: TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, __graft_entry__.smoke() and bench.py's CPU-baseline / reference arm may load,
+ * call or link this file.  The CUDA library never does, and this file includes nothing of it.
+ *
+ * A plain, slow, single-threaded CPU restatement of what the filter-and-verify hot path of
+ * Köster & Rahmann, "Massively parallel read mapping on GPUs with PEANUT", computes:
+ *
+ *   Section "Validation": E[i][j] is the smallest edit distance (unit costs) between the read
+ *   prefix of length i and any reference substring ending at j.  Boundary: E[0][j] = 0 (the
+ *   alignment may start anywhere), E[i][-1] = i.  Recurrence:
+ *       E[i][j] = min(E[i-1][j-1] + [P[i-1] != R[j]], E[i-1][j] + 1, E[i][j-1] + 1).
+ *   D[j] = E[m][j] for j in [0, n).
+ *
+ *   Hit set (the reading adopted for the paper's "duplicate removal" and strata, Section
+ *   "Postprocessing"): for read r, strand s (s = 1 aligns the reverse complement of the read to
+ *   the forward reference, in forward coordinates) and every maximal run of consecutive end
+ *   positions j with D[j] <= k, one tuple (r, s, j*, D[j*]) where j* is the leftmost position of
+ *   the run's minimum.  "all" mode keeps every tuple; "best-stratum" keeps, per read, the tuples
+ *   whose D equals the read's minimum over both strands.
+ *
+ * Two routes to the same set:
+ *   oracle_map_bruteforce: the definition above, the full DP over the whole reference;
+ *   oracle_map_filter:     the q-gram filter of Section "Filtration" (hash-map q-gram index of the
+ *                          reads and of their reverse complements; every reference q-gram looked
+ *                          up; hits counted per (read, strand, diagonal d = p - i)), the q-gram
+ *                          lemma threshold t = m + 1 - q(k + 1) of Section "The q-group index"
+ *                          applied to every window of k+1 consecutive diagonals, and the DP of
+ *                          Section "Validation" run only over the end range
+ *                          [d0 + m - 1 - 2k, d0 + m - 1 + 3k] of each window that passes.
+ *   oracle_qgroup_build:   Algorithm 1 (q-group index I, S, S', O) over a text of q-gram codes,
+ *                          with GROUPBIT / GROUPRANK / INDEXPAIR as defined in Section
+ *                          "The q-group index" and Section "Filtration".
+ *
+ * Readings where the paper is silent: 0-based inclusive end positions in forward coordinates;
+ * exclusive cumulative sums in Algorithm 1, S' with one sentinel entry holding |T|; only
+ * q-grams lying fully inside one read are indexed.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- encoding (Section "The q-group index": A=00, C=01, G=10, T=11) ---- */
+
+static int base_code(char c) {
+    switch (c) {
+        case 'A': return 0;
+        case 'C': return 1;
+        case 'G': return 2;
+        case 'T': return 3;
+        default: return -1;
+    }
+}
+
+static char complement(char c) {
+    switch (c) {
+        case 'A': return 'T';
+        case 'C': return 'G';
+        case 'G': return 'C';
+        default: return 'A';
+    }
+}
+
+static int check_acgt(const char* s, int64_t n) {
+    for (int64_t i = 0; i < n; i++)
+        if (base_code(s[i]) < 0) return -1;
+    return 0;
+}
+
+/* ---- semiglobal DP (Section "Validation") ---- */
+
+/* One DP column sweep over R[a..b] (inclusive) with boundary E[i][a-1] = i; D[j - a] = E[m][j]. */
+static void dp_columns(const char* P, int64_t m, const char* R, int64_t a, int64_t b, int32_t* col,
+                       int32_t* D) {
+    for (int64_t i = 0; i <= m; i++) col[i] = (int32_t)i;
+    for (int64_t j = a; j <= b; j++) {
+        int32_t diag = col[0]; /* E[0][j-1] */
+        col[0] = 0;            /* E[0][j] */
+        for (int64_t i = 1; i <= m; i++) {
+            int32_t up = col[i]; /* E[i][j-1] */
+            int32_t v = diag + (P[i - 1] != R[j] ? 1 : 0);
+            if (up + 1 < v) v = up + 1;
+            if (col[i - 1] + 1 < v) v = col[i - 1] + 1;
+            col[i] = v;
+            diag = up;
+        }
+        D[j - a] = col[m];
+    }
+}
+
+/* D[j] = E[m][j] for all j in [0, n).  Returns 0, or -1 on a non-ACGT character. */
+int oracle_semiglobal_column(const char* P, int64_t m, const char* R, int64_t n, int32_t* D) {
+    if (check_acgt(P, m) || check_acgt(R, n)) return -1;
+    if (n <= 0) return 0;
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    dp_columns(P, m, R, 0, n - 1, col, D);
+    free(col);
+    return 0;
+}
+
+/* ---- result list ---- */
+
+typedef struct {
+    int64_t n, cap;
+    uint32_t* read;
+    uint8_t* strand;
+    int64_t* end;
+    int32_t* dist;
+} oracle_hits;
+
+static void hits_push(oracle_hits* h, uint32_t r, uint8_t s, int64_t j, int32_t d) {
+    if (h->n == h->cap) {
+        h->cap = h->cap ? 2 * h->cap : 1024;
+        h->read = (uint32_t*)realloc(h->read, sizeof(uint32_t) * (size_t)h->cap);
+        h->strand = (uint8_t*)realloc(h->strand, (size_t)h->cap);
+        h->end = (int64_t*)realloc(h->end, sizeof(int64_t) * (size_t)h->cap);
+        h->dist = (int32_t*)realloc(h->dist, sizeof(int32_t) * (size_t)h->cap);
+    }
+    h->read[h->n] = r;
+    h->strand[h->n] = s;
+    h->end[h->n] = j;
+    h->dist[h->n] = d;
+    h->n++;
+}
+
+int64_t oracle_hits_count(const oracle_hits* h) { return h ? h->n : -1; }
+
+void oracle_hits_copy(const oracle_hits* h, uint32_t* read, uint8_t* strand, int64_t* end, int32_t* dist) {
+    memcpy(read, h->read, sizeof(uint32_t) * (size_t)h->n);
+    memcpy(strand, h->strand, (size_t)h->n);
+    memcpy(end, h->end, sizeof(int64_t) * (size_t)h->n);
+    memcpy(dist, h->dist, sizeof(int32_t) * (size_t)h->n);
+}
+
+void oracle_hits_free(oracle_hits* h) {
+    if (!h) return;
+    free(h->read);
+    free(h->strand);
+    free(h->end);
+    free(h->dist);
+    free(h);
+}
+
+/* mode: 0 = all (canonical tuple per maximal run), 1 = best stratum, 2 = every end with D <= k */
+enum { MODE_ALL = 0, MODE_BEST = 1, MODE_ENDS = 2 };
+
+/* Ends js[0..cnt) strictly increasing with values ds (all <= k): emit one tuple per maximal run
+ * of consecutive positions (leftmost minimum), or every end in MODE_ENDS. */
+static void emit_runs(oracle_hits* h, uint32_t r, uint8_t s, const int64_t* js, const int32_t* ds,
+                      int64_t cnt, int mode) {
+    int64_t x = 0;
+    while (x < cnt) {
+        if (mode == MODE_ENDS) {
+            hits_push(h, r, s, js[x], ds[x]);
+            x++;
+            continue;
+        }
+        int64_t y = x, best = x;
+        while (y + 1 < cnt && js[y + 1] == js[y] + 1) {
+            y++;
+            if (ds[y] < ds[best]) best = y;
+        }
+        hits_push(h, r, s, js[best], ds[best]);
+        x = y + 1;
+    }
+}
+
+/* Best stratum: keep, for every read, the tuples whose distance equals that read's minimum.
+ * Tuples of one read are contiguous in h (both strands). */
+static void best_stratum(oracle_hits* h) {
+    int64_t w = 0, x = 0;
+    while (x < h->n) {
+        int64_t y = x;
+        int32_t mn = h->dist[x];
+        while (y < h->n && h->read[y] == h->read[x]) {
+            if (h->dist[y] < mn) mn = h->dist[y];
+            y++;
+        }
+        for (int64_t z = x; z < y; z++) {
+            if (h->dist[z] == mn) {
+                h->read[w] = h->read[z];
+                h->strand[w] = h->strand[z];
+                h->end[w] = h->end[z];
+                h->dist[w] = h->dist[z];
+                w++;
+            }
+        }
+        x = y;
+    }
+    h->n = w;
+}
+
+static char* revcomp_copy(const char* s, int64_t m) {
+    char* o = (char*)malloc((size_t)m + 1);
+    for (int64_t i = 0; i < m; i++) o[i] = complement(s[m - 1 - i]);
+    o[m] = 0;
+    return o;
+}
+
+/* ---- brute force: the definition over the whole reference ---- */
+
+oracle_hits* oracle_map_bruteforce(const char* R, int64_t n, const char* reads, const int64_t* offs,
+                                   int64_t nreads, const int32_t* k, int mode) {
+    if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return NULL;
+    oracle_hits* h = (oracle_hits*)calloc(1, sizeof(oracle_hits));
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* js = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* ds = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t r = 0; r < nreads; r++) {
+        int64_t m = offs[r + 1] - offs[r];
+        for (int s = 0; s < 2; s++) {
+            char* P = s == 0 ? NULL : revcomp_copy(reads + offs[r], m);
+            const char* pat = s == 0 ? reads + offs[r] : P;
+            oracle_semiglobal_column(pat, m, R, n, D);
+            int64_t cnt = 0;
+            for (int64_t j = 0; j < n; j++)
+                if (D[j] <= k[r]) {
+                    js[cnt] = j;
+                    ds[cnt] = D[j];
+                    cnt++;
+                }
+            emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
+            free(P);
+        }
+    }
+    free(D);
+    free(js);
+    free(ds);
+    if (mode == MODE_BEST) best_stratum(h);
+    return h;
+}
+
+/* ---- q-gram filter (Section "Filtration") + windowed DP ---- */
+
+typedef struct { uint64_t key; int64_t head; } slot_t;
+typedef struct { int32_t r; int8_t s; int16_t i; int64_t next; } occ_t;
+
+typedef struct { int64_t* v; int64_t n, cap; } vec64;
+
+static void vec_push(vec64* a, int64_t x) {
+    if (a->n == a->cap) {
+        a->cap = a->cap ? 2 * a->cap : 16;
+        a->v = (int64_t*)realloc(a->v, sizeof(int64_t) * (size_t)a->cap);
+    }
+    a->v[a->n++] = x;
+}
+
+static int cmp_i64(const void* a, const void* b) {
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return x < y ? -1 : x > y;
+}
+
+typedef struct { int64_t lo, hi; } ival;
+
+static int cmp_ival(const void* a, const void* b) {
+    const ival* x = (const ival*)a;
+    const ival* y = (const ival*)b;
+    if (x->lo != y->lo) return x->lo < y->lo ? -1 : 1;
+    return x->hi < y->hi ? -1 : x->hi > y->hi;
+}
+
+/* first index in sorted v[0..n) with v[idx] >= x */
+static int64_t lower_bound(const int64_t* v, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (v[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+static uint64_t hash64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    return x;
+}
+
+/* q-gram code, first base most significant (numeric order = lexicographic order) */
+static uint64_t qgram_code(const char* s, int q) {
+    uint64_t g = 0;
+    for (int t = 0; t < q; t++) g = (g << 2) | (uint64_t)base_code(s[t]);
+    return g;
+}
+
+/* Returns NULL if q is out of range [1, 31], a character is not ACGT, or some read has a
+ * lemma threshold t = m + 1 - q(k + 1) below 1 (the filter would not be lossless). */
+oracle_hits* oracle_map_filter(const char* R, int64_t n, const char* reads, const int64_t* offs,
+                               int64_t nreads, const int32_t* k, int q, int mode) {
+    if (q < 1 || q > 31) return NULL;
+    if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return NULL;
+    for (int64_t r = 0; r < nreads; r++) {
+        int64_t m = offs[r + 1] - offs[r];
+        if (m + 1 - (int64_t)q * (k[r] + 1) < 1) return NULL;
+    }
+    /* 1. index: q-gram code -> list of (read, strand, offset), reads and reverse complements */
+    int64_t total = 0;
+    for (int64_t r = 0; r < nreads; r++) total += 2 * (offs[r + 1] - offs[r] - q + 1);
+    uint64_t cap = 16;
+    while (cap < (uint64_t)(2 * total + 16)) cap <<= 1;
+    slot_t* tab = (slot_t*)malloc(sizeof(slot_t) * cap);
+    for (uint64_t x = 0; x < cap; x++) { tab[x].key = UINT64_MAX; tab[x].head = -1; }
+    occ_t* occ = (occ_t*)malloc(sizeof(occ_t) * (size_t)(total > 0 ? total : 1));
+    int64_t nocc = 0;
+    char** pats = (char**)malloc(sizeof(char*) * (size_t)(2 * nreads + 1));
+    for (int64_t r = 0; r < nreads; r++) {
+        int64_t m = offs[r + 1] - offs[r];
+        pats[2 * r] = (char*)malloc((size_t)m + 1);
+        memcpy(pats[2 * r], reads + offs[r], (size_t)m);
+        pats[2 * r + 1] = revcomp_copy(reads + offs[r], m);
+        for (int s = 0; s < 2; s++) {
+            const char* P = pats[2 * r + s];
+            for (int64_t i = 0; i + q <= m; i++) {
+                uint64_t g = qgram_code(P + i, q);
+                uint64_t x = hash64(g) & (cap - 1);
+                while (tab[x].key != UINT64_MAX && tab[x].key != g) x = (x + 1) & (cap - 1);
+                tab[x].key = g;
+                occ[nocc].r = (int32_t)r;
+                occ[nocc].s = (int8_t)s;
+                occ[nocc].i = (int16_t)i;
+                occ[nocc].next = tab[x].head;
+                tab[x].head = nocc++;
+            }
+        }
+    }
+    /* 2. scan: every reference q-gram, hits on diagonal d = p - i */
+    vec64* dg = (vec64*)calloc((size_t)(2 * nreads + 1), sizeof(vec64));
+    for (int64_t p = 0; p + q <= n; p++) {
+        uint64_t g = qgram_code(R + p, q);
+        uint64_t x = hash64(g) & (cap - 1);
+        while (tab[x].key != UINT64_MAX && tab[x].key != g) x = (x + 1) & (cap - 1);
+        if (tab[x].key != g) continue;
+        for (int64_t e = tab[x].head; e >= 0; e = occ[e].next)
+            vec_push(&dg[2 * occ[e].r + occ[e].s], p - occ[e].i);
+    }
+    /* 3.-5. windows of k+1 diagonals with >= t hits, end ranges, windowed DP */
+    oracle_hits* h = (oracle_hits*)calloc(1, sizeof(oracle_hits));
+    for (int64_t r = 0; r < nreads; r++) {
+        int64_t m = offs[r + 1] - offs[r];
+        int64_t kk = k[r];
+        int64_t t = m + 1 - (int64_t)q * (kk + 1);
+        int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+        for (int s = 0; s < 2; s++) {
+            vec64* v = &dg[2 * r + s];
+            if (v->n == 0) continue;
+            qsort(v->v, (size_t)v->n, sizeof(int64_t), cmp_i64);
+            ival* iv = NULL;
+            int64_t niv = 0, civ = 0;
+            for (int64_t x = 0; x < v->n; x++) {
+                if (x > 0 && v->v[x] == v->v[x - 1]) continue;
+                for (int64_t d0 = v->v[x] - kk; d0 <= v->v[x]; d0++) {
+                    int64_t c = lower_bound(v->v, v->n, d0 + kk + 1) - lower_bound(v->v, v->n, d0);
+                    if (c < t) continue;
+                    if (niv == civ) {
+                        civ = civ ? 2 * civ : 64;
+                        iv = (ival*)realloc(iv, sizeof(ival) * (size_t)civ);
+                    }
+                    iv[niv].lo = d0 + m - 1 - 2 * kk;
+                    iv[niv].hi = d0 + m - 1 + 3 * kk;
+                    niv++;
+                }
+            }
+            if (niv == 0) { free(iv); continue; }
+            qsort(iv, (size_t)niv, sizeof(ival), cmp_ival);
+            /* union of end ranges, clipped to the reference; DP over each merged range */
+            int64_t* js = NULL;
+            int32_t* ds = NULL;
+            int64_t cnt = 0, cj = 0;
+            int64_t x = 0;
+            while (x < niv) {
+                int64_t lo = iv[x].lo, hi = iv[x].hi;
+                x++;
+                while (x < niv && iv[x].lo <= hi + 1) {
+                    if (iv[x].hi > hi) hi = iv[x].hi;
+                    x++;
+                }
+                if (lo < 0) lo = 0;
+                if (hi > n - 1) hi = n - 1;
+                if (lo > hi) continue;
+                int64_t a = lo - (m + kk) + 1;
+                if (a < 0) a = 0;
+                int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(hi - a + 1));
+                dp_columns(pats[2 * r + s], m, R, a, hi, col, D);
+                for (int64_t j = lo; j <= hi; j++) {
+                    if (D[j - a] > kk) continue;
+                    if (cnt == cj) {
+                        cj = cj ? 2 * cj : 64;
+                        js = (int64_t*)realloc(js, sizeof(int64_t) * (size_t)cj);
+                        ds = (int32_t*)realloc(ds, sizeof(int32_t) * (size_t)cj);
+                    }
+                    js[cnt] = j;
+                    ds[cnt] = D[j - a];
+                    cnt++;
+                }
+                free(D);
+            }
+            /* 6. canonical tuple per maximal run */
+            emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
+            free(js);
+            free(ds);
+            free(iv);
+        }
+        free(col);
+    }
+    if (mode == MODE_BEST) best_stratum(h);
+    for (int64_t x = 0; x < 2 * nreads; x++) free(dg[x].v);
+    free(dg);
+    for (int64_t x = 0; x < 2 * nreads; x++) free(pats[x]);
+    free(pats);
+    free(occ);
+    free(tab);
+    return h;
+}
+
+/* ---- Algorithm 1: the q-group index over a text of q-gram codes ---- */
+
+/* GROUPBIT(g) = (g div w, g mod w) */
+static void groupbit(uint64_t g, int w, uint64_t* i, int* j) {
+    *i = g / (uint64_t)w;
+    *j = (int)(g % (uint64_t)w);
+}
+
+static int popcount64(uint64_t x) {
+    int c = 0;
+    while (x) { c += (int)(x & 1); x >>= 1; }
+    return c;
+}
+
+/* GROUPRANK(I, i, j) = popcount(I[i] & (2^j - 1)) */
+static uint64_t grouprank(const uint64_t* I, uint64_t i, int j) {
+    uint64_t mask = j == 0 ? 0 : (j >= 64 ? ~0ULL : ((1ULL << j) - 1));
+    return (uint64_t)popcount64(I[i] & mask);
+}
+
+/* Builds (I, S, S', O) of Algorithm 1 for the text positions 0..T-1 whose q-gram codes are
+ * codes[p]; O stores payload[p] instead of p so the caller can attach (read, offset) labels.
+ * Sizes: I and S have ceil(4^q / w) entries (I holds w-bit words in uint64), S' has T + 1
+ * entries (only the first distinct + 1 are used; the last of those is the sentinel |T|), O has
+ * T entries.  Returns the number of distinct q-grams, or -1 on bad arguments. */
+int64_t oracle_qgroup_build(const uint64_t* codes, const uint64_t* payload, int64_t T, int q, int w,
+                            uint64_t* I, uint64_t* S, uint64_t* Sp, uint64_t* O) {
+    if (q < 1 || q > 31 || w < 1 || w > 64) return -1;
+    uint64_t ngroups = ((1ULL << (2 * q)) + (uint64_t)w - 1) / (uint64_t)w;
+    /* step 1: presence bits */
+    memset(I, 0, sizeof(uint64_t) * ngroups);
+    for (int64_t p = 0; p < T; p++) {
+        uint64_t i;
+        int j;
+        groupbit(codes[p], w, &i, &j);
+        I[i] |= 1ULL << j;
+    }
+    /* steps 2-3: S = exclusive cumulative sum of popcount(I) */
+    uint64_t run = 0;
+    for (uint64_t i = 0; i < ngroups; i++) {
+        uint64_t c = (uint64_t)popcount64(I[i]);
+        S[i] = run;
+        run += c;
+    }
+    uint64_t distinct = run;
+    /* steps 4-5: occurrences per q-gram, then exclusive cumulative sum with sentinel */
+    memset(Sp, 0, sizeof(uint64_t) * (size_t)(T + 1));
+    for (int64_t p = 0; p < T; p++) {
+        uint64_t i;
+        int j;
+        groupbit(codes[p], w, &i, &j);
+        Sp[S[i] + grouprank(I, i, j)] += 1;
+    }
+    run = 0;
+    for (uint64_t x = 0; x <= distinct; x++) {
+        uint64_t c = x < distinct ? Sp[x] : 0;
+        Sp[x] = run;
+        run += c;
+    }
+    /* step 6: every position into the next free entry of its q-gram's interval of O */
+    uint64_t* used = (uint64_t*)calloc((size_t)(distinct + 1), sizeof(uint64_t));
+    for (int64_t p = 0; p < T; p++) {
+        uint64_t i;
+        int j;
+        groupbit(codes[p], w, &i, &j);
+        uint64_t x = S[i] + grouprank(I, i, j);
+        O[Sp[x] + used[x]++] = payload[p];
+    }
+    free(used);
+    return (int64_t)distinct;
+}
+
+/* INDEXPAIR(g) = (S'[S[i] + j'], S'[S[i] + j' + 1]) if bit j of I[i] is set, else (0, 0). */
+void oracle_indexpair(const uint64_t* I, const uint64_t* S, const uint64_t* Sp, int w, uint64_t g,
+                      uint64_t* kstart, uint64_t* kend) {
+    uint64_t i;
+    int j;
+    groupbit(g, w, &i, &j);
+    if (!((I[i] >> j) & 1)) {
+        *kstart = 0;
+        *kend = 0;
+        return;
+    }
+    uint64_t x = S[i] + grouprank(I, i, j);
+    *kstart = Sp[x];
+    *kend = Sp[x + 1];
+}
+
+/* ---- the canonical q-gram text the GPU index is built over ---- */
+
+/* For every read r and offset i in [0, m - q]: g = code of read[i..i+q), h = code of the same
+ * window of the reverse complement read (positions m-q-i .. m-i-1 of revcomp), c = min(g, h),
+ * f = (g != c).  Writes codes[x] = c and payload[x] = (r << 9) | (f << 8) | i in read order, and
+ * returns the count.  Returns -1 on a non-ACGT character or q outside [1, 31]. */
+int64_t oracle_canonical_text(const char* reads, const int64_t* offs, int64_t nreads, int q,
+                              uint64_t* codes, uint64_t* payload) {
+    if (q < 1 || q > 31) return -1;
+    if (check_acgt(reads, offs[nreads] - offs[0])) return -1;
+    int64_t x = 0;
+    for (int64_t r = 0; r < nreads; r++) {
+        int64_t m = offs[r + 1] - offs[r];
+        char* rc = revcomp_copy(reads + offs[r], m);
+        for (int64_t i = 0; i + q <= m; i++) {
+            uint64_t g = qgram_code(reads + offs[r] + i, q);
+            uint64_t h = qgram_code(rc + (m - q - i), q);
+            uint64_t c = g < h ? g : h;
+            codes[x] = c;
+            payload[x] = ((uint64_t)r << 9) | ((uint64_t)(g != c) << 8) | (uint64_t)i;
+            x++;
+        }
+        free(rc);
+    }
+    return x;
+}
+
+/* Occurrence count of every canonical q-gram of the reference whose count exceeds cap:
+ * writes up to max_out (code, count) pairs sorted by code and returns how many exist.
+ * The canonical code of position p is min(code(R[p..p+q)), code(revcomp(R[p..p+q)))). */
+int64_t oracle_frequent_qgrams(const char* R, int64_t n, int q, int64_t cap, uint64_t* out_codes,
+                               int64_t* out_counts, int64_t max_out) {
+    if (q < 1 || q > 31 || check_acgt(R, n)) return -1;
+    int64_t np = n - q + 1;
+    if (np <= 0) return 0;
+    uint64_t* cs = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)np);
+    char* win = (char*)malloc((size_t)q);
+    for (int64_t p = 0; p < np; p++) {
+        for (int t = 0; t < q; t++) win[t] = complement(R[p + q - 1 - t]);
+        uint64_t g = qgram_code(R + p, q), h = qgram_code(win, q);
+        cs[p] = g < h ? g : h;
+    }
+    free(win);
+    qsort(cs, (size_t)np, sizeof(uint64_t), cmp_i64); /* codes < 2^62: signed order = unsigned */
+    int64_t nout = 0, x = 0;
+    while (x < np) {
+        int64_t y = x;
+        while (y < np && cs[y] == cs[x]) y++;
+        if (y - x > cap) {
+            if (nout < max_out) { out_codes[nout] = cs[x]; out_counts[nout] = y - x; }
+            nout++;
+        }
+        x = y;
+    }
+    free(cs);
+    return nout;
+}
