@@ -1,0 +1,200 @@
+/* peanut.h: C ABI of the GB300 (sm_103a) filter-and-verify read-mapping library.
+ *
+ * The library maps DNA reads to a reference with at most k unit-cost edits, following Köster &
+ * Rahmann, "Massively parallel read mapping on GPUs with PEANUT":
+ *   - a q-group index (Section "The q-group index", Algorithm 1) is built over a batch of reads
+ *     on the device;
+ *   - the 2-bit packed reference is streamed past it and q-gram hits are counted per
+ *     (read, strand, diagonal) (Section "Filtration", Algorithm 2);
+ *   - every candidate region is verified with bit-parallel semiglobal edit distance (Section
+ *     "Validation", Myers' algorithm) and reduced to one hit per maximal run of end positions
+ *     within k edits, in all-hits or best-stratum mode (Section "Postprocessing").
+ *
+ * Output definition (exact, no heuristics): for read r of length m with error budget k and
+ * strand s (0 = the read, 1 = its reverse complement, both aligned to the FORWARD reference),
+ * D[j] = min edit distance between the pattern and any reference substring ending at j.  For
+ * every maximal run of consecutive j with D[j] <= k the library reports one hit
+ * (r, s, j*, D[j*]), j* = the leftmost position of the run's minimum.  End positions are 0-based
+ * and inclusive.  Best-stratum mode keeps, per read, only the hits whose D equals the read's
+ * minimum over both strands.  Hits are sorted by (read, strand, end).
+ *
+ * Conventions for every call:
+ *   - Return value: peanut_status; PEANUT_OK = 0.  On failure peanut_last_error() returns a
+ *     message (thread-local, valid until the next call on the same thread).  No call aborts.
+ *   - "host" pointers are CPU memory, "device" pointers are CUDA device memory of the current
+ *     device.  Inputs are caller-owned and only read during the call (device inputs until the
+ *     work queued on the given stream completes).  Outputs are library-owned objects released
+ *     with peanut_free().
+ *   - stream: a cudaStream_t passed as void* (NULL = the legacy default stream).  All device
+ *     work of a call is queued on that stream; calls that return host results synchronize it.
+ *   - Objects may be used from one host thread at a time.
+ *   - Sequences are ASCII 'A','C','G','T' (upper case).  Any other byte (including 'N') makes
+ *     the call fail with PEANUT_INVALID_ARG.
+ */
+#ifndef PEANUT_H
+#define PEANUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PEANUT_OK = 0,
+    PEANUT_INVALID_ARG = 1,  /* bad argument, bad base, read too long, threshold below 1 */
+    PEANUT_NO_MEMORY = 2,    /* a device or host allocation failed */
+    PEANUT_CUDA_ERROR = 3,   /* a CUDA runtime call or kernel failed */
+    PEANUT_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    PEANUT_UNSUPPORTED = 5   /* valid but not supported by this build (e.g. q > 16) */
+} peanut_status;
+
+typedef struct peanut_ref peanut_ref;     /* resident packed reference (device) */
+typedef struct peanut_reads peanut_reads; /* a read batch and its q-group index (device) */
+
+/* Host-side hit list (struct of arrays, n entries each), sorted by (read_id, strand, end_pos). */
+typedef struct {
+    uint64_t n;
+    uint32_t* read_id; /* index of the read within its batch */
+    uint8_t* strand;   /* 0 = read, 1 = reverse complement of the read */
+    uint64_t* end_pos; /* 0-based inclusive end on the forward reference */
+    uint8_t* dist;     /* edit distance, <= the read's k */
+} peanut_hits;
+
+/* Device-side hit list: same layout, pointers are device memory owned by the object. */
+typedef struct {
+    uint64_t n;
+    uint32_t* read_id;
+    uint8_t* strand;
+    uint64_t* end_pos;
+    uint8_t* dist;
+} peanut_device_hits;
+
+/* Per-batch parameters. */
+typedef struct {
+    uint32_t q;          /* q-gram length, 1..16 (Section "The q-group index"; the paper uses 16) */
+    uint32_t k_fixed;    /* error budget of every read; UINT32_MAX = derive from k_permille */
+    uint32_t k_permille; /* k = ceil(length * k_permille / 1000) when k_fixed == UINT32_MAX */
+    uint32_t freq_cap;   /* a canonical q-gram occurring more than freq_cap times in the
+                            reference is not indexed; reads containing such q-grams are verified
+                            around every occurrence cluster instead (exact either way).
+                            0 = default (256) */
+    void* stream;        /* cudaStream_t for all device work of the batch */
+} peanut_params;
+
+/* Counters of the last peanut_map() on a batch (diagnostics; all device-computed). */
+typedef struct {
+    uint64_t hits;             /* q-gram hits emitted by the reference scan */
+    uint64_t candidates;       /* candidate end ranges verified */
+    uint64_t candidate_columns;/* reference columns run through the bit-vector verification */
+    uint64_t results;          /* hits returned */
+    uint64_t lowcx_reads;      /* reads verified around frequent q-gram clusters */
+    uint64_t scan_retries;     /* hit-buffer regrowths */
+    float ms_scan, ms_bin, ms_windows, ms_verify, ms_output; /* device time per stage */
+} peanut_map_stats;
+
+/* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
+ * base most significant; Section "The q-group index", encoding paragraph) and keeps it resident.
+ *   seq: host, len bytes of 'A'/'C'/'G'/'T'.  len: 1 .. 2^39.  stream: see conventions.
+ *   out: receives the new reference object.
+ * Errors: INVALID_ARG (NULL pointer, len out of range, non-ACGT byte), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream, peanut_ref** out);
+
+/* Reference length in bases. */
+uint64_t peanut_ref_length(const peanut_ref* ref);
+
+/* Builds the q-group index (I, S, S', O of Algorithm 1, with the canonical q-gram of every read
+ * position, Section "The q-group index") over a batch of reads, on the device.
+ *   ref: the reference the batch will be mapped against (it must outlive the batch; its
+ *        frequent-q-gram table for this q is computed and cached on first use).
+ *   seqs: host, the concatenated reads; offsets: host, n_reads + 1 ascending byte offsets
+ *        into seqs (read i = seqs[offsets[i] .. offsets[i+1])).
+ *   n_reads: 1 .. 2^23.  Every read length must be 1..255 and every read must satisfy the
+ *        q-gram lemma threshold t = m + 1 - q(k + 1) >= 1 (Section "The q-group index").
+ *   p: parameters (q, k rule, stream).
+ *   out: receives the batch object.
+ * Errors: INVALID_ARG (argument out of range, non-ACGT byte, length or threshold violation),
+ *         UNSUPPORTED (q outside 1..16), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_index_reads(const peanut_ref* ref, const char* seqs, const uint64_t* offsets,
+                                 uint32_t n_reads, const peanut_params* p, peanut_reads** out);
+
+/* Same as peanut_index_reads with the reads already in device memory:
+ *   d_seqs: device, total_bases bytes; d_offsets: device, n_reads + 1 uint64 offsets. */
+peanut_status peanut_index_reads_device(const peanut_ref* ref, const char* d_seqs,
+                                        const uint64_t* d_offsets, uint32_t n_reads,
+                                        uint64_t total_bases, const peanut_params* p,
+                                        peanut_reads** out);
+
+/* Maps a batch: reference scan and hit counting (Algorithm 2), candidate compaction, bit-vector
+ * verification (Section "Validation") and per-read stratum reduction (Section "Postprocessing").
+ *   mode: 0 = all hits, 1 = best stratum.
+ *   out: receives a host hit list (see peanut_hits), sorted by (read_id, strand, end_pos).
+ * Synchronizes the batch's stream.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA_ERROR, TIMEOUT. */
+peanut_status peanut_map(const peanut_ref* ref, peanut_reads* reads, int mode, peanut_hits** out);
+
+/* Same as peanut_map with the result left in device memory (peanut_device_hits). */
+peanut_status peanut_map_device(const peanut_ref* ref, peanut_reads* reads, int mode,
+                                peanut_device_hits** out);
+
+/* Copies a device hit list to a new host hit list. */
+peanut_status peanut_download_hits(const peanut_device_hits* dh, void* stream, peanut_hits** out);
+
+/* Counters and stage times of the last map call on this batch. */
+peanut_status peanut_get_map_stats(const peanut_reads* reads, peanut_map_stats* out);
+
+/* Frees any object returned by this library (peanut_ref, peanut_reads, peanut_hits,
+ * peanut_device_hits).  NULL is a no-op.  Device memory is released on the object's stream. */
+void peanut_free(void* obj);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char* peanut_last_error(void);
+
+/* Device memory provider for all later allocations (e.g. a caching allocator of the host
+ * framework).  alloc(bytes, stream, ctx) returns device memory or NULL; release(ptr, stream,
+ * ctx) frees it.  Passing NULL functions restores the default (cudaMallocAsync /
+ * cudaFreeAsync on the stream).  Not thread-safe with concurrent calls. */
+typedef void* (*peanut_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*peanut_release_fn)(void* ptr, void* stream, void* ctx);
+peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn release, void* ctx);
+
+/* ---- introspection used by the parity tests ---- */
+
+/* Sizes of a batch's q-group index: n_groups = ceil(4^q / 32) (entries of I and S),
+ * n_distinct = distinct indexed q-grams (S' has n_distinct + 1 entries, the last = n_indexed),
+ * n_indexed = indexed q-gram positions (entries of O). */
+peanut_status peanut_index_sizes(const peanut_reads* reads, uint64_t* n_groups, uint64_t* n_distinct,
+                                 uint64_t* n_indexed);
+
+/* Copies the index arrays to host buffers sized by peanut_index_sizes (any pointer may be NULL):
+ * I[n_groups] (bit j of I[i] = canonical q-gram 32 i + j occurs), S[n_groups] (exclusive
+ * cumulative popcount of I), Sp[n_distinct + 1], O[n_indexed] (entries
+ * (read << 9) | (orientation << 8) | offset; orientation 1 = the read holds the reverse
+ * complement of the canonical q-gram at that offset). */
+peanut_status peanut_export_index(const peanut_reads* reads, uint32_t* I, uint32_t* S, uint32_t* Sp,
+                                  uint32_t* O);
+
+/* Per-read filter parameters chosen at indexing: thr[i] = q-gram count threshold used for read i,
+ * lowcx[i] = 1 if read i is verified around frequent-q-gram clusters (host arrays of n_reads). */
+peanut_status peanut_export_read_params(const peanut_reads* reads, uint16_t* thr, uint8_t* lowcx);
+
+/* Candidate end ranges of the last map call (host arrays of *n entries, or NULL to query n):
+ * read, strand, lo, hi (inclusive, clipped to the reference). */
+peanut_status peanut_export_candidates(const peanut_reads* reads, uint64_t* n, uint32_t* read,
+                                       uint8_t* strand, uint64_t* lo, uint64_t* hi);
+
+/* Runs the bit-vector verification kernel alone: for pattern i (ASCII, lengths 1..255, host
+ * arrays pat / pat_off[n_pat + 1]) against text i (ASCII, host arrays txt / txt_off[n_pat + 1]),
+ * writes D[j] (semiglobal distance of the whole pattern ending at text position j, boundary
+ * E[i][-1] = i) to out (host, txt_off[n_pat] int32 entries).  Test hook for the kernel that
+ * peanut_map uses. */
+peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat,
+                                             const char* txt, const uint64_t* txt_off, int32_t* out,
+                                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEANUT_H */

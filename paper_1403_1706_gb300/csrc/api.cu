@@ -1,0 +1,409 @@
+// The C ABI (include/peanut.h): argument checks, object lifetimes, errors, device memory.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace pn {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+static peanut_alloc_fn g_alloc = nullptr;
+static peanut_release_fn g_release = nullptr;
+static void* g_ctx = nullptr;
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (g_alloc) {
+        p = g_alloc(bytes, (void*)s, g_ctx);
+        if (!p) {
+            set_error("device allocation of %zu bytes failed (external allocator)", bytes);
+            throw Fail{PEANUT_NO_MEMORY};
+        }
+        return p;
+    }
+    const cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        throw Fail{PEANUT_NO_MEMORY};
+    }
+    return p;
+}
+
+void dfree(void* p, cudaStream_t s) {
+    if (!p) return;
+    if (g_release) {
+        g_release(p, (void*)s, g_ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+void free_device_hits(DeviceHits* H);
+
+}  // namespace pn
+
+using namespace pn;
+
+template <class F>
+static peanut_status guarded(F&& f) {
+    clear_error();
+    try {
+        f();
+        return PEANUT_OK;
+    } catch (const Fail& e) {
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return PEANUT_NO_MEMORY;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PEANUT_CUDA_ERROR;
+    }
+}
+
+extern "C" {
+
+const char* peanut_last_error(void) { return g_err; }
+
+peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn release, void* ctx) {
+    return guarded([&] {
+        PN_REQUIRE((alloc == nullptr) == (release == nullptr), PEANUT_INVALID_ARG,
+                   "allocator and release must both be set or both be NULL");
+        g_alloc = alloc;
+        g_release = release;
+        g_ctx = ctx;
+    });
+}
+
+peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream, peanut_ref** out) {
+    return guarded([&] {
+        PN_REQUIRE(seq && out, PEANUT_INVALID_ARG, "NULL argument");
+        PN_REQUIRE(len >= 1 && len < kMaxRefLen, PEANUT_INVALID_ARG, "reference length %llu outside 1..2^39",
+                   (unsigned long long)len);
+        *out = nullptr;
+        peanut_ref* ref = new peanut_ref();
+        ref->stream = (cudaStream_t)stream;
+        try {
+            pack_reference(ref, seq, len, ref->stream);
+        } catch (...) {
+            delete ref;
+            throw;
+        }
+        *out = ref;
+    });
+}
+
+uint64_t peanut_ref_length(const peanut_ref* ref) {
+    return ref && ref->magic == kMagicRef ? ref->n : 0;
+}
+
+static void check_params(const peanut_params* p) {
+    PN_REQUIRE(p, PEANUT_INVALID_ARG, "NULL params");
+    PN_REQUIRE(p->q >= 1 && p->q <= 16, PEANUT_UNSUPPORTED, "q = %u outside 1..16", p->q);
+    PN_REQUIRE(p->k_fixed != 0xFFFFFFFFu || p->k_permille <= 1000, PEANUT_INVALID_ARG, "k_permille > 1000");
+}
+
+static peanut_status index_common(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets,
+                                  uint32_t n_reads, uint64_t total, const peanut_params* p, peanut_reads** out,
+                                  bool host_input, const char* h_seqs, const uint64_t* h_offsets) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && out, PEANUT_INVALID_ARG, "bad reference or NULL out");
+        check_params(p);
+        PN_REQUIRE(n_reads >= 1 && n_reads <= kMaxReads, PEANUT_INVALID_ARG, "n_reads = %u outside 1..2^23", n_reads);
+        *out = nullptr;
+        cudaStream_t s = (cudaStream_t)p->stream;
+        const uint32_t cap = p->freq_cap ? p->freq_cap : kDefaultFreqCap;
+        peanut_ref* mref = const_cast<peanut_ref*>(ref);
+        if (!mref->prep[p->q] || mref->prep[p->q]->cap != cap) {
+            if (mref->prep[p->q]) {
+                free_prep(mref->prep[p->q]);
+                mref->prep[p->q] = nullptr;
+            }
+            mref->prep[p->q] = prepare_reference(ref, p->q, cap, s);
+        }
+        peanut_reads* R = new peanut_reads();
+        try {
+            R->ref = ref;
+            R->stream = s;
+            R->q = p->q;
+            R->n_reads = n_reads;
+            R->freq_cap = cap;
+            R->total_bases = total;
+            if (host_input) {
+                DBuf<char> ds(total ? total : 1, s);
+                DBuf<uint64_t> doff((uint64_t)n_reads + 1, s);
+                if (total) PN_CUDA(cudaMemcpyAsync(ds.p, h_seqs, total, cudaMemcpyHostToDevice, s));
+                PN_CUDA(cudaMemcpyAsync(doff.p, h_offsets, ((uint64_t)n_reads + 1) * sizeof(uint64_t),
+                                        cudaMemcpyHostToDevice, s));
+                index_reads(R, ds.p, doff.p, p->k_fixed, p->k_permille);
+            } else {
+                index_reads(R, d_seqs, d_offsets, p->k_fixed, p->k_permille);
+            }
+        } catch (...) {
+            delete R;
+            throw;
+        }
+        *out = R;
+    });
+}
+
+peanut_status peanut_index_reads(const peanut_ref* ref, const char* seqs, const uint64_t* offsets,
+                                 uint32_t n_reads, const peanut_params* p, peanut_reads** out) {
+    if (!seqs || !offsets) {
+        set_error("NULL argument");
+        return PEANUT_INVALID_ARG;
+    }
+    if (n_reads >= 1 && n_reads <= kMaxReads) {
+        for (uint32_t i = 0; i < n_reads; ++i)
+            if (offsets[i + 1] < offsets[i]) {
+                set_error("read offsets must ascend");
+                return PEANUT_INVALID_ARG;
+            }
+        if (offsets[0] != 0) {
+            // rebase: the device copy starts at offsets[0]
+            uint64_t* o = (uint64_t*)malloc(((uint64_t)n_reads + 1) * sizeof(uint64_t));
+            if (!o) return PEANUT_NO_MEMORY;
+            for (uint32_t i = 0; i <= n_reads; ++i) o[i] = offsets[i] - offsets[0];
+            const peanut_status st =
+                index_common(ref, nullptr, nullptr, n_reads, o[n_reads], p, out, true, seqs + offsets[0], o);
+            free(o);
+            return st;
+        }
+    }
+    const uint64_t total = (n_reads >= 1 && n_reads <= kMaxReads) ? offsets[n_reads] : 0;
+    return index_common(ref, nullptr, nullptr, n_reads, total, p, out, true, seqs, offsets);
+}
+
+peanut_status peanut_index_reads_device(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets,
+                                        uint32_t n_reads, uint64_t total_bases, const peanut_params* p,
+                                        peanut_reads** out) {
+    if (!d_seqs || !d_offsets) {
+        set_error("NULL argument");
+        return PEANUT_INVALID_ARG;
+    }
+    return index_common(ref, d_seqs, d_offsets, n_reads, total_bases, p, out, false, nullptr, nullptr);
+}
+
+peanut_status peanut_map_device(const peanut_ref* ref, peanut_reads* reads, int mode, peanut_device_hits** out) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && reads && reads->magic == kMagicReads && out, PEANUT_INVALID_ARG,
+                   "bad reference, batch or NULL out");
+        PN_REQUIRE(reads->ref == ref, PEANUT_INVALID_ARG, "batch was indexed against another reference");
+        PN_REQUIRE(mode == 0 || mode == 1, PEANUT_INVALID_ARG, "mode must be 0 (all) or 1 (best stratum)");
+        *out = nullptr;
+        DeviceHits* H = map_batch(ref, reads, mode);
+        *out = &H->h;
+    });
+}
+
+static DeviceHits* dh_of(const peanut_device_hits* h) {
+    return reinterpret_cast<DeviceHits*>(reinterpret_cast<char*>(const_cast<peanut_device_hits*>(h)) -
+                                         offsetof(DeviceHits, h));
+}
+
+static HostHits* hh_of(peanut_hits* h) {
+    return reinterpret_cast<HostHits*>(reinterpret_cast<char*>(h) - offsetof(HostHits, h));
+}
+
+peanut_status peanut_download_hits(const peanut_device_hits* dh, void* stream, peanut_hits** out) {
+    return guarded([&] {
+        PN_REQUIRE(dh && out && dh_of(dh)->magic == kMagicDHits, PEANUT_INVALID_ARG, "bad device hits");
+        *out = nullptr;
+        cudaStream_t s = (cudaStream_t)stream;
+        HostHits* H = new HostHits();
+        const uint64_t n = dh->n;
+        H->h.n = n;
+        const uint64_t c = n ? n : 1;
+        H->h.read_id = (uint32_t*)malloc(c * sizeof(uint32_t));
+        H->h.strand = (uint8_t*)malloc(c);
+        H->h.end_pos = (uint64_t*)malloc(c * sizeof(uint64_t));
+        H->h.dist = (uint8_t*)malloc(c);
+        if (!H->h.read_id || !H->h.strand || !H->h.end_pos || !H->h.dist) {
+            free(H->h.read_id);
+            free(H->h.strand);
+            free(H->h.end_pos);
+            free(H->h.dist);
+            delete H;
+            set_error("host allocation failed");
+            throw Fail{PEANUT_NO_MEMORY};
+        }
+        if (n) {
+            PN_CUDA(cudaMemcpyAsync(H->h.read_id, dh->read_id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.strand, dh->strand, n, cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.end_pos, dh->end_pos, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.dist, dh->dist, n, cudaMemcpyDeviceToHost, s));
+        }
+        PN_CUDA(cudaStreamSynchronize(s));
+        *out = &H->h;
+    });
+}
+
+peanut_status peanut_map(const peanut_ref* ref, peanut_reads* reads, int mode, peanut_hits** out) {
+    peanut_device_hits* dh = nullptr;
+    peanut_status st = peanut_map_device(ref, reads, mode, &dh);
+    if (st != PEANUT_OK) return st;
+    st = peanut_download_hits(dh, (void*)reads->stream, out);
+    peanut_free(dh);
+    return st;
+}
+
+peanut_status peanut_get_map_stats(const peanut_reads* reads, peanut_map_stats* out) {
+    return guarded([&] {
+        PN_REQUIRE(reads && reads->magic == kMagicReads && out, PEANUT_INVALID_ARG, "bad batch");
+        *out = reads->stats;
+    });
+}
+
+void peanut_free(void* obj) {
+    if (!obj) return;
+    const uint32_t magic = *static_cast<const uint32_t*>(obj);
+    if (magic == kMagicRef) {
+        peanut_ref* r = static_cast<peanut_ref*>(obj);
+        cudaStreamSynchronize(r->stream);
+        for (auto& p : r->prep)
+            if (p) free_prep(p);
+        r->magic = 0;
+        delete r;
+        return;
+    }
+    if (magic == kMagicReads) {
+        peanut_reads* R = static_cast<peanut_reads*>(obj);
+        cudaStreamSynchronize(R->stream);
+        R->magic = 0;
+        delete R;
+        return;
+    }
+    // hit lists are passed by their public struct; their headers sit just before it
+    HostHits* hh = hh_of(static_cast<peanut_hits*>(obj));
+    if (hh->magic == kMagicHits) {
+        free(hh->h.read_id);
+        free(hh->h.strand);
+        free(hh->h.end_pos);
+        free(hh->h.dist);
+        hh->magic = 0;
+        delete hh;
+        return;
+    }
+    DeviceHits* dh = dh_of(static_cast<peanut_device_hits*>(obj));
+    if (dh->magic == kMagicDHits) {
+        free_device_hits(dh);
+        dh->magic = 0;
+        delete dh;
+        return;
+    }
+}
+
+peanut_status peanut_index_sizes(const peanut_reads* R, uint64_t* n_groups, uint64_t* n_distinct,
+                                 uint64_t* n_indexed) {
+    return guarded([&] {
+        PN_REQUIRE(R && R->magic == kMagicReads, PEANUT_INVALID_ARG, "bad batch");
+        if (n_groups) *n_groups = R->n_groups;
+        if (n_distinct) *n_distinct = R->n_distinct;
+        if (n_indexed) *n_indexed = R->n_indexed;
+    });
+}
+
+peanut_status peanut_export_index(const peanut_reads* R, uint32_t* I, uint32_t* S, uint32_t* Sp, uint32_t* O) {
+    return guarded([&] {
+        PN_REQUIRE(R && R->magic == kMagicReads, PEANUT_INVALID_ARG, "bad batch");
+        cudaStream_t s = R->stream;
+        if (I || S) {
+            uint2* tmp = (uint2*)malloc(R->n_groups * sizeof(uint2));
+            PN_REQUIRE(tmp, PEANUT_NO_MEMORY, "host allocation failed");
+            const cudaError_t e = cudaMemcpyAsync(tmp, R->IS.p, R->n_groups * sizeof(uint2), cudaMemcpyDeviceToHost, s);
+            const cudaError_t e2 = cudaStreamSynchronize(s);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                free(tmp);
+                set_error("copy of the index failed");
+                throw Fail{PEANUT_CUDA_ERROR};
+            }
+            for (uint64_t g = 0; g < R->n_groups; ++g) {
+                if (I) I[g] = tmp[g].x;
+                if (S) S[g] = tmp[g].y;
+            }
+            free(tmp);
+        }
+        if (Sp) PN_CUDA(cudaMemcpyAsync(Sp, R->Sp.p, (R->n_distinct + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        if (O && R->n_indexed)
+            PN_CUDA(cudaMemcpyAsync(O, R->O.p, R->n_indexed * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+peanut_status peanut_export_read_params(const peanut_reads* R, uint16_t* thr, uint8_t* lowcx) {
+    return guarded([&] {
+        PN_REQUIRE(R && R->magic == kMagicReads, PEANUT_INVALID_ARG, "bad batch");
+        cudaStream_t s = R->stream;
+        if (thr) PN_CUDA(cudaMemcpyAsync(thr, R->thr.p, R->n_reads * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
+        if (lowcx) PN_CUDA(cudaMemcpyAsync(lowcx, R->lowcx.p, R->n_reads, cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+peanut_status peanut_export_candidates(const peanut_reads* R, uint64_t* n, uint32_t* read, uint8_t* strand,
+                                       uint64_t* lo, uint64_t* hi) {
+    return guarded([&] {
+        PN_REQUIRE(R && R->magic == kMagicReads && n, PEANUT_INVALID_ARG, "bad batch or NULL n");
+        const uint64_t nc = R->n_cand;
+        if (!read && !strand && !lo && !hi) {
+            *n = nc;
+            return;
+        }
+        PN_REQUIRE(*n >= nc, PEANUT_INVALID_ARG, "buffers hold %llu entries, %llu needed", (unsigned long long)*n,
+                   (unsigned long long)nc);
+        *n = nc;
+        if (!nc) return;
+        uint64_t* k = (uint64_t*)malloc(nc * 8);
+        uint64_t* h = (uint64_t*)malloc(nc * 8);
+        PN_REQUIRE(k && h, PEANUT_NO_MEMORY, "host allocation failed");
+        cudaStream_t s = R->stream;
+        cudaMemcpyAsync(k, R->cand_key.p, nc * 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h, R->cand_hi.p, nc * 8, cudaMemcpyDeviceToHost, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        for (uint64_t x = 0; x < nc && e == cudaSuccess; ++x) {
+            if (read) read[x] = (uint32_t)(k[x] >> 41);
+            if (strand) strand[x] = (uint8_t)((k[x] >> 40) & 1);
+            if (lo) lo[x] = k[x] & ((1ull << 40) - 1);
+            if (hi) hi[x] = h[x];
+        }
+        free(k);
+        free(h);
+        PN_REQUIRE(e == cudaSuccess, PEANUT_CUDA_ERROR, "candidate copy failed: %s", cudaGetErrorString(e));
+    });
+}
+
+peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
+                                             const uint64_t* txt_off, int32_t* out, void* stream) {
+    return guarded([&] {
+        PN_REQUIRE(pat && pat_off && txt && txt_off && out && n_pat >= 1, PEANUT_INVALID_ARG, "bad arguments");
+        bitvector_columns(pat, pat_off, n_pat, txt, txt_off, out, (cudaStream_t)stream);
+    });
+}
+
+}  // extern "C"

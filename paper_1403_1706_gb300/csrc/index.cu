@@ -1,0 +1,560 @@
+// Reference packing, the reference's frequent-q-gram clusters, and the q-group index over reads.
+//
+// Encoding (Section "The q-group index"): A=00 C=01 G=10 T=11, a q-gram is the 2q-bit number
+// with its first base most significant.  The index is Algorithm 1 run over the CANONICAL code
+// c = min(g, revcomp(g)) of every read q-gram, so one index serves both strands; each
+// occurrence records whether the read holds c itself or its reverse complement.
+#include <cstdio>
+
+#include "prims.cuh"
+
+namespace pn {
+
+__constant__ uint8_t kCodeLut[256];
+
+static void init_lut() {
+    static bool done = false;
+    if (done) return;
+    uint8_t lut[256];
+    for (int i = 0; i < 256; ++i) lut[i] = 0xFF;
+    lut['A'] = 0;
+    lut['C'] = 1;
+    lut['G'] = 2;
+    lut['T'] = 3;
+    PN_CUDA(cudaMemcpyToSymbol(kCodeLut, lut, sizeof(lut)));
+    done = true;
+}
+
+// ---- reference packing --------------------------------------------------------------------
+
+// One packed word (16 bases) per thread; bytes at or beyond len pack as A (never read as data).
+__global__ void pack_reference_k(const uint8_t* __restrict__ ascii, uint64_t len,
+                                 uint32_t* __restrict__ words, uint32_t* status) {
+    const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t b0 = w * 16;
+    if (b0 >= len) return;
+    uint8_t buf[16];
+    if (b0 + 16 <= len) {
+        const uint4 v = *reinterpret_cast<const uint4*>(ascii + b0);
+        *reinterpret_cast<uint4*>(buf) = v;
+    } else {
+        for (int t = 0; t < 16; ++t) buf[t] = b0 + t < len ? ascii[b0 + t] : 'A';
+    }
+    uint32_t word = 0;
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        const uint8_t c = kCodeLut[buf[t]];
+        bad |= c > 3;
+        word |= (uint32_t)(c & 3) << (30 - 2 * t);
+    }
+    words[w] = word;
+    if (bad) atomicOr(status, kStBadBase);
+}
+
+void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s) {
+    init_lut();
+    ref->n = len;
+    ref->n_words = (len + 15) / 16 + 8;  // lookahead padding for the scan's 64-bit windows
+    ref->packed.alloc(ref->n_words, s);
+    ref->packed.zero();
+    DBuf<uint32_t> status(1, s);
+    status.zero();
+    const uint64_t chunk = 1ull << 30;  // bases per upload (multiple of 16)
+    DBuf<uint8_t> tmp(len < chunk ? ((len + 15) / 16) * 16 : chunk, s);
+    for (uint64_t b = 0; b < len; b += chunk) {
+        const uint64_t nb = len - b < chunk ? len - b : chunk;
+        PN_CUDA(cudaMemcpyAsync(tmp.p, host_seq + b, nb, cudaMemcpyHostToDevice, s));
+        const uint64_t nw = (nb + 15) / 16;
+        pack_reference_k<<<grid_for(nw, 256), 256, 0, s>>>(tmp.p, nb, ref->packed.p + b / 16, status.p);
+        PN_CHECK_LAUNCH();
+    }
+    const uint32_t st = to_host(status.p, s);
+    PN_REQUIRE(!(st & kStBadBase), PEANUT_INVALID_ARG, "reference contains a byte other than A/C/G/T");
+}
+
+// ---- frequent q-grams of the reference ------------------------------------------------------
+
+// 2q-bit code of the q-gram starting at chunk offset o (0..31) of a 32-base chunk whose packed
+// words are w[0..2] (w[0] holds the chunk's first 16 bases).
+__device__ __forceinline__ uint32_t chunk_code(const uint32_t w[3], int o, uint32_t q) {
+    const uint64_t win = ((uint64_t)w[o >> 4] << 32) | w[(o >> 4) + 1];
+    const uint64_t g = win >> (64 - 2 * q - 2 * (o & 15));
+    return q == 16 ? (uint32_t)g : (uint32_t)g & ((1u << (2 * q)) - 1u);
+}
+
+// tab[c] += 1 for the canonical code c of every reference position p <= n - q.
+__global__ void ref_count_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, uint32_t* tab) {
+    const uint64_t nchunks = (n + 31) / 32;
+    for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
+         ch += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p0 = ch * 32;
+        const uint32_t w[3] = {packed[p0 / 16], packed[p0 / 16 + 1], packed[p0 / 16 + 2]};
+        for (int o = 0; o < 32; ++o) {
+            const uint64_t p = p0 + o;
+            if (p + q > n) break;
+            const uint32_t g = chunk_code(w, o, q);
+            const uint32_t h = revcomp_code(g, q);
+            atomicAdd(&tab[g < h ? g : h], 1u);
+        }
+    }
+}
+
+__global__ void phi_collect_k(const uint32_t* tab, uint64_t size, uint32_t cap, uint64_t* out,
+                              unsigned long long* n_out) {
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < size;
+         c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = tab[c];
+        if (v > cap) {
+            const unsigned long long i = atomicAdd(n_out, 1ull);
+            if (out) out[i] = (c << 32) | v;
+        }
+    }
+}
+
+__global__ void phi_mark_k(const uint64_t* keys, uint32_t n_phi, uint32_t* tab, uint32_t* codes,
+                           uint64_t* counts, uint32_t* filter, uint32_t shift) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_phi) return;
+    const uint32_t c = (uint32_t)(keys[i] >> 32);
+    codes[i] = c;
+    counts[i] = keys[i] & 0xFFFFFFFFull;
+    tab[c] = 0x80000000u | i;
+    const uint32_t b = c >> shift;
+    atomicOr(&filter[b >> 5], 1u << (b & 31));
+}
+
+// For each position whose canonical q-gram is frequent: key = phi << 41 | orientation << 40 | p.
+__global__ void ref_occ_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q,
+                          const uint32_t* __restrict__ tab, uint64_t* occ, unsigned long long* n_occ) {
+    const uint64_t nchunks = (n + 31) / 32;
+    for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
+         ch += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p0 = ch * 32;
+        const uint32_t w[3] = {packed[p0 / 16], packed[p0 / 16 + 1], packed[p0 / 16 + 2]};
+        for (int o = 0; o < 32; ++o) {
+            const uint64_t p = p0 + o;
+            if (p + q > n) break;
+            const uint32_t g = chunk_code(w, o, q);
+            const uint32_t h = revcomp_code(g, q);
+            const uint32_t v = tab[g < h ? g : h];
+            if (v & 0x80000000u) {
+                const uint64_t phi = v & 0x7FFFFFFFu;
+                const unsigned long long i = atomicAdd(n_occ, 1ull);
+                occ[i] = (phi << 41) | ((uint64_t)(g > h) << 40) | p;
+            }
+        }
+    }
+}
+
+__global__ void cluster_start_k(const uint64_t* occ, uint64_t n, uint32_t* start) {
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint64_t mask = (1ull << 40) - 1;
+    bool s = x == 0;
+    if (!s) {
+        const uint64_t a = occ[x - 1], b = occ[x];
+        s = (a >> 40) != (b >> 40) || (b & mask) - (a & mask) > kClusterGap;
+    }
+    start[x] = s;
+}
+
+__global__ void cluster_write_k(const uint64_t* occ, uint64_t n, const uint32_t* start,
+                                const uint64_t* sid, uint64_t* lo, uint64_t* hi, uint64_t* gcnt) {
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint64_t mask = (1ull << 40) - 1;
+    const uint64_t p = occ[x] & mask;
+    const bool s = start[x];
+    const uint64_t cid = s ? sid[x] : sid[x] - 1;
+    if (s) {
+        lo[cid] = p;
+        atomicAdd((unsigned long long*)&gcnt[occ[x] >> 40], 1ull);
+    }
+    if (x + 1 == n || start[x + 1]) hi[cid] = p;
+}
+
+void free_prep(RefPrep* p) { delete p; }
+
+RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s) {
+    RefPrep* P = new RefPrep();
+    try {
+        P->q = q;
+        P->cap = cap;
+        const uint64_t size = 1ull << (2 * q);
+        P->filter_shift = 2 * q > (uint32_t)kFilterBits ? 2 * q - kFilterBits : 0;
+        P->filter.alloc((1ull << kFilterBits) / 32, s);
+        P->filter.zero();
+        const uint64_t n = ref->n;
+        if (n < q) {
+            P->grp_off.alloc(1, s);
+            P->grp_off.zero();
+            return P;
+        }
+        DBuf<uint32_t> tab(size, s);
+        tab.zero();
+        const uint64_t nchunks = (n + 31) / 32;
+        const unsigned g = grid_for(nchunks, 256, (unsigned)sm_count() * 32);
+        ref_count_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, tab.p);
+        PN_CHECK_LAUNCH();
+        DBuf<unsigned long long> cnt(1, s);
+        cnt.zero();
+        const unsigned gt = grid_for(size, 256, (unsigned)sm_count() * 64);
+        phi_collect_k<<<gt, 256, 0, s>>>(tab.p, size, cap, nullptr, cnt.p);
+        PN_CHECK_LAUNCH();
+        const uint64_t n_phi = to_host(cnt.p, s);
+        PN_REQUIRE(n_phi < (1ull << 23), PEANUT_UNSUPPORTED, "too many frequent q-grams (%llu)",
+                   (unsigned long long)n_phi);
+        P->n_phi = (uint32_t)n_phi;
+        if (n_phi == 0) {
+            P->grp_off.alloc(1, s);
+            P->grp_off.zero();
+            return P;
+        }
+        DBuf<uint64_t> keys(n_phi, s), tmpk(n_phi, s);
+        cnt.zero();
+        phi_collect_k<<<gt, 256, 0, s>>>(tab.p, size, cap, keys.p, cnt.p);
+        PN_CHECK_LAUNCH();
+        radix_sort_u64(keys.p, tmpk.p, n_phi, 64, s);
+        P->phi_codes.alloc(n_phi, s);
+        DBuf<uint64_t> counts(n_phi, s);
+        phi_mark_k<<<grid_for(n_phi, 256), 256, 0, s>>>(keys.p, (uint32_t)n_phi, tab.p, P->phi_codes.p,
+                                                        counts.p, P->filter.p, P->filter_shift);
+        PN_CHECK_LAUNCH();
+        // every occurrence of a frequent q-gram, sorted by (phi, orientation, position)
+        DBuf<uint64_t> tot(1, s);
+        DBuf<uint64_t> scratch(n_phi, s);
+        exclusive_scan(ArrayIn<uint64_t>{counts.p}, ArrayOut<uint64_t>{scratch.p}, n_phi, tot.p, s);
+        const uint64_t n_occ = to_host(tot.p, s);
+        P->n_occ = n_occ;
+        DBuf<uint64_t> occ(n_occ, s), occ_tmp(n_occ, s);
+        cnt.zero();
+        ref_occ_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, tab.p, occ.p, cnt.p);
+        PN_CHECK_LAUNCH();
+        tab.reset();
+        int phi_bits = 0;
+        while ((1ull << phi_bits) < n_phi) ++phi_bits;
+        radix_sort_u64(occ.p, occ_tmp.p, n_occ, 41 + phi_bits, s);
+        occ_tmp.reset();
+        // clusters: maximal runs of one (phi, orientation) with gaps <= kClusterGap
+        DBuf<uint32_t> start(n_occ, s);
+        DBuf<uint64_t> sid(n_occ, s);
+        cluster_start_k<<<grid_for(n_occ, 256), 256, 0, s>>>(occ.p, n_occ, start.p);
+        PN_CHECK_LAUNCH();
+        exclusive_scan(ArrayIn<uint32_t>{start.p}, ArrayOut<uint64_t>{sid.p}, n_occ, tot.p, s);
+        const uint64_t ncl = to_host(tot.p, s);
+        P->n_clusters = ncl;
+        P->cl_lo.alloc(ncl, s);
+        P->cl_hi.alloc(ncl, s);
+        DBuf<uint64_t> gcnt(2 * n_phi + 1, s);
+        gcnt.zero();
+        cluster_write_k<<<grid_for(n_occ, 256), 256, 0, s>>>(occ.p, n_occ, start.p, sid.p, P->cl_lo.p,
+                                                             P->cl_hi.p, gcnt.p);
+        PN_CHECK_LAUNCH();
+        P->grp_off.alloc(2 * n_phi + 1, s);
+        exclusive_scan(ArrayIn<uint64_t>{gcnt.p}, ArrayOut<uint64_t>{P->grp_off.p}, 2 * n_phi + 1, nullptr, s);
+        PN_CUDA(cudaStreamSynchronize(s));
+        return P;
+    } catch (...) {
+        delete P;
+        throw;
+    }
+}
+
+// ---- the read batch ---------------------------------------------------------------------
+
+__device__ __forceinline__ int phi_lookup(uint32_t c, const uint32_t* __restrict__ filter, uint32_t shift,
+                                          const uint32_t* __restrict__ codes, uint32_t n) {
+    if (n == 0) return -1;
+    const uint32_t b = c >> shift;
+    if (!((filter[b >> 5] >> (b & 31)) & 1u)) return -1;
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (codes[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && codes[lo] == c ? (int)lo : -1;
+}
+
+__global__ void read_meta_k(const uint64_t* __restrict__ off, uint32_t n_reads, uint64_t total,
+                            uint32_t q, uint32_t k_fixed, uint32_t k_permille, uint8_t* len, uint8_t* kk,
+                            uint64_t* nq, uint32_t* status, uint32_t* maxes) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_reads) return;
+    const uint64_t a = off[r], b = off[r + 1];
+    if (b < a || b > total || b - a < 1 || b - a > (uint64_t)kMaxReadLen) {
+        atomicOr(status, kStBadLength);
+        len[r] = 0;
+        kk[r] = 0;
+        nq[r] = 0;
+        return;
+    }
+    const uint32_t m = (uint32_t)(b - a);
+    uint64_t k = k_fixed != 0xFFFFFFFFu ? k_fixed : ((uint64_t)m * k_permille + 999) / 1000;
+    const int64_t t = (int64_t)m + 1 - (int64_t)q * (int64_t)(k + 1);
+    if (t < 1 || k > 255) {
+        atomicOr(status, kStBadThreshold);
+        k = 0;
+    }
+    len[r] = (uint8_t)m;
+    kk[r] = (uint8_t)k;
+    nq[r] = m >= q ? m - q + 1 : 0;
+    atomicMax(&maxes[0], m);
+    atomicMax(&maxes[1], (uint32_t)k);
+}
+
+__global__ void read_codes_k(const uint8_t* __restrict__ ascii, uint64_t total, uint8_t* codes, uint32_t* status) {
+    bool bad = false;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint8_t c = kCodeLut[ascii[x]];
+        bad |= c > 3;
+        codes[x] = c & 3;
+    }
+    if (bad) atomicOr(status, kStBadBase);
+}
+
+// Classifies every read q-gram (one warp per read): canonical code, orientation, whether it is
+// frequent in the reference.  Indexed q-grams go to (tcode, tpay); frequent ones to fent.  Then
+// chooses the read's filter threshold: t* = (#non-frequent offsets) - (most non-frequent offsets
+// that k windows of q consecutive offsets can cover) is the q-gram lemma bound restricted to the
+// indexed q-grams (each edit destroys the q-grams of at most q consecutive offsets).  If t* >= 1
+// the read is filtered with t* on indexed q-grams alone; otherwise it keeps the full lemma
+// threshold t and is also verified around every cluster of its frequent q-grams.
+__global__ void __launch_bounds__(256)
+    read_qgrams_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ off,
+                  const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk,
+                  const uint64_t* __restrict__ qoff, uint32_t n_reads, uint32_t q,
+                  const uint32_t* __restrict__ filter, uint32_t shift, const uint32_t* __restrict__ phi,
+                  uint32_t n_phi, uint32_t* tcode, uint32_t* tpay, uint64_t* fent, uint32_t* fcnt,
+                  uint16_t* thr, uint8_t* lowcx, uint32_t* lowcx_list, uint32_t* n_lowcx) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += warps) {
+        const uint32_t m = len[r], k = kk[r];
+        const uint32_t nq = m >= q ? m - q + 1 : 0;
+        const uint8_t* rd = codes + off[r];
+        const uint64_t qb = qoff[r];
+        uint32_t nf = 0;
+        uint32_t fmask[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) fmask[t] = 0;
+#pragma unroll 1
+        for (uint32_t t = 0; t * 32 < nq; ++t) {
+            const uint32_t i = t * 32 + lane;
+            bool freq = false;
+            uint64_t fe = 0;
+            if (i < nq) {
+                uint32_t g = 0;
+                for (uint32_t x = 0; x < q; ++x) g = (g << 2) | rd[i + x];
+                const uint32_t h = revcomp_code(g, q);
+                const uint32_t c = g < h ? g : h;
+                const uint32_t f = g > h ? 1u : 0u;
+                const int ph = phi_lookup(c, filter, shift, phi, n_phi);
+                if (ph < 0) {
+                    tcode[qb + i] = c;
+                    tpay[qb + i] = (r << 9) | (f << 8) | i;
+                } else {
+                    tcode[qb + i] = kSentinel;
+                    freq = true;
+                    fe = ((uint64_t)ph << 32) | ((uint64_t)(g == h) << 9) | (f << 8) | i;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFull, freq);
+            if (freq) fent[qb + nf + __popc(bal & lanemask_lt())] = fe;
+            nf += __popc(bal);
+            if (t < 8) fmask[t] = bal;
+        }
+        if (lane == 0) {
+            const int32_t tlemma = (int32_t)m + 1 - (int32_t)(q * (k + 1));
+            fcnt[r] = nf;
+            if (nf == 0) {
+                thr[r] = (uint16_t)tlemma;
+                lowcx[r] = 0;
+            } else {
+                // maximum coverage of the non-frequent offsets by k windows of q offsets
+                uint16_t pre[257], f0[257], f1[257];
+                pre[0] = 0;
+                for (uint32_t x = 0; x < nq; ++x)
+                    pre[x + 1] = pre[x] + (((fmask[x >> 5] >> (x & 31)) & 1u) ? 0 : 1);
+                for (uint32_t x = 0; x <= nq; ++x) f0[x] = 0;
+                uint16_t* prev = f0;
+                uint16_t* cur = f1;
+                for (uint32_t j = 1; j <= k; ++j) {
+                    cur[nq] = 0;
+                    for (int x = (int)nq - 1; x >= 0; --x) {
+                        const uint32_t e = (uint32_t)x + q < nq ? (uint32_t)x + q : nq;
+                        const uint16_t v = (uint16_t)(pre[e] - pre[x] + prev[e]);
+                        cur[x] = v > cur[x + 1] ? v : cur[x + 1];
+                    }
+                    uint16_t* tt = prev;
+                    prev = cur;
+                    cur = tt;
+                }
+                const int32_t tstar = (int32_t)pre[nq] - (int32_t)prev[0];
+                if (tstar >= 1) {
+                    thr[r] = (uint16_t)tstar;
+                    lowcx[r] = 0;
+                } else {
+                    thr[r] = (uint16_t)tlemma;
+                    lowcx[r] = 1;
+                    lowcx_list[atomicAdd(n_lowcx, 1u)] = r;
+                }
+            }
+        }
+    }
+}
+
+__global__ void set_bits_k(const uint32_t* __restrict__ tcode, uint64_t n, uint2* IS) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = tcode[x];
+        if (c != kSentinel) atomicOr(&IS[c >> 5].x, 1u << (c & 31));
+    }
+}
+
+struct PopcIn {
+    const uint2* IS;
+    __device__ __forceinline__ uint64_t operator()(uint64_t i) const { return __popc(IS[i].x); }
+};
+struct SOut {
+    uint2* IS;
+    __device__ __forceinline__ void operator()(uint64_t i, uint64_t v) const { IS[i].y = (uint32_t)v; }
+};
+
+// GROUPBIT + GROUPRANK: the slot of code c in S' (S[i] + popcount(I[i] & (2^j - 1))).
+__device__ __forceinline__ uint32_t qgram_slot(const uint2* __restrict__ IS, uint32_t c) {
+    const uint2 v = IS[c >> 5];
+    return v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
+}
+
+__global__ void count_qgrams_k(const uint32_t* __restrict__ tcode, uint64_t n, const uint2* __restrict__ IS,
+                               uint32_t* cnt) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = tcode[x];
+        if (c != kSentinel) atomicAdd(&cnt[qgram_slot(IS, c)], 1u);
+    }
+}
+
+__global__ void scatter_qgrams_k(const uint32_t* __restrict__ tcode, const uint32_t* __restrict__ tpay,
+                                 uint64_t n, const uint2* __restrict__ IS, const uint32_t* __restrict__ Sp,
+                                 uint32_t* cur, uint32_t* O) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = tcode[x];
+        if (c == kSentinel) continue;
+        const uint32_t slot = qgram_slot(IS, c);
+        O[Sp[slot] + atomicAdd(&cur[slot], 1u)] = tpay[x];
+    }
+}
+
+// Match masks of Myers' algorithm (Section "Validation"): bit i of peq[r][s][c][w] is set when
+// position 64 w + i of the pattern (the read for s = 0, its reverse complement for s = 1) is c.
+__global__ void peq_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ off,
+                      const uint8_t* __restrict__ len, uint32_t n_reads, uint64_t* peq) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_reads) return;
+    const uint32_t m = len[r];
+    const uint8_t* rd = codes + off[r];
+    uint64_t* out = peq + (uint64_t)r * 2 * 4 * kMaxWords;
+    for (int s = 0; s < 2; ++s) {
+        uint64_t w[4][kMaxWords] = {};
+        for (uint32_t i = 0; i < m; ++i) {
+            const uint32_t c = s == 0 ? rd[i] : 3u - rd[m - 1 - i];
+            w[c][i >> 6] |= 1ull << (i & 63);
+        }
+        for (int c = 0; c < 4; ++c)
+            for (int x = 0; x < kMaxWords; ++x) out[(s * 4 + c) * kMaxWords + x] = w[c][x];
+    }
+}
+
+void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
+                 uint32_t k_permille) {
+    init_lut();
+    cudaStream_t s = R->stream;
+    const uint32_t n = R->n_reads, q = R->q;
+    const uint64_t total = R->total_bases;
+    R->base_off.alloc((uint64_t)n + 1, s);
+    PN_CUDA(cudaMemcpyAsync(R->base_off.p, d_offsets, ((uint64_t)n + 1) * sizeof(uint64_t),
+                            cudaMemcpyDeviceToDevice, s));
+    R->len.alloc(n, s);
+    R->kk.alloc(n, s);
+    DBuf<uint64_t> nq(n, s);
+    DBuf<uint32_t> status(3, s);  // [0] status, [1] max len, [2] max k
+    status.zero();
+    read_meta_k<<<grid_for(n, 256), 256, 0, s>>>(R->base_off.p, n, total, q, k_fixed, k_permille, R->len.p,
+                                                  R->kk.p, nq.p, status.p, status.p + 1);
+    PN_CHECK_LAUNCH();
+    R->codes.alloc(total ? total : 1, s);
+    read_codes_k<<<grid_for(total, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+        (const uint8_t*)d_seqs, total, R->codes.p, status.p);
+    PN_CHECK_LAUNCH();
+    uint32_t st[3];
+    PN_CUDA(cudaMemcpyAsync(st, status.p, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    PN_REQUIRE(!(st[0] & kStBadLength), PEANUT_INVALID_ARG,
+               "read offsets must ascend within the sequence buffer and give lengths 1..%d", kMaxReadLen);
+    PN_REQUIRE(!(st[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T");
+    PN_REQUIRE(!(st[0] & kStBadThreshold), PEANUT_INVALID_ARG,
+               "a read violates the q-gram lemma threshold m + 1 - q(k + 1) >= 1 (q = %u)", q);
+    R->max_len = st[1];
+    R->max_k = st[2];
+
+    // q-gram slots per read
+    R->qoff.alloc((uint64_t)n + 1, s);
+    DBuf<uint64_t> tot(1, s);
+    exclusive_scan(ArrayIn<uint64_t>{nq.p}, ArrayOut<uint64_t>{R->qoff.p}, n, tot.p, s);
+    PN_CUDA(cudaMemcpyAsync(R->qoff.p + n, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    const uint64_t nqg = to_host(tot.p, s);
+    R->n_qgrams = nqg;
+    nq.reset();
+
+    const RefPrep* P = R->ref->prep[q];
+    DBuf<uint32_t> tcode(nqg ? nqg : 1, s), tpay(nqg ? nqg : 1, s);
+    R->fent.alloc(nqg ? nqg : 1, s);
+    R->fcnt.alloc(n, s);
+    R->thr.alloc(n, s);
+    R->lowcx.alloc(n, s);
+    R->lowcx_list.alloc(n, s);
+    DBuf<uint32_t> nlc(1, s);
+    nlc.zero();
+    read_qgrams_k<<<grid_for((uint64_t)n * 32, 256, (unsigned)sm_count() * 8), 256, 0, s>>>(
+        R->codes.p, R->base_off.p, R->len.p, R->kk.p, R->qoff.p, n, q, P->filter.p, P->filter_shift,
+        P->phi_codes.p, P->n_phi, tcode.p, tpay.p, R->fent.p, R->fcnt.p, R->thr.p, R->lowcx.p,
+        R->lowcx_list.p, nlc.p);
+    PN_CHECK_LAUNCH();
+
+    // Algorithm 1 over the indexed canonical codes
+    R->n_groups = ((1ull << (2 * q)) + 31) / 32;
+    R->IS.alloc(R->n_groups, s);
+    R->IS.zero();
+    const unsigned gq = grid_for(nqg, 256, (unsigned)sm_count() * 16);
+    set_bits_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->IS.p);
+    PN_CHECK_LAUNCH();
+    DBuf<uint64_t> tot2(1, s);
+    exclusive_scan(PopcIn{R->IS.p}, SOut{R->IS.p}, R->n_groups, tot2.p, s);
+    DBuf<uint32_t> cnt(nqg + 1, s);
+    cnt.zero();
+    count_qgrams_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->IS.p, cnt.p);
+    PN_CHECK_LAUNCH();
+    R->Sp.alloc(nqg + 1, s);
+    exclusive_scan(ArrayIn<uint32_t>{cnt.p}, ArrayOut<uint32_t>{R->Sp.p}, nqg + 1, tot.p, s);
+    cnt.zero();
+    uint64_t sizes[2];
+    PN_CUDA(cudaMemcpyAsync(&sizes[0], tot2.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaMemcpyAsync(&sizes[1], tot.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    R->n_distinct = sizes[0];
+    R->n_indexed = sizes[1];
+    R->O.alloc(R->n_indexed ? R->n_indexed : 1, s);
+    scatter_qgrams_k<<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, R->IS.p, R->Sp.p, cnt.p, R->O.p);
+    PN_CHECK_LAUNCH();
+
+    R->peq.alloc((uint64_t)n * 2 * 4 * kMaxWords, s);
+    peq_k<<<grid_for(n, 128), 128, 0, s>>>(R->codes.p, R->base_off.p, R->len.p, n, R->peq.p);
+    PN_CHECK_LAUNCH();
+    R->n_lowcx = to_host(nlc.p, s);
+}
+
+}  // namespace pn

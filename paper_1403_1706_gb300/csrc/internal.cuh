@@ -1,0 +1,196 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "peanut.h"
+
+namespace pn {
+
+constexpr int kMaxReadLen = 255;
+constexpr int kMaxWords = 4;                 // 64-bit words per bit-vector column (m <= 256)
+constexpr uint32_t kMaxReads = 1u << 23;     // read id fits 23 bits of a hit key
+constexpr uint64_t kMaxRefLen = 1ull << 39;  // biased diagonal fits 40 bits of a hit key
+constexpr int64_t kDiagBias = 256;           // diagonal d >= -254; key stores d + kDiagBias
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // "not indexed" code (no canonical q-gram is all ones)
+constexpr uint32_t kDefaultFreqCap = 256;
+constexpr uint64_t kClusterGap = 64;         // occurrences closer than this share a cluster
+constexpr int kFilterBits = 24;              // frequent-q-gram prefilter: 2^24 bits
+
+constexpr uint32_t kMagicRef = 0x50524546u;    // 'PREF'
+constexpr uint32_t kMagicReads = 0x50524453u;  // 'PRDS'
+constexpr uint32_t kMagicHits = 0x50484954u;   // 'PHIT'
+constexpr uint32_t kMagicDHits = 0x50444854u;  // 'PDHT'
+
+// device status bits (written by kernels, read at synchronization points)
+enum : uint32_t {
+    kStBadBase = 1u,
+    kStBadLength = 2u,
+    kStBadThreshold = 4u,
+    kStOverflow = 8u,
+};
+
+// ---- errors -------------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Fail {
+    peanut_status st;
+};
+
+#define PN_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ::pn::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                            __LINE__);                                                      \
+            throw ::pn::Fail{PEANUT_CUDA_ERROR};                                            \
+        }                                                                                   \
+    } while (0)
+
+#define PN_CHECK_LAUNCH() PN_CUDA(cudaGetLastError())
+
+#define PN_REQUIRE(cond, status, ...)        \
+    do {                                     \
+        if (!(cond)) {                       \
+            ::pn::set_error(__VA_ARGS__);    \
+            throw ::pn::Fail{status};        \
+        }                                    \
+    } while (0)
+
+// ---- device memory ----------------------------------------------------------------------
+void* dalloc(size_t bytes, cudaStream_t s);  // throws Fail{NO_MEMORY}
+void dfree(void* p, cudaStream_t s);
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { reset(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { reset(); }
+    void alloc(size_t count, cudaStream_t st) {
+        reset();
+        s = st;
+        n = count;
+        p = count ? static_cast<T*>(dalloc(count * sizeof(T), st)) : nullptr;
+    }
+    void zero() {
+        if (n) PN_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+    void reset() {
+        if (p) dfree(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    T* release() { T* q = p; p = nullptr; n = 0; return q; }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+template <class T>
+T to_host(const T* d, cudaStream_t s) {
+    T h;
+    PN_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 1u << 30) {
+    uint64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+int sm_count();
+
+// ---- frequent q-grams of a reference (per q) --------------------------------------------
+struct RefPrep {
+    uint32_t q = 0, cap = 0;
+    uint32_t n_phi = 0;          // number of frequent canonical q-grams
+    uint64_t n_clusters = 0;
+    uint64_t n_occ = 0;          // their total occurrences
+    DBuf<uint32_t> phi_codes;    // sorted canonical codes, n_phi
+    DBuf<uint32_t> filter;       // 2^kFilterBits bit prefilter over code >> filter_shift
+    uint32_t filter_shift = 0;
+    DBuf<uint64_t> grp_off;      // 2*n_phi + 1: cluster range of (phi, orientation)
+    DBuf<uint64_t> cl_lo, cl_hi; // first / last occurrence position of each cluster
+};
+
+}  // namespace pn
+
+struct peanut_ref {
+    uint32_t magic = pn::kMagicRef;
+    uint64_t n = 0;             // bases
+    uint64_t n_words = 0;       // packed 32-bit words (16 bases each), plus padding
+    pn::DBuf<uint32_t> packed;  // base p at bits 30 - 2 (p % 16) of word p / 16
+    cudaStream_t stream = nullptr;
+    pn::RefPrep* prep[17] = {};
+};
+
+struct peanut_reads {
+    uint32_t magic = pn::kMagicReads;
+    const peanut_ref* ref = nullptr;
+    cudaStream_t stream = nullptr;
+    uint32_t q = 0, n_reads = 0, max_len = 0, max_k = 0, freq_cap = 0;
+    uint64_t total_bases = 0;
+    // per read
+    pn::DBuf<uint64_t> base_off;  // n+1 offsets into codes
+    pn::DBuf<uint8_t> codes;      // 2-bit codes, one per byte
+    pn::DBuf<uint8_t> len;        // read length (1..255)
+    pn::DBuf<uint8_t> kk;         // error budget
+    pn::DBuf<uint16_t> thr;       // q-gram count threshold used by the filter
+    pn::DBuf<uint8_t> lowcx;      // 1 = verified around frequent-q-gram clusters
+    pn::DBuf<uint64_t> peq;       // [n][2 strands][4 bases][kMaxWords] match bit masks
+    // q-group index
+    uint64_t n_groups = 0, n_distinct = 0, n_indexed = 0, n_qgrams = 0;
+    pn::DBuf<uint2> IS;           // (I word, S) per group of 32 canonical codes
+    pn::DBuf<uint32_t> Sp;        // n_qgrams + 1 (first n_distinct + 1 meaningful)
+    pn::DBuf<uint32_t> O;         // n_indexed entries (read << 9 | orientation << 8 | offset)
+    // frequent q-grams of each read (only meaningful for reads with fcnt > 0)
+    pn::DBuf<uint64_t> qoff;      // n+1: q-gram slot offsets
+    pn::DBuf<uint32_t> fcnt;      // frequent q-grams per read
+    pn::DBuf<uint64_t> fent;      // phi << 32 | palindrome << 9 | orientation << 8 | offset
+    pn::DBuf<uint32_t> lowcx_list;
+    uint32_t n_lowcx = 0;
+    // results of the last map call kept for introspection
+    pn::DBuf<uint64_t> cand_key;  // lo (40 bits) | strand << 40 | read << 41
+    pn::DBuf<uint64_t> cand_hi;
+    uint64_t n_cand = 0;
+    peanut_map_stats stats = {};
+};
+
+struct HostHits {
+    uint32_t magic = pn::kMagicHits;
+    peanut_hits h = {};
+};
+
+struct DeviceHits {
+    uint32_t magic = pn::kMagicDHits;
+    peanut_device_hits h = {};
+    cudaStream_t stream = nullptr;
+};
+
+namespace pn {
+// index.cu
+void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s);
+RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s);
+void free_prep(RefPrep* p);
+void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
+                 uint32_t k_permille);
+// map.cu
+DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode);
+void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
+                       const uint64_t* txt_off, int32_t* out, cudaStream_t s);
+}  // namespace pn

@@ -1,0 +1,1012 @@
+// Mapping a read batch: reference scan (Algorithm 2), candidate windows, bit-vector verification
+// (Section "Validation") and the per-read stratum reduction (Section "Postprocessing").
+//
+// Hit key layout (64 bits): read << 41 | strand << 40 | (diagonal + kDiagBias).
+// The diagonal of a hit is the putative read start d = p - i (Section "Filtration"); for the
+// reverse-complement strand the offset i is taken in the reverse-complemented read.
+//
+// Candidate windows (the q-gram lemma, Section "The q-group index"): an alignment with e <= k
+// edits keeps at least t of the read's q-grams intact, all on diagonals spanning at most e + 1
+// values; with d0 the smallest of them, the alignment ends in [d0 + m - 1 - k, d0 + m - 1 + k].
+// So it suffices to verify, for every window of k + 1 consecutive diagonals holding at least t
+// hits, the end range [d0 + m - 1 - k, d0 + m - 1 + k]; with sorted hit diagonals d_x this is
+// the union over x with d_{x+t-1} - d_x <= k of [d_{x+t-1} + m - 1 - 2k, d_x + m - 1 + k].
+// Overlapping or touching ranges are merged so every maximal run of end positions lies in one.
+#include <cstdio>
+
+#include "prims.cuh"
+
+namespace pn {
+
+constexpr int kScanBlock = 256;
+constexpr int kStageCap = 256;  // staged hits per warp before one global append
+constexpr int kWinWarps = 4;
+constexpr int kWinCap = 1024;   // hits per read sorted in shared memory by one warp
+constexpr uint64_t kKeyMask41 = (1ull << 41) - 1;
+constexpr uint64_t kPosMask40 = (1ull << 40) - 1;
+
+// ---- reference scan ------------------------------------------------------------------------
+
+__device__ __forceinline__ void stage_flush(uint64_t* st, uint32_t cnt, uint64_t* hits, uint64_t cap,
+                                            unsigned long long* n_hits) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0 && cnt) base = atomicAdd(n_hits, (unsigned long long)cnt);
+    base = __shfl_sync(kFull, base, 0);
+    for (uint32_t j = threadIdx.x & 31; j < cnt; j += 32)
+        if (base + j < cap) hits[base + j] = st[j];
+    __syncwarp();
+}
+
+// One pass over reference positions p in [0, n - q].  Each lane handles 32 consecutive positions
+// of a chunk; the canonical code of each position is probed in the read index and every
+// occurrence becomes a hit key.  Hits are staged per warp in shared memory and appended to the
+// global buffer with one atomic per stage; rcount[r] counts each read's hits.
+__global__ void __launch_bounds__(kScanBlock)
+    scan_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
+               const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O,
+               const uint8_t* __restrict__ len, uint64_t* __restrict__ hits, uint64_t cap,
+               unsigned long long* n_hits, uint32_t* __restrict__ rcount) {
+    __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t* st = stage[wid];
+    uint32_t scnt = 0;
+    const uint64_t npos = n >= q ? n - q + 1 : 0;
+    const uint64_t nchunks = (npos + 31) / 32;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t qm = q == 16 ? 0xFFFFFFFFu : (1u << (2 * q)) - 1u;
+    for (uint64_t ch0 = gwarp * 32; ch0 < nchunks; ch0 += nwarps * 32) {
+        const uint64_t ch = ch0 + lane;
+        const bool active = ch < nchunks;
+        const uint64_t p0 = ch * 32;
+        uint32_t w0 = 0, w1 = 0, w2 = 0;
+        if (active) {
+            w0 = __ldg(packed + p0 / 16);
+            w1 = __ldg(packed + p0 / 16 + 1);
+            w2 = __ldg(packed + p0 / 16 + 2);
+        }
+#pragma unroll 1
+        for (int o0 = 0; o0 < 32; o0 += 8) {
+            uint32_t cc[8];
+            uint2 vv[8];
+            uint32_t meta[8];  // bit 0: valid, bit 1: f_ref, bit 2: palindrome
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int o = o0 + u;
+                const uint64_t win = o < 16 ? (((uint64_t)w0 << 32) | w1) : (((uint64_t)w1 << 32) | w2);
+                const uint32_t g = (uint32_t)(win >> (64 - 2 * q - 2 * (o & 15))) & qm;
+                const uint32_t h = revcomp_code(g, q);
+                const uint32_t c = g < h ? g : h;
+                const bool valid = active && p0 + o < npos;
+                cc[u] = c;
+                meta[u] = (valid ? 1u : 0u) | (g > h ? 2u : 0u) | (g == h ? 4u : 0u);
+                vv[u] = valid ? __ldg(IS + (c >> 5)) : make_uint2(0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t c = cc[u];
+                const uint2 v = vv[u];
+                uint32_t kb = 0, ke = 0;
+                if ((v.x >> (c & 31)) & 1u) {
+                    const uint32_t slot = v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
+                    kb = __ldg(Sp + slot);
+                    ke = __ldg(Sp + slot + 1);
+                }
+                const int64_t p = (int64_t)(p0 + o0 + u);
+                const uint32_t fref = (meta[u] >> 1) & 1u;
+                const bool pal = (meta[u] >> 2) & 1u;
+                while (true) {
+                    const bool has = kb < ke;
+                    if (!__any_sync(kFull, has)) break;
+                    uint64_t key0 = 0, key1 = 0;
+                    int nk = 0;
+                    if (has) {
+                        const uint32_t e = __ldg(O + kb);
+                        ++kb;
+                        const uint32_t r = e >> 9, fr = (e >> 8) & 1u, i = e & 255u;
+                        const int64_t m = __ldg(len + r);
+                        const int64_t dp = p - (int64_t)i + kDiagBias;
+                        const int64_t dm = p - (m - (int64_t)q - (int64_t)i) + kDiagBias;
+                        const uint64_t rk = (uint64_t)r << 41;
+                        if (pal) {
+                            key0 = rk | (uint64_t)dp;
+                            key1 = rk | (1ull << 40) | (uint64_t)dm;
+                            nk = 2;
+                        } else if (fr == fref) {
+                            key0 = rk | (uint64_t)dp;
+                            nk = 1;
+                        } else {
+                            key0 = rk | (1ull << 40) | (uint64_t)dm;
+                            nk = 1;
+                        }
+                        atomicAdd(rcount + r, (uint32_t)nk);
+                    }
+                    const unsigned b1 = __ballot_sync(kFull, nk >= 1), b2 = __ballot_sync(kFull, nk == 2);
+                    const uint32_t tot = __popc(b1) + __popc(b2);
+                    if (scnt + tot > kStageCap) {
+                        stage_flush(st, scnt, hits, cap, n_hits);
+                        scnt = 0;
+                    }
+                    const uint32_t pos = scnt + __popc(b1 & lanemask_lt()) + __popc(b2 & lanemask_lt());
+                    if (nk >= 1) st[pos] = key0;
+                    if (nk == 2) st[pos + 1] = key1;
+                    scnt += tot;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    stage_flush(st, scnt, hits, cap, n_hits);
+}
+
+// ---- binning hits by read ---------------------------------------------------------------
+
+__global__ void bin_hits_k(const uint64_t* __restrict__ hits, uint64_t nh, const uint64_t* __restrict__ roff,
+                           uint32_t* cur, uint64_t* __restrict__ binned) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nh;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = hits[x];
+        const uint32_t r = (uint32_t)(key >> 41);
+        binned[roff[r] + atomicAdd(cur + r, 1u)] = key & kKeyMask41;
+    }
+}
+
+// ---- windows ----------------------------------------------------------------------------
+
+struct WinParams {
+    const uint64_t* roff;
+    const uint8_t* len;
+    const uint8_t* kk;
+    const uint16_t* thr;
+    uint64_t n;           // reference length
+    uint64_t* wlo;        // interval lo | strand << 40, at roff[r] + x
+    uint64_t* whi;
+    uint32_t* wcnt;       // [2 * r + s]
+};
+
+__device__ __forceinline__ int64_t key_diag(uint64_t key) {
+    return (int64_t)(key & kPosMask40) - kDiagBias;
+}
+
+// Lane 0 accumulates merged end ranges of one (read, strand) in increasing order.
+struct RangeMerger {
+    int64_t lo = 0, hi = -1;
+    bool open = false;
+    uint32_t cnt = 0;
+    __device__ __forceinline__ void flush(uint64_t* wlo, uint64_t* whi, uint64_t base, uint32_t s, uint64_t n) {
+        if (!open) return;
+        const int64_t a = lo < 0 ? 0 : lo;
+        const int64_t b = hi > (int64_t)n - 1 ? (int64_t)n - 1 : hi;
+        if (a <= b) {
+            wlo[base + cnt] = (uint64_t)a | ((uint64_t)s << 40);
+            whi[base + cnt] = (uint64_t)b;
+            ++cnt;
+        }
+        open = false;
+    }
+    __device__ __forceinline__ void add(int64_t l, int64_t h, uint64_t* wlo, uint64_t* whi, uint64_t base,
+                                        uint32_t s, uint64_t n) {
+        if (open && l <= hi + 1) {
+            if (h > hi) hi = h;
+            return;
+        }
+        flush(wlo, whi, base, s, n);
+        lo = l;
+        hi = h;
+        open = true;
+    }
+};
+
+// Sweep of one read's sorted hit keys (both strands) by one warp; writes the merged end ranges.
+__device__ void window_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const WinParams& P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = P.len[r], k = P.kk[r];
+    const uint32_t T = P.thr[r];
+    const uint64_t base = P.roff[r];
+    // number of strand-0 keys
+    uint32_t h0 = 0;
+    for (uint32_t x = lane; x < h; x += 32) h0 += (keys[x] & kKeyMask41) < (1ull << 40) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h0 += __shfl_xor_sync(kFull, h0, o);
+    uint32_t total = 0;
+    for (uint32_t s = 0; s < 2; ++s) {
+        const uint32_t b = s == 0 ? 0 : h0, e = s == 0 ? h0 : h;
+        RangeMerger mg;
+        mg.cnt = total;
+        for (uint32_t j0 = b; j0 + T - 1 < e; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool valid = false;
+            if (j + T - 1 < e) valid = key_diag(keys[j + T - 1]) - key_diag(keys[j]) <= k;
+            unsigned bal = __ballot_sync(kFull, valid);
+            if (lane == 0) {
+                while (bal) {
+                    const int bit = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const uint32_t jj = j0 + bit;
+                    const int64_t lo = key_diag(keys[jj + T - 1]) + m - 1 - 2 * k;
+                    const int64_t hi = key_diag(keys[jj]) + m - 1 + k;
+                    mg.add(lo, hi, P.wlo, P.whi, base, s, P.n);
+                }
+            }
+        }
+        if (lane == 0) {
+            mg.flush(P.wlo, P.whi, base, s, P.n);
+            P.wcnt[2 * r + s] = mg.cnt - total;
+        }
+        total = __shfl_sync(kFull, mg.cnt, 0);
+    }
+}
+
+// One warp per read: sort its hits in shared memory (bitonic), then sweep.  Reads with more
+// than kWinCap hits are deferred to the global-memory path.
+__global__ void __launch_bounds__(kWinWarps * 32)
+    windows_k(const uint64_t* __restrict__ binned, uint32_t n_reads, WinParams P, uint32_t* big_list,
+              uint32_t* n_big) {
+    __shared__ uint64_t sk[kWinWarps][kWinCap];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t* s = sk[wid];
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += nw) {
+        const uint64_t b = P.roff[r];
+        const uint32_t h = (uint32_t)(P.roff[r + 1] - b);
+        if (h < P.thr[r]) {
+            if (lane == 0) P.wcnt[2 * r] = P.wcnt[2 * r + 1] = 0;
+            continue;
+        }
+        if (h > (uint32_t)kWinCap) {
+            if (lane == 0) big_list[atomicAdd(n_big, 1u)] = r;
+            continue;
+        }
+        uint32_t np = 32;
+        while (np < h) np <<= 1;
+        for (uint32_t x = lane; x < np; x += 32) s[x] = x < h ? binned[b + x] : ~0ull;
+        __syncwarp();
+        for (uint32_t size = 2; size <= np; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t t = lane; t < np / 2; t += 32) {
+                    const uint32_t i = 2 * stride * (t / stride) + (t % stride);
+                    const uint32_t j = i + stride;
+                    const bool up = (i & size) == 0;
+                    const uint64_t a = s[i], c = s[j];
+                    if ((a > c) == up) {
+                        s[i] = c;
+                        s[j] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        window_sweep(s, h, r, P);
+        __syncwarp();
+    }
+}
+
+// Deferred reads: their hits, tagged with the list index, sorted globally; one warp each.
+__global__ void big_gather_k(const uint64_t* __restrict__ binned, const uint32_t* big_list, uint32_t n_big,
+                             const uint64_t* roff, const uint64_t* goff, uint64_t* out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n_big; x += nw) {
+        const uint32_t r = big_list[x];
+        const uint64_t b = roff[r], h = roff[r + 1] - b;
+        for (uint64_t j = lane; j < h; j += 32) out[goff[x] + j] = ((uint64_t)x << 41) | binned[b + j];
+    }
+}
+
+struct BigSize {
+    const uint32_t* list;
+    const uint64_t* roff;
+    __device__ uint64_t operator()(uint64_t x) const { return roff[list[x] + 1] - roff[list[x]]; }
+};
+
+__global__ void big_sweep_k(const uint64_t* sorted, const uint32_t* big_list, uint32_t n_big,
+                            const uint64_t* goff, WinParams P) {
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n_big; x += nw) {
+        const uint32_t r = big_list[x];
+        window_sweep(sorted + goff[x], (uint32_t)(goff[x + 1] - goff[x]), r, P);
+    }
+}
+
+// ---- reads verified around frequent-q-gram clusters -------------------------------------
+
+struct LcParams {
+    const uint32_t* list;   // lowcx reads
+    uint32_t n_list;
+    const uint64_t* qoff;
+    const uint32_t* fcnt;
+    uint64_t* fent;         // sorted in place per read by lc_sort_k
+    const uint8_t* len;
+    const uint8_t* kk;
+    uint32_t q;
+    uint64_t n;
+    const uint64_t* grp_off;
+    const uint64_t* cl_lo;
+    const uint64_t* cl_hi;
+    const uint64_t* roff;   // W_n ranges of the read at roff[r]
+    const uint64_t* wlo;
+    const uint64_t* whi;
+    const uint32_t* wcnt;
+};
+
+// Sort each listed read's frequent entries by (phi, orientation, offset) (insertion sort; <= 252).
+__global__ void lc_sort_k(LcParams L) {
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n_list) return;
+    const uint32_t r = L.list[x];
+    uint64_t* a = L.fent + L.qoff[r];
+    const uint32_t n = L.fcnt[r];
+    for (uint32_t i = 1; i < n; ++i) {
+        const uint64_t v = a[i];
+        int j = (int)i - 1;
+        while (j >= 0 && a[j] > v) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = v;
+    }
+}
+
+// Visits, for (read r, strand s), every list of clusters to verify: the clusters of (phi, f_ref)
+// with the smallest and largest offset i' of the read's q-grams on that strand.  For strand 0 a
+// read q-gram of orientation f meets reference occurrences of orientation f at diagonal p - i;
+// for strand 1 those of orientation 1 - f at diagonal p - (m - q - i).  A palindromic q-gram
+// meets its (single-orientation) occurrences on both strands.
+template <class F>
+__device__ void lc_lists(const LcParams& L, uint32_t r, uint32_t s, F&& visit) {
+    const uint64_t* a = L.fent + L.qoff[r];
+    const uint32_t n = L.fcnt[r];
+    const int64_t m = L.len[r], q = L.q;
+    uint32_t x = 0;
+    while (x < n) {
+        const uint32_t phi = (uint32_t)(a[x] >> 32);
+        int64_t mn[2] = {INT64_MAX, INT64_MAX}, mx[2] = {INT64_MIN, INT64_MIN};
+        while (x < n && (uint32_t)(a[x] >> 32) == phi) {
+            const uint32_t f = (a[x] >> 8) & 1u, pal = (a[x] >> 9) & 1u, i = a[x] & 255u;
+            const uint32_t fref = pal ? 0u : (s == 0 ? f : 1u - f);
+            const int64_t ip = s == 0 ? (int64_t)i : m - q - (int64_t)i;
+            if (ip < mn[fref]) mn[fref] = ip;
+            if (ip > mx[fref]) mx[fref] = ip;
+            ++x;
+        }
+        for (uint32_t fr = 0; fr < 2; ++fr)
+            if (mn[fr] != INT64_MAX) visit(L.grp_off[2 * phi + fr], L.grp_off[2 * phi + fr + 1], mn[fr], mx[fr]);
+    }
+}
+
+__device__ __forceinline__ bool span_of(const LcParams& L, uint64_t c, int64_t imin, int64_t imax, int64_t m,
+                                        int64_t k, int64_t* lo, int64_t* hi) {
+    const int64_t n = (int64_t)L.n;
+    int64_t a = (int64_t)L.cl_lo[c] - imax + m - 1 - 2 * k;
+    int64_t b = (int64_t)L.cl_hi[c] - imin + m - 1 + k;
+    if (a < 0) a = 0;
+    if (b > n - 1) b = n - 1;
+    *lo = a;
+    *hi = b;
+    return a <= b;
+}
+
+// Exact number of (clipped, non-empty) ranges of segment y = 2 * list index + strand.
+__global__ void lc_count_k(LcParams L, uint64_t* cnt) {
+    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= 2 * L.n_list) return;
+    const uint32_t r = L.list[y >> 1], s = y & 1;
+    const int64_t m = L.len[r], k = L.kk[r];
+    uint64_t c = L.wcnt[2 * r + s];
+    lc_lists(L, r, s, [&](uint64_t cb, uint64_t ce, int64_t imin, int64_t imax) {
+        for (uint64_t x = cb; x < ce; ++x) {
+            int64_t lo, hi;
+            c += span_of(L, x, imin, imax, m, k, &lo, &hi) ? 1 : 0;
+        }
+    });
+    cnt[y] = c;
+}
+
+// Writes (segment << 40 | lo, hi) for every range of segment y = 2 * list index + strand.
+__global__ void lc_fill_k(LcParams L, const uint64_t* off, uint64_t* keys, uint64_t* vals) {
+    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= 2 * L.n_list) return;
+    const uint32_t r = L.list[y >> 1], s = y & 1;
+    const int64_t m = L.len[r], k = L.kk[r];
+    uint64_t o = off[y];
+    const uint64_t seg = (uint64_t)y << 40;
+    // the W_n ranges of this strand (already clipped)
+    const uint64_t wb = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
+    for (uint32_t x = 0; x < L.wcnt[2 * r + s]; ++x) {
+        keys[o] = seg | (L.wlo[wb + x] & kPosMask40);
+        vals[o] = L.whi[wb + x];
+        ++o;
+    }
+    lc_lists(L, r, s, [&](uint64_t cb, uint64_t ce, int64_t imin, int64_t imax) {
+        for (uint64_t c = cb; c < ce; ++c) {
+            int64_t lo, hi;
+            if (!span_of(L, c, imin, imax, m, k, &lo, &hi)) continue;
+            keys[o] = seg | (uint64_t)lo;
+            vals[o] = (uint64_t)hi;
+            ++o;
+        }
+    });
+}
+
+// Merges each segment's sorted ranges in place; lcnt[y] = merged count.
+__global__ void lc_merge_k(uint32_t nseg, const uint64_t* off, uint64_t* keys, uint64_t* vals, uint32_t* lcnt) {
+    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= nseg) return;
+    const uint64_t b = off[y], e = off[y + 1];
+    uint32_t c = 0;
+    int64_t lo = 0, hi = -2;
+    bool open = false;
+    for (uint64_t x = b; x < e; ++x) {
+        const int64_t l = (int64_t)(keys[x] & kPosMask40), h = (int64_t)vals[x];
+        if (open && l <= hi + 1) {
+            if (h > hi) hi = h;
+            continue;
+        }
+        if (open) {
+            keys[b + c] = (uint64_t)lo;
+            vals[b + c] = (uint64_t)hi;
+            ++c;
+        }
+        lo = l;
+        hi = h;
+        open = true;
+    }
+    if (open) {
+        keys[b + c] = (uint64_t)lo;
+        vals[b + c] = (uint64_t)hi;
+        ++c;
+    }
+    lcnt[y] = c;
+}
+
+// ---- candidate compaction ---------------------------------------------------------------
+
+struct CandCount {
+    const uint32_t* wcnt;
+    const uint8_t* lowcx;
+    const uint32_t* lcpos;
+    const uint32_t* lcnt;
+    __device__ uint64_t operator()(uint64_t r) const {
+        if (lowcx && lowcx[r]) {
+            const uint32_t x = lcpos[r];
+            return (uint64_t)lcnt[2 * x] + lcnt[2 * x + 1];
+        }
+        return (uint64_t)wcnt[2 * r] + wcnt[2 * r + 1];
+    }
+};
+
+__global__ void lcpos_k(const uint32_t* list, uint32_t n, uint32_t* lcpos) {
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n) lcpos[list[x]] = x;
+}
+
+// One warp per read copies its ranges (strand 0 first) into the candidate arrays.
+__global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, const uint64_t* roff,
+                          const uint64_t* wlo, const uint64_t* whi, const uint64_t* lc_off,
+                          const uint64_t* lc_keys, const uint64_t* lc_vals, uint64_t* cand_key,
+                          uint64_t* cand_hi) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += nw) {
+        const uint64_t o = coff[r];
+        const uint64_t rk = (uint64_t)r << 41;
+        if (cc.lowcx && cc.lowcx[r]) {
+            const uint32_t x = cc.lcpos[r];
+            const uint32_t c0 = cc.lcnt[2 * x], c1 = cc.lcnt[2 * x + 1];
+            for (uint32_t j = lane; j < c0 + c1; j += 32) {
+                const uint32_t s = j < c0 ? 0 : 1;
+                const uint64_t src = lc_off[2 * x + s] + (s ? j - c0 : j);
+                cand_key[o + j] = rk | ((uint64_t)s << 40) | lc_keys[src];
+                cand_hi[o + j] = lc_vals[src];
+            }
+        } else {
+            const uint32_t c = cc.wcnt[2 * r] + cc.wcnt[2 * r + 1];
+            for (uint32_t j = lane; j < c; j += 32) {
+                cand_key[o + j] = rk | wlo[roff[r] + j];
+                cand_hi[o + j] = whi[roff[r] + j];
+            }
+        }
+    }
+}
+
+// ---- bit-vector verification (Myers 1999, block form; Section "Validation") ----------------
+//
+// Column j of the semiglobal matrix is held as vertical delta vectors Pv (+1) and Mv (-1), one
+// bit per pattern row, in W 64-bit words.  Rows enter from word 0; the horizontal delta leaving
+// the top row of one word enters the bottom row of the next.  Row 0 has E[0][j] = 0 for every j,
+// so the delta entering word 0 is 0.  Initial column (j = a - 1): E[i][a-1] = i, all Pv set.
+
+template <int W>
+struct Myers {
+    uint64_t Pv[W], Mv[W];
+    uint64_t eq[4][W];
+    int32_t score;
+    int lastbit;
+
+    __device__ __forceinline__ void init(const uint64_t* __restrict__ peq, uint32_t m) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int w = 0; w < W; ++w) eq[c][w] = __ldg(peq + c * kMaxWords + w);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            Pv[w] = ~0ull;
+            Mv[w] = 0;
+        }
+        score = (int32_t)m;
+        lastbit = (int)((m - 1) & 63);
+    }
+
+    // Advances one text column with base code c; returns E[m][j].
+    __device__ __forceinline__ int32_t step(uint32_t c) {
+        int hin = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t e = c == 0 ? eq[0][w] : c == 1 ? eq[1][w] : c == 2 ? eq[2][w] : eq[3][w];
+            const uint64_t pv = Pv[w], mv = Mv[w];
+            const uint64_t xv = e | mv;
+            if (hin < 0) e |= 1ull;
+            const uint64_t xh = (((e & pv) + pv) ^ pv) | e;
+            uint64_t ph = mv | ~(xh | pv);
+            uint64_t mh = pv & xh;
+            int hout;
+            if (w == W - 1) {
+                hout = (int)((ph >> lastbit) & 1ull) - (int)((mh >> lastbit) & 1ull);
+            } else {
+                hout = (int)(ph >> 63) - (int)(mh >> 63);
+            }
+            ph <<= 1;
+            mh <<= 1;
+            if (hin < 0) mh |= 1ull;
+            else if (hin > 0) ph |= 1ull;
+            Pv[w] = mh | ~(xv | ph);
+            Mv[w] = ph & xv;
+            hin = hout;
+        }
+        score += hin;
+        return score;
+    }
+};
+
+struct VerifyParams {
+    const uint64_t* cand_key;
+    const uint64_t* cand_hi;
+    uint64_t n_cand;
+    const uint32_t* packed;
+    const uint8_t* len;
+    const uint8_t* kk;
+    const uint64_t* peq;
+    uint32_t* cnt;          // tuples per candidate
+    uint64_t* inl;          // 2 inline tuples per candidate: end << 8 | dist
+    unsigned long long* columns;
+    // phase 2
+    const uint64_t* toff;
+    uint32_t* out_read;
+    uint8_t* out_strand;
+    uint64_t* out_end;
+    uint8_t* out_dist;
+};
+
+template <int W, bool kWrite>
+__device__ void verify_one(const VerifyParams& V, uint64_t x) {
+    const uint64_t key = V.cand_key[x];
+    const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
+    const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)V.cand_hi[x];
+    const uint32_t m = V.len[r];
+    const int32_t k = V.kk[r];
+    int64_t a = lo - ((int64_t)m + k) + 1;
+    if (a < 0) a = 0;
+    Myers<W> M;
+    M.init(V.peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords, m);
+    uint32_t word = __ldg(V.packed + (a >> 4));
+    uint32_t nt = 0;
+    uint64_t o = kWrite ? V.toff[x] : 0;
+    bool in = false;
+    int32_t best = 0;
+    int64_t bestj = 0;
+    for (int64_t j = a; j <= hi; ++j) {
+        if ((j & 15) == 0) word = __ldg(V.packed + (j >> 4));
+        const uint32_t c = (word >> (30 - 2 * (uint32_t)(j & 15))) & 3u;
+        const int32_t d = M.step(c);
+        if (j < lo) continue;
+        if (d <= k) {
+            if (!in || d < best) {
+                best = d;
+                bestj = j;
+            }
+            in = true;
+        }
+        if (in && (d > k || j == hi)) {
+            if (kWrite) {
+                V.out_read[o] = r;
+                V.out_strand[o] = (uint8_t)s;
+                V.out_end[o] = (uint64_t)bestj;
+                V.out_dist[o] = (uint8_t)best;
+                ++o;
+            } else if (nt < 2) {
+                V.inl[2 * x + nt] = ((uint64_t)bestj << 8) | (uint64_t)best;
+            }
+            ++nt;
+            in = false;
+        }
+    }
+    if (!kWrite) {
+        V.cnt[x] = nt;
+        atomicAdd(V.columns, (unsigned long long)(hi - a + 1));
+    }
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(128) verify_k(VerifyParams V) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < V.n_cand;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        if (kWrite && V.cnt[x] <= 2) continue;
+        const uint32_t r = (uint32_t)(V.cand_key[x] >> 41);
+        const uint32_t W = (V.len[r] + 63) >> 6;
+        switch (W) {
+            case 1: verify_one<1, kWrite>(V, x); break;
+            case 2: verify_one<2, kWrite>(V, x); break;
+            case 3: verify_one<3, kWrite>(V, x); break;
+            default: verify_one<4, kWrite>(V, x); break;
+        }
+    }
+}
+
+__global__ void inline_out_k(VerifyParams V) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < V.n_cand;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = V.cnt[x];
+        if (c == 0 || c > 2) continue;
+        const uint64_t key = V.cand_key[x];
+        const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
+        const uint64_t o = V.toff[x];
+        for (uint32_t t = 0; t < c; ++t) {
+            const uint64_t v = V.inl[2 * x + t];
+            V.out_read[o + t] = r;
+            V.out_strand[o + t] = (uint8_t)s;
+            V.out_end[o + t] = v >> 8;
+            V.out_dist[o + t] = (uint8_t)(v & 255u);
+        }
+    }
+}
+
+// ---- best stratum ------------------------------------------------------------------------
+
+__global__ void min_dist_k(const uint32_t* rd, const uint8_t* dist, uint64_t n, uint32_t* mind) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x)
+        atomicMin(mind + rd[x], (uint32_t)dist[x]);
+}
+
+struct KeepBest {
+    const uint32_t* rd;
+    const uint8_t* dist;
+    const uint32_t* mind;
+    __device__ uint64_t operator()(uint64_t x) const { return dist[x] == mind[rd[x]] ? 1 : 0; }
+};
+
+__global__ void keep_best_k(KeepBest kb, uint64_t n, const uint64_t* pos, const uint32_t* rd, const uint8_t* st,
+                            const uint64_t* en, const uint8_t* di, uint32_t* ord, uint8_t* ost, uint64_t* oen,
+                            uint8_t* odi) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        if (!kb(x)) continue;
+        const uint64_t o = pos[x];
+        ord[o] = rd[x];
+        ost[o] = st[x];
+        oen[o] = en[x];
+        odi[o] = di[x];
+    }
+}
+
+// ---- driver -------------------------------------------------------------------------------
+
+struct Timer {
+    cudaEvent_t ev[8];
+    int n = 0;
+    cudaStream_t s;
+    explicit Timer(cudaStream_t st) : s(st) {
+        for (auto& e : ev) PN_CUDA(cudaEventCreate(&e));
+    }
+    ~Timer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+    void mark() { PN_CUDA(cudaEventRecord(ev[n++], s)); }
+    float ms(int a, int b) {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
+
+static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s) {
+    H->stream = s;
+    H->h.n = n;
+    const uint64_t c = n ? n : 1;
+    H->h.read_id = static_cast<uint32_t*>(dalloc(c * sizeof(uint32_t), s));
+    H->h.strand = static_cast<uint8_t*>(dalloc(c, s));
+    H->h.end_pos = static_cast<uint64_t*>(dalloc(c * sizeof(uint64_t), s));
+    H->h.dist = static_cast<uint8_t*>(dalloc(c, s));
+}
+
+static void free_hits_arrays(DeviceHits* H) {
+    if (H->h.read_id) dfree(H->h.read_id, H->stream);
+    if (H->h.strand) dfree(H->h.strand, H->stream);
+    if (H->h.end_pos) dfree(H->h.end_pos, H->stream);
+    if (H->h.dist) dfree(H->h.dist, H->stream);
+    H->h = peanut_device_hits{};
+}
+
+DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
+    cudaStream_t s = R->stream;
+    const uint32_t n_reads = R->n_reads, q = R->q;
+    const uint64_t n = ref->n;
+    Timer tm(s);
+    peanut_map_stats st = {};
+    tm.mark();  // 0
+
+    // 1. reference scan
+    DBuf<uint32_t> rcount((uint64_t)n_reads + 1, s);
+    DBuf<unsigned long long> nh(1, s);
+    const double rand_hits = 2.0 * (double)n * (double)R->n_indexed / (double)(1ull << (2 * q));
+    uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
+    DBuf<uint64_t> hits;
+    uint64_t H = 0;
+    const unsigned gscan = (unsigned)sm_count() * 8;
+    for (int attempt = 0;; ++attempt) {
+        hits.alloc(cap, s);
+        rcount.zero();
+        nh.zero();
+        scan_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->Sp.p, R->O.p, R->len.p, hits.p,
+                                                cap, nh.p, rcount.p);
+        PN_CHECK_LAUNCH();
+        H = to_host(nh.p, s);
+        if (H <= cap) break;
+        st.scan_retries++;
+        cap = H + (H >> 4) + 1024;
+        PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "hit buffer kept overflowing");
+    }
+    st.hits = H;
+    tm.mark();  // 1
+
+    // 2. bin by read
+    DBuf<uint64_t> roff((uint64_t)n_reads + 1, s), tot(1, s);
+    exclusive_scan(ArrayIn<uint32_t>{rcount.p}, ArrayOut<uint64_t>{roff.p}, n_reads, tot.p, s);
+    PN_CUDA(cudaMemcpyAsync(roff.p + n_reads, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    DBuf<uint64_t> binned(H ? H : 1, s);
+    rcount.zero();
+    bin_hits_k<<<grid_for(H, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(hits.p, H, roff.p, rcount.p, binned.p);
+    PN_CHECK_LAUNCH();
+    hits.reset();
+    tm.mark();  // 2
+
+    // 3. windows
+    DBuf<uint64_t> wlo(H ? H : 1, s), whi(H ? H : 1, s);
+    DBuf<uint32_t> wcnt(2 * (uint64_t)n_reads, s);
+    DBuf<uint32_t> big_list(n_reads, s), nbig(1, s);
+    nbig.zero();
+    WinParams WP{roff.p, R->len.p, R->kk.p, R->thr.p, n, wlo.p, whi.p, wcnt.p};
+    windows_k<<<grid_for((uint64_t)n_reads * 32, kWinWarps * 32, (unsigned)sm_count() * 16), kWinWarps * 32, 0, s>>>(
+        binned.p, n_reads, WP, big_list.p, nbig.p);
+    PN_CHECK_LAUNCH();
+    const uint32_t n_big = to_host(nbig.p, s);
+    if (n_big) {
+        DBuf<uint64_t> goff((uint64_t)n_big + 1, s);
+        exclusive_scan(BigSize{big_list.p, roff.p}, ArrayOut<uint64_t>{goff.p}, n_big, tot.p, s);
+        PN_CUDA(cudaMemcpyAsync(goff.p + n_big, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        const uint64_t nbk = to_host(tot.p, s);
+        DBuf<uint64_t> bk(nbk, s), btmp(nbk, s);
+        big_gather_k<<<grid_for((uint64_t)n_big * 32, 256), 256, 0, s>>>(binned.p, big_list.p, n_big, roff.p,
+                                                                          goff.p, bk.p);
+        PN_CHECK_LAUNCH();
+        int bits = 0;
+        while ((1ull << bits) < n_big) ++bits;
+        radix_sort_u64(bk.p, btmp.p, nbk, 41 + bits, s);
+        big_sweep_k<<<grid_for((uint64_t)n_big * 32, 256), 256, 0, s>>>(bk.p, big_list.p, n_big, goff.p, WP);
+        PN_CHECK_LAUNCH();
+    }
+    binned.reset();
+
+    // 3b. low-complexity reads: W_n ranges plus a span around every cluster of their frequent
+    // q-grams, sorted per (read, strand) and merged
+    const RefPrep* P = ref->prep[q];
+    const uint32_t nl = R->n_lowcx;
+    DBuf<uint32_t> lcpos, lcnt;
+    DBuf<uint64_t> lc_off, lc_keys, lc_vals;
+    if (nl) {
+        LcParams L{R->lowcx_list.p, nl, R->qoff.p, R->fcnt.p, R->fent.p, R->len.p, R->kk.p, q, n,
+                   P->grp_off.p, P->cl_lo.p, P->cl_hi.p, roff.p, wlo.p, whi.p, wcnt.p};
+        lc_sort_k<<<grid_for(nl, 128), 128, 0, s>>>(L);
+        PN_CHECK_LAUNCH();
+        DBuf<uint64_t> cnt(2 * (uint64_t)nl, s);
+        lc_count_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(L, cnt.p);
+        PN_CHECK_LAUNCH();
+        lc_off.alloc(2 * (uint64_t)nl + 1, s);
+        exclusive_scan(ArrayIn<uint64_t>{cnt.p}, ArrayOut<uint64_t>{lc_off.p}, 2 * (uint64_t)nl, tot.p, s);
+        PN_CUDA(cudaMemcpyAsync(lc_off.p + 2 * (uint64_t)nl, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        const uint64_t nsp = to_host(tot.p, s);
+        lc_keys.alloc(nsp ? nsp : 1, s);
+        lc_vals.alloc(nsp ? nsp : 1, s);
+        lc_fill_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(L, lc_off.p, lc_keys.p, lc_vals.p);
+        PN_CHECK_LAUNCH();
+        if (nsp > 1) {
+            DBuf<uint64_t> tk(nsp, s), tv(nsp, s);
+            int segbits = 0;
+            while ((1ull << segbits) < 2 * (uint64_t)nl) ++segbits;
+            radix_sort_pairs(lc_keys.p, lc_vals.p, tk.p, tv.p, nsp, 40 + segbits, s);
+        }
+        lcnt.alloc(2 * (uint64_t)nl, s);
+        lcpos.alloc(n_reads, s);
+        lcpos_k<<<grid_for(nl, 256), 256, 0, s>>>(R->lowcx_list.p, nl, lcpos.p);
+        PN_CHECK_LAUNCH();
+        lc_merge_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(2 * nl, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p);
+        PN_CHECK_LAUNCH();
+    }
+    st.lowcx_reads = nl;
+
+    // 3c. candidate compaction in (read, strand, lo) order
+    CandCount cc{wcnt.p, nl ? R->lowcx.p : nullptr, lcpos.p, lcnt.p};
+    DBuf<uint64_t> coff((uint64_t)n_reads + 1, s);
+    exclusive_scan(cc, ArrayOut<uint64_t>{coff.p}, n_reads, tot.p, s);
+    const uint64_t NC = to_host(tot.p, s);
+    R->cand_key.alloc(NC ? NC : 1, s);
+    R->cand_hi.alloc(NC ? NC : 1, s);
+    R->n_cand = NC;
+    compact_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+        n_reads, cc, coff.p, roff.p, wlo.p, whi.p, lc_off.p, lc_keys.p, lc_vals.p, R->cand_key.p, R->cand_hi.p);
+    PN_CHECK_LAUNCH();
+    st.candidates = NC;
+    wlo.reset();
+    whi.reset();
+    tm.mark();  // 3
+
+    // 4. verification: count + inline pass, offsets, write pass
+    DBuf<uint32_t> vcnt(NC ? NC : 1, s);
+    DBuf<uint64_t> inl(2 * (NC ? NC : 1), s), toff(NC ? NC : 1, s);
+    DBuf<unsigned long long> cols(1, s);
+    cols.zero();
+    VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
+                   cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
+    const unsigned gv = grid_for(NC, 128, (unsigned)sm_count() * 32);
+    if (NC) {
+        verify_k<false><<<gv, 128, 0, s>>>(V);
+        PN_CHECK_LAUNCH();
+    }
+    exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
+    const uint64_t NT = to_host(tot.p, s);
+    st.candidate_columns = to_host(cols.p, s);
+    DeviceHits* out = new DeviceHits();
+    try {
+        DeviceHits all;
+        alloc_hits(&all, NT, s);
+        V.out_read = all.h.read_id;
+        V.out_strand = all.h.strand;
+        V.out_end = all.h.end_pos;
+        V.out_dist = all.h.dist;
+        if (NC) {
+            inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
+            PN_CHECK_LAUNCH();
+            verify_k<true><<<gv, 128, 0, s>>>(V);
+            PN_CHECK_LAUNCH();
+        }
+        tm.mark();  // 4
+        // 5. best stratum
+        if (mode == 1 && NT) {
+            DBuf<uint32_t> mind(n_reads, s);
+            PN_CUDA(cudaMemsetAsync(mind.p, 0xFF, (uint64_t)n_reads * sizeof(uint32_t), s));
+            min_dist_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(all.h.read_id, all.h.dist, NT,
+                                                                                     mind.p);
+            PN_CHECK_LAUNCH();
+            KeepBest kb{all.h.read_id, all.h.dist, mind.p};
+            DBuf<uint64_t> pos(NT, s);
+            exclusive_scan(kb, ArrayOut<uint64_t>{pos.p}, NT, tot.p, s);
+            const uint64_t NB = to_host(tot.p, s);
+            alloc_hits(out, NB, s);
+            keep_best_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+                kb, NT, pos.p, all.h.read_id, all.h.strand, all.h.end_pos, all.h.dist, out->h.read_id,
+                out->h.strand, out->h.end_pos, out->h.dist);
+            PN_CHECK_LAUNCH();
+            free_hits_arrays(&all);
+        } else {
+            out->stream = s;
+            out->h = all.h;
+            all.h = peanut_device_hits{};
+        }
+        tm.mark();  // 5
+        PN_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        free_hits_arrays(out);
+        delete out;
+        throw;
+    }
+    st.results = out->h.n;
+    st.ms_scan = tm.ms(0, 1);
+    st.ms_bin = tm.ms(1, 2);
+    st.ms_windows = tm.ms(2, 3);
+    st.ms_verify = tm.ms(3, 4);
+    st.ms_output = tm.ms(4, 5);
+    R->stats = st;
+    return out;
+}
+
+void free_device_hits(DeviceHits* H) {
+    free_hits_arrays(H);
+}
+
+// ---- test hook: bit-vector columns of explicit (pattern, text) pairs ------------------------
+
+__global__ void bv_columns_k(const uint8_t* pat, const uint64_t* pat_off, uint32_t n_pat, const uint8_t* txt,
+                             const uint64_t* txt_off, const uint64_t* peq, int32_t* out) {
+    const uint32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n_pat) return;
+    const uint32_t m = (uint32_t)(pat_off[x + 1] - pat_off[x]);
+    const uint32_t W = (m + 63) >> 6;
+    const uint64_t* pq = peq + (uint64_t)x * 2 * 4 * kMaxWords;
+    const uint64_t b = txt_off[x], e = txt_off[x + 1];
+    auto run = [&](auto M) {
+        M.init(pq, m);
+        for (uint64_t j = b; j < e; ++j) out[j] = M.step(txt[j]);
+    };
+    switch (W) {
+        case 1: run(Myers<1>{}); break;
+        case 2: run(Myers<2>{}); break;
+        case 3: run(Myers<3>{}); break;
+        default: run(Myers<4>{}); break;
+    }
+}
+
+__global__ void ascii_codes_k(uint8_t* a, uint64_t n, uint32_t* bad) {
+    const uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint8_t c = a[x];
+    uint8_t v = c == 'A' ? 0 : c == 'C' ? 1 : c == 'G' ? 2 : c == 'T' ? 3 : 255;
+    if (v == 255) {
+        atomicOr(bad, 1u);
+        v = 0;
+    }
+    a[x] = v;
+}
+
+__global__ void pattern_peq_k(const uint8_t* pat, const uint64_t* off, const uint8_t* len, uint32_t n, uint64_t* peq);
+
+void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
+                       const uint64_t* txt_off, int32_t* out, cudaStream_t s) {
+    const uint64_t np = pat_off[n_pat], nt = txt_off[n_pat];
+    for (uint32_t i = 0; i < n_pat; ++i) {
+        const uint64_t m = pat_off[i + 1] - pat_off[i];
+        PN_REQUIRE(m >= 1 && m <= (uint64_t)kMaxReadLen, PEANUT_INVALID_ARG, "pattern length out of range");
+        PN_REQUIRE(txt_off[i + 1] >= txt_off[i], PEANUT_INVALID_ARG, "text offsets must ascend");
+    }
+    DBuf<uint8_t> dp(np ? np : 1, s), dt(nt ? nt : 1, s), lens(n_pat, s);
+    DBuf<uint64_t> dpo((uint64_t)n_pat + 1, s), dto((uint64_t)n_pat + 1, s), peq((uint64_t)n_pat * 2 * 4 * kMaxWords, s);
+    DBuf<int32_t> dout(nt ? nt : 1, s);
+    DBuf<uint32_t> bad(1, s);
+    bad.zero();
+    PN_CUDA(cudaMemcpyAsync(dp.p, pat, np, cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaMemcpyAsync(dt.p, txt, nt, cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaMemcpyAsync(dpo.p, pat_off, ((uint64_t)n_pat + 1) * 8, cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaMemcpyAsync(dto.p, txt_off, ((uint64_t)n_pat + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (np) ascii_codes_k<<<grid_for(np, 256), 256, 0, s>>>(dp.p, np, bad.p);
+    if (nt) ascii_codes_k<<<grid_for(nt, 256), 256, 0, s>>>(dt.p, nt, bad.p);
+    PN_CHECK_LAUNCH();
+    pattern_peq_k<<<grid_for(n_pat, 128), 128, 0, s>>>(dp.p, dpo.p, nullptr, n_pat, peq.p);
+    PN_CHECK_LAUNCH();
+    bv_columns_k<<<grid_for(n_pat, 64), 64, 0, s>>>(dp.p, dpo.p, n_pat, dt.p, dto.p, peq.p, dout.p);
+    PN_CHECK_LAUNCH();
+    PN_REQUIRE(to_host(bad.p, s) == 0, PEANUT_INVALID_ARG, "non-ACGT byte");
+    PN_CUDA(cudaMemcpyAsync(out, dout.p, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+}
+
+__global__ void pattern_peq_k(const uint8_t* pat, const uint64_t* off, const uint8_t*, uint32_t n, uint64_t* peq) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t m = (uint32_t)(off[r + 1] - off[r]);
+    uint64_t w[4][kMaxWords] = {};
+    for (uint32_t i = 0; i < m; ++i) w[pat[off[r] + i]][i >> 6] |= 1ull << (i & 63);
+    for (int c = 0; c < 4; ++c)
+        for (int x = 0; x < kMaxWords; ++x) peq[((uint64_t)r * 2 * 4 + c) * kMaxWords + x] = w[c][x];
+}
+
+}  // namespace pn

@@ -1,0 +1,325 @@
+"""Python binding of libpeanut (include/peanut.h): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name; all mapping work runs in the CUDA
+library.  There is no CPU fallback: if libpeanut.so is missing or no GPU is present, calls raise.
+
+Hit sets come back as numpy structured arrays with fields read (u4), strand (u1), end (i8) and
+dist (i4), sorted by (read, strand, end) -- the layout of peanut_hits widened for comparison.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_char_p, c_float, c_int, c_int32, c_size_t, c_uint8, c_uint16
+from ctypes import c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpeanut.so")
+HIT_DTYPE = np.dtype([("read", "<u4"), ("strand", "u1"), ("end", "<i8"), ("dist", "<i4")])
+MODES = {"all": 0, "best": 1}
+K_FROM_PERMILLE = 0xFFFFFFFF
+
+_lib = None
+
+
+class PeanutError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"peanut status {status}: {msg}")
+        self.status = status
+
+
+class Params(Structure):
+    _fields_ = [("q", c_uint32), ("k_fixed", c_uint32), ("k_permille", c_uint32), ("freq_cap", c_uint32),
+                ("stream", c_void_p)]
+
+
+class Hits(Structure):
+    _fields_ = [("n", c_uint64), ("read_id", POINTER(c_uint32)), ("strand", POINTER(c_uint8)),
+                ("end_pos", POINTER(c_uint64)), ("dist", POINTER(c_uint8))]
+
+
+class DeviceHitsStruct(Structure):
+    _fields_ = [("n", c_uint64), ("read_id", c_void_p), ("strand", c_void_p), ("end_pos", c_void_p),
+                ("dist", c_void_p)]
+
+
+class MapStats(Structure):
+    _fields_ = [("hits", c_uint64), ("candidates", c_uint64), ("candidate_columns", c_uint64),
+                ("results", c_uint64), ("lowcx_reads", c_uint64), ("scan_retries", c_uint64),
+                ("ms_scan", c_float), ("ms_bin", c_float), ("ms_windows", c_float), ("ms_verify", c_float),
+                ("ms_output", c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+def load():
+    """Loads libpeanut.so (built by paper_1403_1706_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_1403_1706_gb300.build.build() first "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    st = c_int
+    sig = {
+        "peanut_last_error": (c_char_p, []),
+        "peanut_set_allocator": (st, [ALLOC_FN, RELEASE_FN, c_void_p]),
+        "peanut_pack_reference": (st, [c_void_p, c_uint64, c_void_p, POINTER(c_void_p)]),
+        "peanut_ref_length": (c_uint64, [c_void_p]),
+        "peanut_index_reads": (st, [c_void_p, c_void_p, c_void_p, c_uint32, POINTER(Params), POINTER(c_void_p)]),
+        "peanut_index_reads_device": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint64, POINTER(Params),
+                                           POINTER(c_void_p)]),
+        "peanut_map": (st, [c_void_p, c_void_p, c_int, POINTER(POINTER(Hits))]),
+        "peanut_map_device": (st, [c_void_p, c_void_p, c_int, POINTER(POINTER(DeviceHitsStruct))]),
+        "peanut_download_hits": (st, [POINTER(DeviceHitsStruct), c_void_p, POINTER(POINTER(Hits))]),
+        "peanut_get_map_stats": (st, [c_void_p, POINTER(MapStats)]),
+        "peanut_free": (None, [c_void_p]),
+        "peanut_index_sizes": (st, [c_void_p, POINTER(c_uint64), POINTER(c_uint64), POINTER(c_uint64)]),
+        "peanut_export_index": (st, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+        "peanut_export_read_params": (st, [c_void_p, c_void_p, c_void_p]),
+        "peanut_export_candidates": (st, [c_void_p, POINTER(c_uint64), c_void_p, c_void_p, c_void_p, c_void_p]),
+        "peanut_debug_bitvector_columns": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
+                                                c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PeanutError(status, load().peanut_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _host_u8(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(x, dtype=np.uint8)
+    return np.ascontiguousarray(x, dtype=np.uint8)
+
+
+# ---- allocator -----------------------------------------------------------------------------
+
+_alloc_keep = None
+
+
+def use_torch_allocator():
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+    import torch
+    global _alloc_keep
+
+    def _alloc(size, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(), stream or 0))
+        except Exception:
+            return None
+
+    def _release(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, r = ALLOC_FN(_alloc), RELEASE_FN(_release)
+    _check(load().peanut_set_allocator(a, r, None))
+    _alloc_keep = (a, r)
+
+
+def use_default_allocator():
+    global _alloc_keep
+    _check(load().peanut_set_allocator(ALLOC_FN(), RELEASE_FN(), None))
+    _alloc_keep = None
+
+
+# ---- objects -------------------------------------------------------------------------------
+
+class _Handle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def free(self):
+        if self.ptr:
+            load().peanut_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Reference(_Handle):
+    @property
+    def length(self) -> int:
+        return int(load().peanut_ref_length(self.ptr))
+
+
+class ReadBatch(_Handle):
+    def __init__(self, ptr, ref: Reference, n_reads: int):
+        super().__init__(ptr)
+        self.ref = ref  # keeps the reference alive while the batch exists
+        self.n_reads = n_reads
+
+
+def pack_reference(seq, stream=None) -> Reference:
+    """peanut_pack_reference: ASCII reference (bytes or uint8 array) -> resident packed reference."""
+    a = _host_u8(seq)
+    out = c_void_p()
+    _check(load().peanut_pack_reference(a.ctypes.data, a.size, _stream_ptr(stream), ctypes.byref(out)))
+    return Reference(out.value)
+
+
+def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None) -> Params:
+    if k is None and k_permille is None:
+        raise ValueError("give k or k_permille")
+    return Params(q, K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(freq_cap),
+                  _stream_ptr(stream))
+
+
+def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
+                stream=None) -> ReadBatch:
+    """peanut_index_reads: host reads (concatenated ASCII + n+1 offsets) -> indexed batch."""
+    s = _host_u8(seq)
+    o = np.ascontiguousarray(offsets, dtype=np.uint64)
+    p = make_params(q, k, k_permille, freq_cap, stream)
+    out = c_void_p()
+    _check(load().peanut_index_reads(ref.ptr, s.ctypes.data, o.ctypes.data, o.size - 1, ctypes.byref(p),
+                                     ctypes.byref(out)))
+    return ReadBatch(out.value, ref, o.size - 1)
+
+
+def index_reads_device(ref: Reference, d_seq, d_offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
+                       stream=None) -> ReadBatch:
+    """peanut_index_reads_device: reads already in device memory (torch uint8 / int64 tensors)."""
+    p = make_params(q, k, k_permille, freq_cap, stream)
+    out = c_void_p()
+    n = int(d_offsets.numel()) - 1
+    _check(load().peanut_index_reads_device(ref.ptr, d_seq.data_ptr(), d_offsets.data_ptr(), n,
+                                            int(d_seq.numel()), ctypes.byref(p), ctypes.byref(out)))
+    return ReadBatch(out.value, ref, n)
+
+
+def _hits_to_numpy(hp) -> np.ndarray:
+    h = hp.contents
+    n = int(h.n)
+    out = np.empty(n, HIT_DTYPE)
+    if n:
+        out["read"] = np.ctypeslib.as_array(h.read_id, (n,))
+        out["strand"] = np.ctypeslib.as_array(h.strand, (n,))
+        out["end"] = np.ctypeslib.as_array(h.end_pos, (n,)).astype(np.int64)
+        out["dist"] = np.ctypeslib.as_array(h.dist, (n,))
+    return out
+
+
+def map(ref: Reference, batch: ReadBatch, mode: str = "all") -> np.ndarray:
+    """peanut_map: the batch's hit set on the host."""
+    hp = POINTER(Hits)()
+    _check(load().peanut_map(ref.ptr, batch.ptr, MODES[mode], ctypes.byref(hp)))
+    try:
+        return _hits_to_numpy(hp)
+    finally:
+        load().peanut_free(ctypes.cast(hp, c_void_p))
+
+
+class DeviceHits(_Handle):
+    """peanut_device_hits: result arrays left in device memory."""
+
+    def __init__(self, hp):
+        super().__init__(ctypes.cast(hp, c_void_p).value)
+        self._hp = hp
+
+    @property
+    def n(self) -> int:
+        return int(self._hp.contents.n)
+
+    def to_numpy(self, stream=None) -> np.ndarray:
+        out = POINTER(Hits)()
+        _check(load().peanut_download_hits(self._hp, _stream_ptr(stream), ctypes.byref(out)))
+        try:
+            return _hits_to_numpy(out)
+        finally:
+            load().peanut_free(ctypes.cast(out, c_void_p))
+
+
+def map_device(ref: Reference, batch: ReadBatch, mode: str = "all") -> DeviceHits:
+    hp = POINTER(DeviceHitsStruct)()
+    _check(load().peanut_map_device(ref.ptr, batch.ptr, MODES[mode], ctypes.byref(hp)))
+    return DeviceHits(hp)
+
+
+def get_map_stats(batch: ReadBatch) -> dict:
+    s = MapStats()
+    _check(load().peanut_get_map_stats(batch.ptr, ctypes.byref(s)))
+    return s.as_dict()
+
+
+# ---- introspection -------------------------------------------------------------------------
+
+def index_sizes(batch: ReadBatch):
+    a, b, c = c_uint64(), c_uint64(), c_uint64()
+    _check(load().peanut_index_sizes(batch.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return int(a.value), int(b.value), int(c.value)
+
+
+def export_index(batch: ReadBatch):
+    """(I, S, Sp, O) of the batch's q-group index as numpy uint32 arrays."""
+    ng, nd, ni = index_sizes(batch)
+    I = np.empty(ng, np.uint32)
+    S = np.empty(ng, np.uint32)
+    Sp = np.empty(nd + 1, np.uint32)
+    O = np.empty(max(ni, 1), np.uint32)
+    _check(load().peanut_export_index(batch.ptr, I.ctypes.data, S.ctypes.data, Sp.ctypes.data, O.ctypes.data))
+    return I, S, Sp, O[:ni]
+
+
+def export_read_params(batch: ReadBatch):
+    thr = np.empty(batch.n_reads, np.uint16)
+    lc = np.empty(batch.n_reads, np.uint8)
+    _check(load().peanut_export_read_params(batch.ptr, thr.ctypes.data, lc.ctypes.data))
+    return thr, lc
+
+
+def export_candidates(batch: ReadBatch):
+    n = c_uint64(0)
+    _check(load().peanut_export_candidates(batch.ptr, ctypes.byref(n), None, None, None, None))
+    k = int(n.value)
+    r = np.empty(max(k, 1), np.uint32)
+    s = np.empty(max(k, 1), np.uint8)
+    lo = np.empty(max(k, 1), np.uint64)
+    hi = np.empty(max(k, 1), np.uint64)
+    if k:
+        _check(load().peanut_export_candidates(batch.ptr, ctypes.byref(n), r.ctypes.data, s.ctypes.data,
+                                               lo.ctypes.data, hi.ctypes.data))
+    return r[:k], s[:k], lo[:k].astype(np.int64), hi[:k].astype(np.int64)
+
+
+def bitvector_columns(patterns, texts, stream=None):
+    """peanut_debug_bitvector_columns: D columns of (pattern, text) pairs, one int32 array each."""
+    pats = [bytes(p) for p in patterns]
+    txts = [bytes(t) for t in texts]
+    po = np.zeros(len(pats) + 1, np.uint64)
+    po[1:] = np.cumsum([len(p) for p in pats])
+    to = np.zeros(len(txts) + 1, np.uint64)
+    to[1:] = np.cumsum([len(t) for t in txts])
+    P = np.frombuffer(b"".join(pats), np.uint8).copy()
+    T = np.frombuffer(b"".join(txts), np.uint8).copy()
+    out = np.empty(max(int(to[-1]), 1), np.int32)
+    _check(load().peanut_debug_bitvector_columns(P.ctypes.data, po.ctypes.data, len(pats), T.ctypes.data,
+                                                 to.ctypes.data, out.ctypes.data, _stream_ptr(stream)))
+    return [out[int(to[i]):int(to[i + 1])].copy() for i in range(len(pats))]
