@@ -91,7 +91,11 @@ typedef struct {
     uint64_t results;          /* hits returned */
     uint64_t lowcx_reads;      /* reads verified around frequent q-gram clusters */
     uint64_t scan_retries;     /* hit-buffer regrowths */
+    uint64_t present_probes;   /* reference positions whose canonical q-gram is indexed */
+    uint64_t candidate_word_columns; /* columns x 64-bit words of the verification */
     float ms_scan, ms_bin, ms_windows, ms_verify, ms_output; /* device time per stage */
+    float ms_scan_kernel;      /* the reference-scan kernel alone (CUDA events on its stream) */
+    float ms_verify_kernel;    /* the verification count pass alone (CUDA events on its stream) */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
@@ -150,6 +154,9 @@ void peanut_free(void* obj);
 
 /* Message describing the last failure on this thread ("" if none). */
 const char* peanut_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (diagnostics). */
+uint64_t peanut_kernel_launches(void);
 
 /* Device memory provider for all later allocations (e.g. a caching allocator of the host
  * framework).  alloc(bytes, stream, ctx) returns device memory or NULL; release(ptr, stream,

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.cuh"
@@ -19,6 +20,10 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = 0; }
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static peanut_alloc_fn g_alloc = nullptr;
 static peanut_release_fn g_release = nullptr;
@@ -90,6 +95,8 @@ static peanut_status guarded(F&& f) {
 extern "C" {
 
 const char* peanut_last_error(void) { return g_err; }
+
+uint64_t peanut_kernel_launches(void) { return g_launches.load(); }
 
 peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn release, void* ctx) {
     return guarded([&] {

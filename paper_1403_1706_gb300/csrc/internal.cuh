@@ -51,7 +51,12 @@ struct Fail {
         }                                                                                   \
     } while (0)
 
-#define PN_CHECK_LAUNCH() PN_CUDA(cudaGetLastError())
+void note_launch();  // counts kernel launches (peanut_kernel_launches)
+#define PN_CHECK_LAUNCH()                \
+    do {                                 \
+        ::pn::note_launch();             \
+        PN_CUDA(cudaGetLastError());     \
+    } while (0)
 
 #define PN_REQUIRE(cond, status, ...)        \
     do {                                     \

@@ -46,11 +46,12 @@ __global__ void __launch_bounds__(kScanBlock)
     scan_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
                const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O,
                const uint8_t* __restrict__ len, uint64_t* __restrict__ hits, uint64_t cap,
-               unsigned long long* n_hits, uint32_t* __restrict__ rcount) {
+               unsigned long long* n_hits, uint32_t* __restrict__ rcount, unsigned long long* n_present) {
     __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t* st = stage[wid];
     uint32_t scnt = 0;
+    uint32_t present = 0;
     const uint64_t npos = n >= q ? n - q + 1 : 0;
     const uint64_t nchunks = (npos + 31) / 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kScanBlock)
                 const uint2 v = vv[u];
                 uint32_t kb = 0, ke = 0;
                 if ((v.x >> (c & 31)) & 1u) {
+                    ++present;
                     const uint32_t slot = v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
                     kb = __ldg(Sp + slot);
                     ke = __ldg(Sp + slot + 1);
@@ -138,6 +140,9 @@ __global__ void __launch_bounds__(kScanBlock)
         }
     }
     stage_flush(st, scnt, hits, cap, n_hits);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) present += __shfl_xor_sync(kFull, present, o);
+    if (lane == 0) atomicAdd(n_present, (unsigned long long)present);
 }
 
 // ---- binning hits by read ---------------------------------------------------------------
@@ -579,7 +584,7 @@ struct VerifyParams {
     const uint64_t* peq;
     uint32_t* cnt;          // tuples per candidate
     uint64_t* inl;          // 2 inline tuples per candidate: end << 8 | dist
-    unsigned long long* columns;
+    unsigned long long* columns;  // [0] columns, [1] columns x words
     // phase 2
     const uint64_t* toff;
     uint32_t* out_read;
@@ -634,6 +639,7 @@ __device__ void verify_one(const VerifyParams& V, uint64_t x) {
     if (!kWrite) {
         V.cnt[x] = nt;
         atomicAdd(V.columns, (unsigned long long)(hi - a + 1));
+        atomicAdd(V.columns + 1, (unsigned long long)(hi - a + 1) * W);
     }
 }
 
@@ -743,12 +749,14 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     const uint32_t n_reads = R->n_reads, q = R->q;
     const uint64_t n = ref->n;
     Timer tm(s);
+    Timer ktm(s);
+    cudaEvent_t* kev = ktm.ev;
     peanut_map_stats st = {};
     tm.mark();  // 0
 
     // 1. reference scan
     DBuf<uint32_t> rcount((uint64_t)n_reads + 1, s);
-    DBuf<unsigned long long> nh(1, s);
+    DBuf<unsigned long long> nh(2, s);  // [0] hits, [1] present probes
     const double rand_hits = 2.0 * (double)n * (double)R->n_indexed / (double)(1ull << (2 * q));
     uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
     DBuf<uint64_t> hits;
@@ -758,10 +766,16 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         hits.alloc(cap, s);
         rcount.zero();
         nh.zero();
+        PN_CUDA(cudaEventRecord(kev[0], s));
         scan_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->Sp.p, R->O.p, R->len.p, hits.p,
-                                                cap, nh.p, rcount.p);
+                                                cap, nh.p, rcount.p, nh.p + 1);
         PN_CHECK_LAUNCH();
-        H = to_host(nh.p, s);
+        PN_CUDA(cudaEventRecord(kev[1], s));
+        unsigned long long hv[2];
+        PN_CUDA(cudaMemcpyAsync(hv, nh.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+        H = hv[0];
+        st.present_probes = hv[1];
         if (H <= cap) break;
         st.scan_retries++;
         cap = H + (H >> 4) + 1024;
@@ -864,18 +878,26 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     // 4. verification: count + inline pass, offsets, write pass
     DBuf<uint32_t> vcnt(NC ? NC : 1, s);
     DBuf<uint64_t> inl(2 * (NC ? NC : 1), s), toff(NC ? NC : 1, s);
-    DBuf<unsigned long long> cols(1, s);
+    DBuf<unsigned long long> cols(2, s);
     cols.zero();
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
     const unsigned gv = grid_for(NC, 128, (unsigned)sm_count() * 32);
+    PN_CUDA(cudaEventRecord(kev[2], s));
     if (NC) {
         verify_k<false><<<gv, 128, 0, s>>>(V);
         PN_CHECK_LAUNCH();
     }
+    PN_CUDA(cudaEventRecord(kev[3], s));
     exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
     const uint64_t NT = to_host(tot.p, s);
-    st.candidate_columns = to_host(cols.p, s);
+    {
+        unsigned long long cv[2];
+        PN_CUDA(cudaMemcpyAsync(cv, cols.p, sizeof(cv), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+        st.candidate_columns = cv[0];
+        st.candidate_word_columns = cv[1];
+    }
     DeviceHits* out = new DeviceHits();
     try {
         DeviceHits all;
@@ -926,6 +948,8 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.ms_windows = tm.ms(2, 3);
     st.ms_verify = tm.ms(3, 4);
     st.ms_output = tm.ms(4, 5);
+    cudaEventElapsedTime(&st.ms_scan_kernel, kev[0], kev[1]);
+    cudaEventElapsedTime(&st.ms_verify_kernel, kev[2], kev[3]);
     R->stats = st;
     return out;
 }

@@ -48,8 +48,9 @@ class DeviceHitsStruct(Structure):
 class MapStats(Structure):
     _fields_ = [("hits", c_uint64), ("candidates", c_uint64), ("candidate_columns", c_uint64),
                 ("results", c_uint64), ("lowcx_reads", c_uint64), ("scan_retries", c_uint64),
+                ("present_probes", c_uint64), ("candidate_word_columns", c_uint64),
                 ("ms_scan", c_float), ("ms_bin", c_float), ("ms_windows", c_float), ("ms_verify", c_float),
-                ("ms_output", c_float)]
+                ("ms_output", c_float), ("ms_scan_kernel", c_float), ("ms_verify_kernel", c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -71,6 +72,7 @@ def load():
     st = c_int
     sig = {
         "peanut_last_error": (c_char_p, []),
+        "peanut_kernel_launches": (c_uint64, []),
         "peanut_set_allocator": (st, [ALLOC_FN, RELEASE_FN, c_void_p]),
         "peanut_pack_reference": (st, [c_void_p, c_uint64, c_void_p, POINTER(c_void_p)]),
         "peanut_ref_length": (c_uint64, [c_void_p]),
@@ -261,6 +263,11 @@ def map_device(ref: Reference, batch: ReadBatch, mode: str = "all") -> DeviceHit
     hp = POINTER(DeviceHitsStruct)()
     _check(load().peanut_map_device(ref.ptr, batch.ptr, MODES[mode], ctypes.byref(hp)))
     return DeviceHits(hp)
+
+
+def kernel_launches() -> int:
+    """peanut_kernel_launches: kernels launched by the library so far in this process."""
+    return int(load().peanut_kernel_launches())
 
 
 def get_map_stats(batch: ReadBatch) -> dict:
