@@ -29,9 +29,12 @@ static peanut_alloc_fn g_alloc = nullptr;
 static peanut_release_fn g_release = nullptr;
 static void* g_ctx = nullptr;
 
-void* dalloc(size_t bytes, cudaStream_t s) {
+Allocator current_allocator() { return Allocator{g_alloc, g_release, g_ctx}; }
+
+void* dalloc(size_t bytes, cudaStream_t s, Allocator* used) {
     void* p = nullptr;
     if (bytes == 0) bytes = 1;
+    if (used) *used = current_allocator();
     if (g_alloc) {
         p = g_alloc(bytes, (void*)s, g_ctx);
         if (!p) {
@@ -49,13 +52,13 @@ void* dalloc(size_t bytes, cudaStream_t s) {
     return p;
 }
 
-void dfree(void* p, cudaStream_t s) {
+void dfree(void* p, cudaStream_t s, const Allocator& a) {
     if (!p) return;
-    if (g_release) {
-        g_release(p, (void*)s, g_ctx);
+    if (a.release) {
+        a.release(p, (void*)s, a.ctx);
         return;
     }
-    cudaFreeAsync(p, s);
+    if (cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();  // never leave a stale error behind
 }
 
 int sm_count() {
@@ -78,6 +81,7 @@ using namespace pn;
 template <class F>
 static peanut_status guarded(F&& f) {
     clear_error();
+    cudaGetLastError();  // an earlier, unrelated failure must not be reported by this call
     try {
         f();
         return PEANUT_OK;

@@ -67,21 +67,29 @@ void note_launch();  // counts kernel launches (peanut_kernel_launches)
     } while (0)
 
 // ---- device memory ----------------------------------------------------------------------
-void* dalloc(size_t bytes, cudaStream_t s);  // throws Fail{NO_MEMORY}
-void dfree(void* p, cudaStream_t s);
+// The provider that made an allocation releases it, even if another was installed since.
+struct Allocator {
+    peanut_alloc_fn alloc = nullptr;      // nullptr: cudaMallocAsync / cudaFreeAsync
+    peanut_release_fn release = nullptr;
+    void* ctx = nullptr;
+};
+Allocator current_allocator();
+void* dalloc(size_t bytes, cudaStream_t s, Allocator* used = nullptr);  // throws Fail{NO_MEMORY}
+void dfree(void* p, cudaStream_t s, const Allocator& a);
 
 template <class T>
 struct DBuf {
     T* p = nullptr;
     size_t n = 0;
     cudaStream_t s = nullptr;
+    Allocator a;
     DBuf() = default;
     DBuf(size_t count, cudaStream_t st) { alloc(count, st); }
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
-    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s), a(o.a) { o.p = nullptr; o.n = 0; }
     DBuf& operator=(DBuf&& o) noexcept {
-        if (this != &o) { reset(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+        if (this != &o) { reset(); p = o.p; n = o.n; s = o.s; a = o.a; o.p = nullptr; o.n = 0; }
         return *this;
     }
     ~DBuf() { reset(); }
@@ -89,13 +97,13 @@ struct DBuf {
         reset();
         s = st;
         n = count;
-        p = count ? static_cast<T*>(dalloc(count * sizeof(T), st)) : nullptr;
+        p = count ? static_cast<T*>(dalloc(count * sizeof(T), st, &a)) : nullptr;
     }
     void zero() {
         if (n) PN_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
     }
     void reset() {
-        if (p) dfree(p, s);
+        if (p) dfree(p, s, a);
         p = nullptr;
         n = 0;
     }
@@ -185,6 +193,7 @@ struct DeviceHits {
     uint32_t magic = pn::kMagicDHits;
     peanut_device_hits h = {};
     cudaStream_t stream = nullptr;
+    pn::Allocator a;  // made the four arrays
 };
 
 namespace pn {

@@ -729,6 +729,7 @@ struct Timer {
 static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s) {
     H->stream = s;
     H->h.n = n;
+    H->a = current_allocator();
     const uint64_t c = n ? n : 1;
     H->h.read_id = static_cast<uint32_t*>(dalloc(c * sizeof(uint32_t), s));
     H->h.strand = static_cast<uint8_t*>(dalloc(c, s));
@@ -737,10 +738,10 @@ static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s) {
 }
 
 static void free_hits_arrays(DeviceHits* H) {
-    if (H->h.read_id) dfree(H->h.read_id, H->stream);
-    if (H->h.strand) dfree(H->h.strand, H->stream);
-    if (H->h.end_pos) dfree(H->h.end_pos, H->stream);
-    if (H->h.dist) dfree(H->h.dist, H->stream);
+    if (H->h.read_id) dfree(H->h.read_id, H->stream, H->a);
+    if (H->h.strand) dfree(H->h.strand, H->stream, H->a);
+    if (H->h.end_pos) dfree(H->h.end_pos, H->stream, H->a);
+    if (H->h.dist) dfree(H->h.dist, H->stream, H->a);
     H->h = peanut_device_hits{};
 }
 
@@ -932,6 +933,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
             free_hits_arrays(&all);
         } else {
             out->stream = s;
+            out->a = all.a;
             out->h = all.h;
             all.h = peanut_device_hits{};
         }
@@ -1034,3 +1036,4 @@ __global__ void pattern_peq_k(const uint8_t* pat, const uint64_t* off, const uin
 }
 
 }  // namespace pn
+

@@ -120,13 +120,12 @@ def _host_u8(x) -> np.ndarray:
 
 # ---- allocator -----------------------------------------------------------------------------
 
-_alloc_keep = None
+_alloc_keep = []  # every callback pair ever installed: objects made under it may still be freed
 
 
 def use_torch_allocator():
     """Routes the library's device allocations through PyTorch's caching allocator."""
     import torch
-    global _alloc_keep
 
     def _alloc(size, stream, ctx):
         try:
@@ -138,14 +137,12 @@ def use_torch_allocator():
         torch.cuda.caching_allocator_delete(int(ptr))
 
     a, r = ALLOC_FN(_alloc), RELEASE_FN(_release)
+    _alloc_keep.append((a, r))
     _check(load().peanut_set_allocator(a, r, None))
-    _alloc_keep = (a, r)
 
 
 def use_default_allocator():
-    global _alloc_keep
     _check(load().peanut_set_allocator(ALLOC_FN(), RELEASE_FN(), None))
-    _alloc_keep = None
 
 
 # ---- objects -------------------------------------------------------------------------------
@@ -330,3 +327,4 @@ def bitvector_columns(patterns, texts, stream=None):
     _check(load().peanut_debug_bitvector_columns(P.ctypes.data, po.ctypes.data, len(pats), T.ctypes.data,
                                                  to.ctypes.data, out.ctypes.data, _stream_ptr(stream)))
     return [out[int(to[i]):int(to[i + 1])].copy() for i in range(len(pats))]
+

@@ -301,3 +301,23 @@ def test_device_variants_match_host(gpu):
         assert_same_hits(gpu.map(R, B2), host)
     finally:
         gpu.use_default_allocator()
+
+
+def test_objects_outlive_an_allocator_switch(gpu):
+    """An object made under one device-memory provider is released by that provider even after
+    another is installed, and leaves no error behind for the next call."""
+    import gc
+    ref, reads, w = synth.make_workload("uniform_1mbp_10k", n_reads=500)
+    R = gpu.pack_reference(ref)
+    want = gpu.map(R, gpu.index_reads(R, reads.seq, reads.offsets, 11, k=5))
+    gpu.use_torch_allocator()
+    try:
+        B = gpu.index_reads(R, reads.seq, reads.offsets, 11, k=5)
+        dh = gpu.map_device(R, B)
+    finally:
+        gpu.use_default_allocator()
+    del B, dh
+    gc.collect()
+    assert_same_hits(gpu.map(R, gpu.index_reads(R, reads.seq, reads.offsets, 11, k=5)), want)
+    assert (gpu.bitvector_columns([b"ACGT"], [b"TTACGTT"])[0].tolist()
+            == oracle.semiglobal_column(b"ACGT", b"TTACGTT").tolist())
