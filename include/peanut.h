@@ -200,6 +200,28 @@ peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pa
                                              const char* txt, const uint64_t* txt_off, int32_t* out,
                                              void* stream);
 
+/* Same computation as peanut_debug_bitvector_columns, for callers that cannot allocate device
+ * memory (the paper has no counterpart): a process whose device memory is all reserved by another
+ * allocator's pool, where a cudaMalloc fails or takes memory the pool counts on, or a
+ * latency-critical path that must not pay an allocation's implicit synchronization.  This call
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   d_pat / d_pat_off[n_pat + 1]: device, ASCII patterns (lengths 1..255) and their offsets.
+ *   d_txt / d_txt_off[n_pat + 1]: device, ASCII texts and their offsets.
+ *   d_out: device, txt_off[n_pat] int32 entries, D[j] for every text position (as above).
+ *   n_pat: 1 .. 8192 (more is rejected with PEANUT_INVALID_ARG).
+ * Scratch: the match masks of up to 8192 patterns and a status word sit in one fixed array of
+ * about 1 MiB of device memory inside the library, held by every GPU that loads it until the
+ * process exits.  The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream capture.  Every call
+ * shares the array and leaves its contents behind; calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it and must be serialized by the caller.  The call
+ * synchronizes the stream to read the status word.
+ * Errors: INVALID_ARG (NULL pointer, n_pat out of range, bad length or offsets, non-ACGT byte),
+ *         CUDA_ERROR. */
+peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat,
+                                               const char* d_txt, const uint64_t* d_txt_off, int32_t* d_out,
+                                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -417,4 +417,13 @@ peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pa
     });
 }
 
+peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat,
+                                               const char* d_txt, const uint64_t* d_txt_off, int32_t* d_out,
+                                               void* stream) {
+    return guarded([&] {
+        PN_REQUIRE(d_pat && d_pat_off && d_txt && d_txt_off && d_out, PEANUT_INVALID_ARG, "NULL argument");
+        bitvector_columns_noalloc(d_pat, d_pat_off, n_pat, d_txt, d_txt_off, d_out, (cudaStream_t)stream);
+    });
+}
+
 }  // extern "C"

@@ -207,4 +207,6 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
 DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode);
 void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
                        const uint64_t* txt_off, int32_t* out, cudaStream_t s);
+void bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat, const char* d_txt,
+                               const uint64_t* d_txt_off, int32_t* d_out, cudaStream_t s);
 }  // namespace pn

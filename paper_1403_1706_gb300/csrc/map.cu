@@ -13,6 +13,7 @@
 // the union over x with d_{x+t-1} - d_x <= k of [d_{x+t-1} + m - 1 - 2k, d_x + m - 1 + k].
 // Overlapping or touching ranges are merged so every maximal run of end positions lies in one.
 #include <cstdio>
+#include <mutex>
 
 #include "prims.cuh"
 
@@ -1037,3 +1038,111 @@ __global__ void pattern_peq_k(const uint8_t* pat, const uint64_t* off, const uin
 
 }  // namespace pn
 
+// ---- bit-vector columns without any allocation ----------------------------------------------
+//
+// peanut_bitvector_columns_noalloc runs the same Myers kernel as the test hook above, for callers
+// that must not allocate device memory.  Its scratch (the match masks of every pattern and one
+// status word) lives in this file-scope device array, which every GPU that loads the library
+// holds until the process exits.  All calls share it: a call overwrites the masks of the
+// patterns it runs and clears the status word first, and two calls whose work overlaps on the
+// GPU (different streams, or different host threads) race on it.
+
+namespace pn {
+
+constexpr uint32_t kNoAllocMaxPatterns = 8192;  // 1 MiB of match masks
+constexpr size_t kNoAllocPeqWords = (size_t)kNoAllocMaxPatterns * 4 * kMaxWords;
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocPeqWords + 32];
+
+enum : uint32_t { kNaBadPatLen = 1u, kNaBadBase = 2u, kNaBadTxtOff = 4u };
+
+__device__ __forceinline__ uint32_t na_code(uint8_t ch, uint32_t* status) {
+    switch (ch) {
+        case 'A': return 0;
+        case 'C': return 1;
+        case 'G': return 2;
+        case 'T': return 3;
+        default: atomicOr(status, kNaBadBase); return 0;
+    }
+}
+
+__global__ void noalloc_peq_k(const uint8_t* __restrict__ pat, const uint64_t* __restrict__ pat_off, uint32_t n,
+                              uint64_t* scratch) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    uint32_t* status = reinterpret_cast<uint32_t*>(scratch + kNoAllocPeqWords);
+    const uint64_t a = pat_off[r], b = pat_off[r + 1];
+    uint64_t w[4][kMaxWords] = {};
+    if (b < a || b - a < 1 || b - a > (uint64_t)kMaxReadLen) {
+        atomicOr(status, kNaBadPatLen);
+    } else {
+        for (uint64_t i = 0; i < b - a; ++i) w[na_code(pat[a + i], status)][i >> 6] |= 1ull << (i & 63);
+    }
+    for (int c = 0; c < 4; ++c)
+        for (int x = 0; x < kMaxWords; ++x) scratch[((uint64_t)r * 4 + c) * kMaxWords + x] = w[c][x];
+}
+
+__global__ void noalloc_columns_k(const uint64_t* __restrict__ pat_off, uint32_t n, const uint8_t* __restrict__ txt,
+                                  const uint64_t* __restrict__ txt_off, int32_t* __restrict__ out,
+                                  const uint64_t* scratch) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    uint32_t* status = reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(scratch) + kNoAllocPeqWords);
+    const uint64_t a = pat_off[r], b = pat_off[r + 1];
+    if (b < a || b - a < 1 || b - a > (uint64_t)kMaxReadLen) return;
+    const uint64_t tb = txt_off[r], te = txt_off[r + 1];
+    if (te < tb) {
+        atomicOr(status, kNaBadTxtOff);
+        return;
+    }
+    const uint32_t m = (uint32_t)(b - a);
+    const uint64_t* pq = scratch + (uint64_t)r * 4 * kMaxWords;
+    auto run = [&](auto M) {
+        M.init(pq, m);
+        for (uint64_t j = tb; j < te; ++j) out[j] = M.step(na_code(txt[j], status));
+    };
+    switch ((m + 63) >> 6) {
+        case 1: run(Myers<1>{}); break;
+        case 2: run(Myers<2>{}); break;
+        case 3: run(Myers<3>{}); break;
+        default: run(Myers<4>{}); break;
+    }
+}
+
+// Device address of the scratch array on the current device, looked up once per device with
+// that device current.
+static uint64_t* noalloc_scratch() {
+    static std::mutex mu;
+    static uint64_t* ptrs[256] = {};
+    int dev = 0;
+    PN_CUDA(cudaGetDevice(&dev));
+    PN_REQUIRE(dev >= 0 && dev < 256, PEANUT_UNSUPPORTED, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        PN_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        ptrs[dev] = static_cast<uint64_t*>(p);
+    }
+    return ptrs[dev];
+}
+
+void bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat, const char* d_txt,
+                               const uint64_t* d_txt_off, int32_t* d_out, cudaStream_t s) {
+    PN_REQUIRE(n_pat >= 1 && n_pat <= kNoAllocMaxPatterns, PEANUT_INVALID_ARG,
+               "n_pat = %u outside 1..%u (the fixed scratch holds the masks of %u patterns)", n_pat,
+               kNoAllocMaxPatterns, kNoAllocMaxPatterns);
+    uint64_t* scratch = noalloc_scratch();
+    PN_CUDA(cudaMemsetAsync(scratch + kNoAllocPeqWords, 0, sizeof(uint64_t), s));
+    noalloc_peq_k<<<grid_for(n_pat, 128), 128, 0, s>>>((const uint8_t*)d_pat, d_pat_off, n_pat, scratch);
+    PN_CHECK_LAUNCH();
+    noalloc_columns_k<<<grid_for(n_pat, 64), 64, 0, s>>>(d_pat_off, n_pat, (const uint8_t*)d_txt, d_txt_off, d_out,
+                                                         scratch);
+    PN_CHECK_LAUNCH();
+    uint32_t st = 0;
+    PN_CUDA(cudaMemcpyAsync(&st, scratch + kNoAllocPeqWords, sizeof(st), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    PN_REQUIRE(!(st & kNaBadPatLen), PEANUT_INVALID_ARG, "a pattern length is outside 1..%d", kMaxReadLen);
+    PN_REQUIRE(!(st & kNaBadTxtOff), PEANUT_INVALID_ARG, "text offsets must ascend");
+    PN_REQUIRE(!(st & kNaBadBase), PEANUT_INVALID_ARG, "a pattern or text contains a byte other than A/C/G/T");
+}
+
+}  // namespace pn

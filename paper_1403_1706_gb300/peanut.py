@@ -90,6 +90,8 @@ def load():
         "peanut_export_candidates": (st, [c_void_p, POINTER(c_uint64), c_void_p, c_void_p, c_void_p, c_void_p]),
         "peanut_debug_bitvector_columns": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
                                                 c_void_p]),
+        "peanut_bitvector_columns_noalloc": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
+                                                  c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -328,3 +330,11 @@ def bitvector_columns(patterns, texts, stream=None):
                                                  to.ctypes.data, out.ctypes.data, _stream_ptr(stream)))
     return [out[int(to[i]):int(to[i + 1])].copy() for i in range(len(pats))]
 
+
+def bitvector_columns_noalloc(d_pat, d_pat_off, d_txt, d_txt_off, d_out, stream=None):
+    """peanut_bitvector_columns_noalloc: the same columns with every buffer in device memory
+    (torch tensors: uint8 patterns / texts, int64 offsets, int32 output) and no allocation
+    inside the library; its scratch is a fixed array of up to 8192 patterns' masks."""
+    _check(load().peanut_bitvector_columns_noalloc(d_pat.data_ptr(), d_pat_off.data_ptr(), int(d_pat_off.numel()) - 1,
+                                                   d_txt.data_ptr(), d_txt_off.data_ptr(), d_out.data_ptr(),
+                                                   _stream_ptr(stream)))
