@@ -31,6 +31,22 @@ static void* g_ctx = nullptr;
 
 Allocator current_allocator() { return Allocator{g_alloc, g_release, g_ctx}; }
 
+// Keep memory freed to the process's default CUDA memory pool cached for reuse (release threshold
+// raised once per device), so per-batch temporaries are not returned to the driver and re-mapped
+// at every stream synchronization.
+static void retain_pool_memory() {
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 void* dalloc(size_t bytes, cudaStream_t s, Allocator* used) {
     void* p = nullptr;
     if (bytes == 0) bytes = 1;
@@ -43,6 +59,7 @@ void* dalloc(size_t bytes, cudaStream_t s, Allocator* used) {
         }
         return p;
     }
+    retain_pool_memory();
     const cudaError_t e = cudaMallocAsync(&p, bytes, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

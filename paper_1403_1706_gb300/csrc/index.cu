@@ -449,6 +449,16 @@ __global__ void scatter_qgrams_k(const uint32_t* __restrict__ tcode, const uint3
     }
 }
 
+__global__ void bloom_set_k(const uint32_t* __restrict__ tcode, uint64_t n, uint64_t* bloom, uint64_t mask) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = tcode[x];
+        if (c == kSentinel) continue;
+        const uint64_t h = bloom_hash(c);
+        atomicOr((unsigned long long*)(bloom + ((h >> 24) & mask)), (unsigned long long)bloom_bits(h));
+    }
+}
+
 // Match masks of Myers' algorithm (Section "Validation"): bit i of peq[r][s][c][w] is set when
 // position 64 w + i of the pattern (the read for s = 0, its reverse complement for s = 1) is c.
 __global__ void peq_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ off,
@@ -549,6 +559,15 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     R->n_indexed = sizes[1];
     R->O.alloc(R->n_indexed ? R->n_indexed : 1, s);
     scatter_qgrams_k<<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, R->IS.p, R->Sp.p, cnt.p, R->O.p);
+    PN_CHECK_LAUNCH();
+    // prefilter for the reference scan: about 6 bits per distinct code, at most 64 MB so that it
+    // stays resident in the 129 MB L2 while the index itself is probed in HBM
+    uint64_t words = 1024;
+    while (words < (1ull << 23) && words * 64 < R->n_distinct * 6) words <<= 1;
+    R->bloom.alloc(words, s);
+    R->bloom.zero();
+    R->bloom_mask = words - 1;
+    bloom_set_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->bloom.p, R->bloom_mask);
     PN_CHECK_LAUNCH();
 
     R->peq.alloc((uint64_t)n * 2 * 4 * kMaxWords, s);

@@ -171,6 +171,8 @@ struct peanut_reads {
     pn::DBuf<uint2> IS;           // (I word, S) per group of 32 canonical codes
     pn::DBuf<uint32_t> Sp;        // n_qgrams + 1 (first n_distinct + 1 meaningful)
     pn::DBuf<uint32_t> O;         // n_indexed entries (read << 9 | orientation << 8 | offset)
+    pn::DBuf<uint64_t> bloom;     // blocked Bloom filter of the indexed canonical codes (L2-sized)
+    uint64_t bloom_mask = 0;      // words - 1
     // frequent q-grams of each read (only meaningful for reads with fcnt > 0)
     pn::DBuf<uint64_t> qoff;      // n+1: q-gram slot offsets
     pn::DBuf<uint32_t> fcnt;      // frequent q-grams per read

@@ -35,7 +35,7 @@ __device__ __forceinline__ void stage_flush(uint64_t* st, uint32_t cnt, uint64_t
     if ((threadIdx.x & 31) == 0 && cnt) base = atomicAdd(n_hits, (unsigned long long)cnt);
     base = __shfl_sync(kFull, base, 0);
     for (uint32_t j = threadIdx.x & 31; j < cnt; j += 32)
-        if (base + j < cap) hits[base + j] = st[j];
+        if (base + j < cap) __stcs(hits + base + j, st[j]);
     __syncwarp();
 }
 
@@ -43,11 +43,12 @@ __device__ __forceinline__ void stage_flush(uint64_t* st, uint32_t cnt, uint64_t
 // of a chunk; the canonical code of each position is probed in the read index and every
 // occurrence becomes a hit key.  Hits are staged per warp in shared memory and appended to the
 // global buffer with one atomic per stage; rcount[r] counts each read's hits.
-__global__ void __launch_bounds__(kScanBlock)
+__global__ void __launch_bounds__(kScanBlock, 4)
     scan_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
                const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O,
-               const uint8_t* __restrict__ len, uint64_t* __restrict__ hits, uint64_t cap,
-               unsigned long long* n_hits, uint32_t* __restrict__ rcount, unsigned long long* n_present) {
+               const uint8_t* __restrict__ len, const uint64_t* __restrict__ bloom, uint64_t bloom_mask,
+               uint64_t* __restrict__ hits, uint64_t cap, unsigned long long* n_hits, uint32_t* __restrict__ rcount,
+               unsigned long long* n_present) {
     __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t* st = stage[wid];
@@ -64,15 +65,15 @@ __global__ void __launch_bounds__(kScanBlock)
         const uint64_t p0 = ch * 32;
         uint32_t w0 = 0, w1 = 0, w2 = 0;
         if (active) {
-            w0 = __ldg(packed + p0 / 16);
-            w1 = __ldg(packed + p0 / 16 + 1);
-            w2 = __ldg(packed + p0 / 16 + 2);
+            w0 = __ldcs(packed + p0 / 16);
+            w1 = __ldcs(packed + p0 / 16 + 1);
+            w2 = __ldcs(packed + p0 / 16 + 2);
         }
 #pragma unroll 1
         for (int o0 = 0; o0 < 32; o0 += 8) {
             uint32_t cc[8];
-            uint2 vv[8];
-            uint32_t meta[8];  // bit 0: valid, bit 1: f_ref, bit 2: palindrome
+            uint32_t meta[8];  // bit 0: passes the prefilter, bit 1: f_ref, bit 2: palindrome
+            uint64_t fw[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int o = o0 + u;
@@ -83,7 +84,14 @@ __global__ void __launch_bounds__(kScanBlock)
                 const bool valid = active && p0 + o < npos;
                 cc[u] = c;
                 meta[u] = (valid ? 1u : 0u) | (g > h ? 2u : 0u) | (g == h ? 4u : 0u);
-                vv[u] = valid ? __ldg(IS + (c >> 5)) : make_uint2(0, 0);
+                fw[u] = valid ? __ldg(bloom + ((bloom_hash(c) >> 24) & bloom_mask)) : 0;
+            }
+            uint2 vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t fb = bloom_bits(bloom_hash(cc[u]));
+                const bool pass = (meta[u] & 1u) && (fw[u] & fb) == fb;
+                vv[u] = pass ? __ldcs(IS + (cc[u] >> 5)) : make_uint2(0, 0);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -93,8 +101,8 @@ __global__ void __launch_bounds__(kScanBlock)
                 if ((v.x >> (c & 31)) & 1u) {
                     ++present;
                     const uint32_t slot = v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
-                    kb = __ldg(Sp + slot);
-                    ke = __ldg(Sp + slot + 1);
+                    kb = __ldcs(Sp + slot);
+                    ke = __ldcs(Sp + slot + 1);
                 }
                 const int64_t p = (int64_t)(p0 + o0 + u);
                 const uint32_t fref = (meta[u] >> 1) & 1u;
@@ -105,7 +113,7 @@ __global__ void __launch_bounds__(kScanBlock)
                     uint64_t key0 = 0, key1 = 0;
                     int nk = 0;
                     if (has) {
-                        const uint32_t e = __ldg(O + kb);
+                        const uint32_t e = __ldcs(O + kb);
                         ++kb;
                         const uint32_t r = e >> 9, fr = (e >> 8) & 1u, i = e & 255u;
                         const int64_t m = __ldg(len + r);
@@ -334,6 +342,9 @@ struct LcParams {
     const uint64_t* wlo;
     const uint64_t* whi;
     const uint32_t* wcnt;
+    const uint8_t* codes;   // read bases (2-bit codes, one per byte)
+    const uint64_t* base_off;
+    const uint32_t* packed; // reference
 };
 
 // Sort each listed read's frequent entries by (phi, orientation, offset) (insertion sort; <= 252).
@@ -393,77 +404,321 @@ __device__ __forceinline__ bool span_of(const LcParams& L, uint64_t c, int64_t i
     return a <= b;
 }
 
-// Exact number of (clipped, non-empty) ranges of segment y = 2 * list index + strand.
-__global__ void lc_count_k(LcParams L, uint64_t* cnt) {
+// One list of clusters to verify for a (read, strand): clusters [cb, ce) of one (q-gram,
+// orientation) with the smallest / largest offset i' of the read's q-grams on that strand; lo / hi
+// is the (clipped) range of cluster cb, the list's next range.
+struct LcDesc {
+    uint64_t cb, ce;
+    int64_t imin, imax;
+    int64_t lo, hi;
+};
+
+// The range to verify around cluster c (Section "Filtration" diagonals p - i'), clipped to the
+// reference: [cl_lo - i'max + m - 1 - 2k, cl_hi - i'min + m - 1 + k].
+__device__ __forceinline__ void cluster_range(const LcParams& L, uint64_t c, int64_t imin, int64_t imax, int64_t m,
+                                              int64_t k, int64_t* lo, int64_t* hi) {
+    const int64_t n = (int64_t)L.n;
+    const int64_t a = (int64_t)L.cl_lo[c] - imax + m - 1 - 2 * k;
+    const int64_t b = (int64_t)L.cl_hi[c] - imin + m - 1 + k;
+    *lo = a < 0 ? 0 : a;
+    *hi = b > n - 1 ? n - 1 : b;
+}
+
+// Per segment y = 2 * list index + strand: its number of cluster lists and an upper bound on its
+// merged ranges (counting-filter ranges plus one per cluster).
+__global__ void lc_count_k(LcParams L, uint64_t* ndesc, uint64_t* cap) {
+    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= 2 * L.n_list) return;
+    const uint32_t r = L.list[y >> 1], s = y & 1;
+    uint64_t nd = 0, c = L.wcnt[2 * r + s];
+    lc_lists(L, r, s, [&](uint64_t cb, uint64_t ce, int64_t, int64_t) {
+        ++nd;
+        c += ce - cb;
+    });
+    ndesc[y] = nd;
+    cap[y] = c;
+}
+
+__global__ void lc_desc_k(LcParams L, const uint64_t* doff, LcDesc* desc) {
     const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= 2 * L.n_list) return;
     const uint32_t r = L.list[y >> 1], s = y & 1;
     const int64_t m = L.len[r], k = L.kk[r];
-    uint64_t c = L.wcnt[2 * r + s];
+    uint64_t o = doff[y];
     lc_lists(L, r, s, [&](uint64_t cb, uint64_t ce, int64_t imin, int64_t imax) {
-        for (uint64_t x = cb; x < ce; ++x) {
-            int64_t lo, hi;
-            c += span_of(L, x, imin, imax, m, k, &lo, &hi) ? 1 : 0;
-        }
-    });
-    cnt[y] = c;
-}
-
-// Writes (segment << 40 | lo, hi) for every range of segment y = 2 * list index + strand.
-__global__ void lc_fill_k(LcParams L, const uint64_t* off, uint64_t* keys, uint64_t* vals) {
-    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= 2 * L.n_list) return;
-    const uint32_t r = L.list[y >> 1], s = y & 1;
-    const int64_t m = L.len[r], k = L.kk[r];
-    uint64_t o = off[y];
-    const uint64_t seg = (uint64_t)y << 40;
-    // the W_n ranges of this strand (already clipped)
-    const uint64_t wb = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
-    for (uint32_t x = 0; x < L.wcnt[2 * r + s]; ++x) {
-        keys[o] = seg | (L.wlo[wb + x] & kPosMask40);
-        vals[o] = L.whi[wb + x];
-        ++o;
-    }
-    lc_lists(L, r, s, [&](uint64_t cb, uint64_t ce, int64_t imin, int64_t imax) {
-        for (uint64_t c = cb; c < ce; ++c) {
-            int64_t lo, hi;
-            if (!span_of(L, c, imin, imax, m, k, &lo, &hi)) continue;
-            keys[o] = seg | (uint64_t)lo;
-            vals[o] = (uint64_t)hi;
-            ++o;
-        }
+        LcDesc d{cb, ce, imin, imax, 0, 0};
+        cluster_range(L, cb, imin, imax, m, k, &d.lo, &d.hi);
+        desc[o++] = d;
     });
 }
 
-// Merges each segment's sorted ranges in place; lcnt[y] = merged count.
-__global__ void lc_merge_k(uint32_t nseg, const uint64_t* off, uint64_t* keys, uint64_t* vals, uint32_t* lcnt) {
-    const uint32_t y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= nseg) return;
-    const uint64_t b = off[y], e = off[y + 1];
-    uint32_t c = 0;
-    int64_t lo = 0, hi = -2;
+// Merged ranges of one segment are written to olo / ohi at off[y] + cnt.
+struct MergeOut {
+    int64_t cur_lo = 0, cur_hi = -2;
     bool open = false;
-    for (uint64_t x = b; x < e; ++x) {
-        const int64_t l = (int64_t)(keys[x] & kPosMask40), h = (int64_t)vals[x];
-        if (open && l <= hi + 1) {
-            if (h > hi) hi = h;
+    uint32_t cnt = 0;
+    // Consumes the next range in increasing start; returns true when a finished range must be
+    // written as (wlo, whi).
+    __device__ __forceinline__ bool add(int64_t lo, int64_t hi, int64_t* wlo, int64_t* whi) {
+        if (lo > hi) return false;  // clipped away
+        if (open && lo <= cur_hi + 1) {
+            if (hi > cur_hi) cur_hi = hi;
+            return false;
+        }
+        const bool flush = open;
+        *wlo = cur_lo;
+        *whi = cur_hi;
+        cur_lo = lo;
+        cur_hi = hi;
+        open = true;
+        return flush;
+    }
+};
+
+// Slow path (a segment with 32 or more cluster lists): one lane merges sequentially.
+__device__ void lc_kmerge_serial(const LcParams& L, uint32_t r, uint32_t s, uint64_t d0, uint64_t d1, LcDesc* desc,
+                                 uint64_t o, uint64_t* olo, uint64_t* ohi, uint32_t* ocnt_y) {
+    const int64_t m = L.len[r], k = L.kk[r];
+    uint64_t w = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
+    const uint64_t we = w + L.wcnt[2 * r + s];
+    MergeOut M;
+    int64_t a, b;
+    while (true) {
+        int64_t lo = INT64_MAX, hi = 0;
+        int64_t src = -2;
+        if (w < we) {
+            lo = (int64_t)(L.wlo[w] & kPosMask40);
+            hi = (int64_t)L.whi[w];
+            src = -1;
+        }
+        for (uint64_t j = d0; j < d1; ++j)
+            if (desc[j].cb < desc[j].ce && desc[j].lo < lo) {
+                lo = desc[j].lo;
+                hi = desc[j].hi;
+                src = (int64_t)j;
+            }
+        if (src == -2) break;
+        if (src == -1) {
+            ++w;
+        } else {
+            LcDesc& d = desc[src];
+            if (++d.cb < d.ce) cluster_range(L, d.cb, d.imin, d.imax, m, k, &d.lo, &d.hi);
+        }
+        if (M.add(lo, hi, &a, &b)) {
+            olo[o + M.cnt] = (uint64_t)a;
+            ohi[o + M.cnt] = (uint64_t)b;
+            ++M.cnt;
+        }
+    }
+    if (M.open) {
+        olo[o + M.cnt] = (uint64_t)M.cur_lo;
+        ohi[o + M.cnt] = (uint64_t)M.cur_hi;
+        ++M.cnt;
+    }
+    *ocnt_y = M.cnt;
+}
+
+constexpr int kMergeWarps = 2;  // warps per block of the k-way merge (16 KB of buffers each)
+
+// k-way merge, one warp per segment: the counting-filter ranges of the strand and every cluster
+// list are each sorted by start.  Lane j < (number of lists) owns list j, the next lane owns the
+// counting-filter ranges.  Each source's next 32 ranges sit in a shared-memory buffer that the
+// warp refills with one coalesced load; every step the warp takes the smallest start (shuffle
+// reduction over the owners' buffer heads), the owner advances, and overlapping or touching
+// ranges are merged, so every maximal run of end positions lies in one output range.
+__global__ void __launch_bounds__(kMergeWarps * 32)
+    lc_kmerge_k(LcParams L, const uint64_t* doff, LcDesc* desc, const uint64_t* off, uint64_t* olo, uint64_t* ohi,
+                uint32_t* ocnt) {
+    __shared__ int64_t blo[kMergeWarps][32][32], bhi[kMergeWarps][32][32];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < 2 * L.n_list; y += nw) {
+        const uint32_t r = L.list[y >> 1], s = y & 1;
+        const int64_t m = L.len[r], k = L.kk[r];
+        const uint64_t d0 = doff[y], d1 = doff[y + 1];
+        const uint32_t nd = (uint32_t)(d1 - d0);
+        const uint64_t o = off[y];
+        if (nd >= 32) {
+            if (lane == 0) lc_kmerge_serial(L, r, s, d0, d1, desc, o, olo, ohi, ocnt + y);
+            __syncwarp();
             continue;
         }
-        if (open) {
-            keys[b + c] = (uint64_t)lo;
-            vals[b + c] = (uint64_t)hi;
-            ++c;
+        const uint32_t S = nd + 1;  // sources: nd cluster lists and the counting-filter ranges
+        uint64_t cur = 0, end = 0;
+        int64_t imin = 0, imax = 0;
+        uint32_t cnt = 0, rd = 0;
+        if (lane < nd) {
+            cur = desc[d0 + lane].cb;
+            end = desc[d0 + lane].ce;
+            imin = desc[d0 + lane].imin;
+            imax = desc[d0 + lane].imax;
+        } else if (lane == nd) {
+            cur = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
+            end = cur + L.wcnt[2 * r + s];
         }
-        lo = l;
-        hi = h;
-        open = true;
+        // the whole warp loads the next (up to) 32 ranges of source j into its buffer
+        auto refill = [&](uint32_t j) {
+            const uint64_t c0 = __shfl_sync(kFull, cur, j), e0 = __shfl_sync(kFull, end, j);
+            const int64_t mn = __shfl_sync(kFull, imin, j), mx = __shfl_sync(kFull, imax, j);
+            const uint64_t e = c0 + lane;
+            if (e < e0) {
+                int64_t lo, hi;
+                if (j < nd) {
+                    cluster_range(L, e, mn, mx, m, k, &lo, &hi);
+                } else {
+                    lo = (int64_t)(L.wlo[e] & kPosMask40);
+                    hi = (int64_t)L.whi[e];
+                }
+                blo[wid][j][lane] = lo;
+                bhi[wid][j][lane] = hi;
+            }
+            const uint32_t got = (uint32_t)(e0 - c0 < 32 ? e0 - c0 : 32);
+            if (lane == j) {
+                cnt = got;
+                rd = 0;
+                cur += got;
+            }
+            __syncwarp();
+        };
+        for (uint32_t j = 0; j < S; ++j) refill(j);
+        MergeOut M;
+        while (true) {
+            unsigned need = __ballot_sync(kFull, lane < S && rd == cnt && cur < end);
+            while (need) {
+                const uint32_t j = __ffs(need) - 1;
+                need &= need - 1;
+                refill(j);
+            }
+            uint64_t key = ~0ull;
+            if (lane < S && rd < cnt) key = ((uint64_t)blo[wid][lane][rd] << 5) | lane;
+#pragma unroll
+            for (int x = 16; x > 0; x >>= 1) {
+                const uint64_t other = __shfl_xor_sync(kFull, key, x);
+                key = other < key ? other : key;
+            }
+            if (key == ~0ull) break;
+            const uint32_t wl = (uint32_t)(key & 31);
+            const int64_t lo = (int64_t)(key >> 5);
+            const int64_t hi = bhi[wid][wl][__shfl_sync(kFull, rd, wl)];
+            if (lane == wl) ++rd;
+            int64_t a, b;
+            if (M.add(lo, hi, &a, &b)) {
+                if (lane == 0) {
+                    olo[o + M.cnt] = (uint64_t)a;
+                    ohi[o + M.cnt] = (uint64_t)b;
+                }
+                ++M.cnt;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (M.open) {
+                olo[o + M.cnt] = (uint64_t)M.cur_lo;
+                ohi[o + M.cnt] = (uint64_t)M.cur_hi;
+            }
+            ocnt[y] = M.cnt + (M.open ? 1 : 0);
+        }
+        __syncwarp();
     }
-    if (open) {
-        keys[b + c] = (uint64_t)lo;
-        vals[b + c] = (uint64_t)hi;
-        ++c;
+}
+
+// ---- piece filter ----------------------------------------------------------------------------
+//
+// Pigeonhole over the pattern, exact: split the pattern into P = floor(m / 8) disjoint 8-base
+// pieces.  An edit breaks at most one piece (a deletion between two pieces breaks none), so an
+// alignment with e <= k edits leaves at least P - k pieces unbroken, and each unbroken piece occurs
+// in the reference inside the aligned text, which for an end in [lo, hi] lies in
+// [lo - (m + k) + 1, hi].  A candidate range whose text holds fewer than P - k of the pieces has no
+// end with distance <= k and is dropped before verification.
+
+struct PieceParams {
+    const uint64_t* cand_key;
+    const uint64_t* cand_hi;
+    uint64_t n_cand;
+    const uint8_t* len;
+    const uint8_t* kk;
+    const uint8_t* codes;
+    const uint64_t* base_off;
+    const uint32_t* packed;
+};
+
+__device__ __forceinline__ uint32_t piece_hash(uint32_t code) { return (code * 0x9E3779B1u) >> 26; }
+
+__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+#pragma unroll
+    for (int x = 16; x > 0; x >>= 1) v |= __shfl_xor_sync(kFull, v, x);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_or32(uint32_t v) {
+#pragma unroll
+    for (int x = 16; x > 0; x >>= 1) v |= __shfl_xor_sync(kFull, v, x);
+    return v;
+}
+
+constexpr int kPieceWarps = 8;
+
+// One warp per candidate range: lane t < P builds piece t; lanes then take the 8-base windows of
+// the range's text 32 at a time (window starts a .. hi - 7), test them against a 64-bit Bloom
+// word of the pieces not yet found, and mark found pieces.  Stops as soon as P - k are found.
+__global__ void __launch_bounds__(kPieceWarps * 32) piece_filter_k(PieceParams F, uint32_t* keep) {
+    __shared__ uint32_t spc[kPieceWarps][32];
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < F.n_cand; x += nw) {
+        const uint64_t key = F.cand_key[x];
+        const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
+        const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)F.cand_hi[x];
+        const int64_t m = F.len[r], k = F.kk[r];
+        const int P = (int)(m >> 3);
+        const int need = P - (int)k;
+        if (need <= 0) {
+            if (lane == 0) keep[x] = 1;
+            continue;
+        }
+        const uint8_t* rd = F.codes + F.base_off[r];
+        uint32_t code = 0;
+        if ((int)lane < P) {
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = 8 * (int64_t)lane + u;
+                code = (code << 2) | (s == 0 ? rd[i] : 3u - rd[m - 1 - i]);
+            }
+        }
+        spc[wid][lane] = code;
+        uint64_t bloom = warp_or64((int)lane < P ? 1ull << piece_hash(code) : 0ull);
+        __syncwarp();
+        int64_t a = lo - (m + k) + 1;
+        if (a < 0) a = 0;
+        uint32_t found = 0, all = 0;
+        for (int64_t j0 = a; j0 + 7 <= hi; j0 += 32) {
+            const int64_t j = j0 + lane;
+            if (j + 7 <= hi) {
+                const uint64_t w = ((uint64_t)__ldg(F.packed + (j >> 4)) << 32) | __ldg(F.packed + (j >> 4) + 1);
+                const uint32_t c8 = (uint32_t)(w >> (48 - 2 * (j & 15))) & 0xFFFFu;
+                if ((bloom >> piece_hash(c8)) & 1ull)
+                    for (int t = 0; t < P; ++t)
+                        if (spc[wid][t] == c8) found |= 1u << t;
+            }
+            const uint32_t now = warp_or32(found);
+            if (now != all) {
+                all = now;
+                if (__popc(all) >= need) break;
+                // pieces already found can no longer help: take them out of the Bloom word
+                bloom = warp_or64(((int)lane < P && !((all >> lane) & 1u)) ? 1ull << piece_hash(code) : 0ull);
+            }
+        }
+        if (lane == 0) keep[x] = __popc(all) >= need ? 1u : 0u;
+        __syncwarp();
     }
-    lcnt[y] = c;
+}
+
+__global__ void keep_compact_k(uint64_t n, const uint32_t* keep, const uint64_t* pos, const uint64_t* a,
+                               const uint64_t* b, uint64_t* oa, uint64_t* ob) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        if (!keep[x]) continue;
+        oa[pos[x]] = a[x];
+        ob[pos[x]] = b[x];
+    }
 }
 
 // ---- candidate compaction ---------------------------------------------------------------
@@ -710,7 +965,7 @@ __global__ void keep_best_k(KeepBest kb, uint64_t n, const uint64_t* pos, const 
 // ---- driver -------------------------------------------------------------------------------
 
 struct Timer {
-    cudaEvent_t ev[8];
+    cudaEvent_t ev[12];
     int n = 0;
     cudaStream_t s;
     explicit Timer(cudaStream_t st) : s(st) {
@@ -720,6 +975,7 @@ struct Timer {
         for (auto& e : ev) cudaEventDestroy(e);
     }
     void mark() { PN_CUDA(cudaEventRecord(ev[n++], s)); }
+    void mark_at(int i) { PN_CUDA(cudaEventRecord(ev[i], s)); }
     float ms(int a, int b) {
         float t = 0;
         cudaEventElapsedTime(&t, ev[a], ev[b]);
@@ -763,14 +1019,16 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
     DBuf<uint64_t> hits;
     uint64_t H = 0;
-    const unsigned gscan = (unsigned)sm_count() * 8;
+    int per_sm = 0;
+    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_ref_k, kScanBlock, 0));
+    const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
     for (int attempt = 0;; ++attempt) {
         hits.alloc(cap, s);
         rcount.zero();
         nh.zero();
         PN_CUDA(cudaEventRecord(kev[0], s));
-        scan_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->Sp.p, R->O.p, R->len.p, hits.p,
-                                                cap, nh.p, rcount.p, nh.p + 1);
+        scan_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->Sp.p, R->O.p, R->len.p,
+                                                R->bloom.p, R->bloom_mask, hits.p, cap, nh.p, rcount.p, nh.p + 1);
         PN_CHECK_LAUNCH();
         PN_CUDA(cudaEventRecord(kev[1], s));
         unsigned long long hv[2];
@@ -823,58 +1081,84 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         PN_CHECK_LAUNCH();
     }
     binned.reset();
+    ktm.mark_at(4);
 
-    // 3b. low-complexity reads: W_n ranges plus a span around every cluster of their frequent
-    // q-grams, sorted per (read, strand) and merged
+    // 3b. low-complexity reads: their counting-filter ranges and a range around every cluster of
+    // their frequent q-grams, merged per (read, strand)
     const RefPrep* P = ref->prep[q];
     const uint32_t nl = R->n_lowcx;
     DBuf<uint32_t> lcpos, lcnt;
     DBuf<uint64_t> lc_off, lc_keys, lc_vals;
     if (nl) {
+        const uint64_t nseg = 2 * (uint64_t)nl;
         LcParams L{R->lowcx_list.p, nl, R->qoff.p, R->fcnt.p, R->fent.p, R->len.p, R->kk.p, q, n,
-                   P->grp_off.p, P->cl_lo.p, P->cl_hi.p, roff.p, wlo.p, whi.p, wcnt.p};
+                   P->grp_off.p, P->cl_lo.p, P->cl_hi.p, roff.p, wlo.p, whi.p, wcnt.p, R->codes.p,
+                   R->base_off.p, ref->packed.p};
         lc_sort_k<<<grid_for(nl, 128), 128, 0, s>>>(L);
         PN_CHECK_LAUNCH();
-        DBuf<uint64_t> cnt(2 * (uint64_t)nl, s);
-        lc_count_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(L, cnt.p);
+        DBuf<uint64_t> nd(nseg, s), cap(nseg, s), doff(nseg + 1, s);
+        lc_count_k<<<grid_for(nseg, 128), 128, 0, s>>>(L, nd.p, cap.p);
         PN_CHECK_LAUNCH();
-        lc_off.alloc(2 * (uint64_t)nl + 1, s);
-        exclusive_scan(ArrayIn<uint64_t>{cnt.p}, ArrayOut<uint64_t>{lc_off.p}, 2 * (uint64_t)nl, tot.p, s);
-        PN_CUDA(cudaMemcpyAsync(lc_off.p + 2 * (uint64_t)nl, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-        const uint64_t nsp = to_host(tot.p, s);
-        lc_keys.alloc(nsp ? nsp : 1, s);
-        lc_vals.alloc(nsp ? nsp : 1, s);
-        lc_fill_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(L, lc_off.p, lc_keys.p, lc_vals.p);
+        exclusive_scan(ArrayIn<uint64_t>{nd.p}, ArrayOut<uint64_t>{doff.p}, nseg, tot.p, s);
+        PN_CUDA(cudaMemcpyAsync(doff.p + nseg, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        const uint64_t ndesc = to_host(tot.p, s);
+        lc_off.alloc(nseg + 1, s);
+        exclusive_scan(ArrayIn<uint64_t>{cap.p}, ArrayOut<uint64_t>{lc_off.p}, nseg, tot.p, s);
+        PN_CUDA(cudaMemcpyAsync(lc_off.p + nseg, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        const uint64_t ncap = to_host(tot.p, s);
+        st.lowcx_ranges = ncap;
+        DBuf<LcDesc> desc(ndesc ? ndesc : 1, s);
+        lc_desc_k<<<grid_for(nseg, 128), 128, 0, s>>>(L, doff.p, desc.p);
         PN_CHECK_LAUNCH();
-        if (nsp > 1) {
-            DBuf<uint64_t> tk(nsp, s), tv(nsp, s);
-            int segbits = 0;
-            while ((1ull << segbits) < 2 * (uint64_t)nl) ++segbits;
-            radix_sort_pairs(lc_keys.p, lc_vals.p, tk.p, tv.p, nsp, 40 + segbits, s);
-        }
-        lcnt.alloc(2 * (uint64_t)nl, s);
+        lc_keys.alloc(ncap ? ncap : 1, s);
+        lc_vals.alloc(ncap ? ncap : 1, s);
+        lcnt.alloc(nseg, s);
+        lc_kmerge_k<<<grid_for(nseg * 32, kMergeWarps * 32, (unsigned)sm_count() * 32), kMergeWarps * 32, 0, s>>>(
+            L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p);
+        PN_CHECK_LAUNCH();
         lcpos.alloc(n_reads, s);
         lcpos_k<<<grid_for(nl, 256), 256, 0, s>>>(R->lowcx_list.p, nl, lcpos.p);
         PN_CHECK_LAUNCH();
-        lc_merge_k<<<grid_for(2 * (uint64_t)nl, 128), 128, 0, s>>>(2 * nl, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p);
-        PN_CHECK_LAUNCH();
     }
     st.lowcx_reads = nl;
+    ktm.mark_at(5);
 
     // 3c. candidate compaction in (read, strand, lo) order
     CandCount cc{wcnt.p, nl ? R->lowcx.p : nullptr, lcpos.p, lcnt.p};
     DBuf<uint64_t> coff((uint64_t)n_reads + 1, s);
     exclusive_scan(cc, ArrayOut<uint64_t>{coff.p}, n_reads, tot.p, s);
-    const uint64_t NC = to_host(tot.p, s);
+    uint64_t NC = to_host(tot.p, s);
     R->cand_key.alloc(NC ? NC : 1, s);
     R->cand_hi.alloc(NC ? NC : 1, s);
     R->n_cand = NC;
     compact_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
         n_reads, cc, coff.p, roff.p, wlo.p, whi.p, lc_off.p, lc_keys.p, lc_vals.p, R->cand_key.p, R->cand_hi.p);
     PN_CHECK_LAUNCH();
-    st.candidates = NC;
     wlo.reset();
     whi.reset();
+    ktm.mark_at(6);
+    // 3d. piece filter over every candidate range, then the kept ranges in the same order
+    if (NC) {
+        DBuf<uint32_t> keep(NC, s);
+        PieceParams F{R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, R->codes.p, R->base_off.p, ref->packed.p};
+        ktm.mark_at(7);
+        piece_filter_k<<<grid_for(NC * 32, kPieceWarps * 32, (unsigned)sm_count() * 16), kPieceWarps * 32, 0, s>>>(
+            F, keep.p);
+        PN_CHECK_LAUNCH();
+        ktm.mark_at(8);
+        DBuf<uint64_t> kpos(NC, s);
+        exclusive_scan(ArrayIn<uint32_t>{keep.p}, ArrayOut<uint64_t>{kpos.p}, NC, tot.p, s);
+        const uint64_t NK = to_host(tot.p, s);
+        DBuf<uint64_t> ck(NK ? NK : 1, s), ch(NK ? NK : 1, s);
+        keep_compact_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(NC, keep.p, kpos.p, R->cand_key.p,
+                                                                                    R->cand_hi.p, ck.p, ch.p);
+        PN_CHECK_LAUNCH();
+        st.candidates_filtered = NC;
+        R->cand_key = std::move(ck);
+        R->cand_hi = std::move(ch);
+        R->n_cand = NC = NK;
+    }
+    st.candidates = NC;
     tm.mark();  // 3
 
     // 4. verification: count + inline pass, offsets, write pass
@@ -953,6 +1237,11 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.ms_output = tm.ms(4, 5);
     cudaEventElapsedTime(&st.ms_scan_kernel, kev[0], kev[1]);
     cudaEventElapsedTime(&st.ms_verify_kernel, kev[2], kev[3]);
+    cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
+    cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
+    cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);
+    cudaEventElapsedTime(&st.ms_piece_filter, kev[6], tm.ev[3]);
+    if (NC) cudaEventElapsedTime(&st.ms_piece_kernel, kev[7], kev[8]);
     R->stats = st;
     return out;
 }

@@ -234,4 +234,19 @@ __device__ __forceinline__ uint32_t revcomp_code(uint32_t g, uint32_t q) {
     return q == 16 ? x : (x >> (32 - 2 * q)) & ((1u << (2 * q)) - 1u);
 }
 
+// Blocked Bloom filter over canonical q-gram codes: one 64-bit word per key (word index from
+// bits 24.. of a 64-bit hash), four bits in that word (bits 0..23 of the hash, 6 each).
+__device__ __forceinline__ uint64_t bloom_hash(uint32_t c) {
+    uint64_t h = (uint64_t)c * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 32;
+    h *= 0xD6E8FEB86659FD93ull;
+    h ^= h >> 29;
+    return h;
+}
+
+__device__ __forceinline__ uint64_t bloom_bits(uint64_t h) {
+    return (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63)) |
+           (1ull << ((h >> 18) & 63));
+}
+
 }  // namespace pn
