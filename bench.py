@@ -344,7 +344,7 @@ def main():
 
     stage = {k2: statistics.mean(s[k2] for s in stats) for k2 in
              ("ms_scan", "ms_scan_kernel", "ms_bin", "ms_windows", "ms_windows_sweep", "ms_lowcx", "ms_compact",
-              "ms_piece_filter", "ms_piece_kernel", "ms_verify", "ms_verify_kernel", "ms_output")}
+              "ms_verify", "ms_verify_kernel", "ms_output")}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -364,7 +364,6 @@ def main():
             "candidate_columns_per_batch": statistics.mean(s["candidate_columns"] for s in stats),
             "lowcx_reads_per_batch": statistics.mean(s["lowcx_reads"] for s in stats),
             "lowcx_ranges_per_batch": statistics.mean(s["lowcx_ranges"] for s in stats),
-            "candidates_before_piece_filter_per_batch": statistics.mean(s["candidates_filtered"] for s in stats),
             "present_probes_per_batch": statistics.mean(s["present_probes"] for s in stats),
             "setup_s": {"generate": t_gen, "pack": t_pack, "warmup": t_warm},
         }

@@ -87,7 +87,6 @@ typedef struct {
 typedef struct {
     uint64_t hits;             /* q-gram hits emitted by the reference scan */
     uint64_t candidates;       /* candidate end ranges verified */
-    uint64_t candidates_filtered; /* candidate end ranges before the piece filter */
     uint64_t candidate_columns;/* reference columns run through the bit-vector verification */
     uint64_t results;          /* hits returned */
     uint64_t lowcx_reads;      /* reads verified around frequent q-gram clusters */
@@ -98,8 +97,7 @@ typedef struct {
     float ms_scan, ms_bin, ms_windows, ms_verify, ms_output; /* device time per stage */
     float ms_scan_kernel;      /* the reference-scan kernel alone (CUDA events on its stream) */
     float ms_verify_kernel;    /* the verification count pass alone (CUDA events on its stream) */
-    float ms_windows_sweep, ms_lowcx, ms_compact, ms_piece_filter; /* parts of ms_windows */
-    float ms_piece_kernel;     /* the piece-filter kernel alone */
+    float ms_windows_sweep, ms_lowcx, ms_compact; /* parts of ms_windows */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first

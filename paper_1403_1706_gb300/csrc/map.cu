@@ -518,7 +518,8 @@ __device__ void lc_kmerge_serial(const LcParams& L, uint32_t r, uint32_t s, uint
     *ocnt_y = M.cnt;
 }
 
-constexpr int kMergeWarps = 2;  // warps per block of the k-way merge (16 KB of buffers each)
+constexpr int kMergeWarps = 4;  // warps per block of the k-way merge
+constexpr int kMergeBuf = 16;   // ranges buffered per source (8 KB per warp)
 
 // k-way merge, one warp per segment: the counting-filter ranges of the strand and every cluster
 // list are each sorted by start.  Lane j < (number of lists) owns list j, the next lane owns the
@@ -529,7 +530,7 @@ constexpr int kMergeWarps = 2;  // warps per block of the k-way merge (16 KB of 
 __global__ void __launch_bounds__(kMergeWarps * 32)
     lc_kmerge_k(LcParams L, const uint64_t* doff, LcDesc* desc, const uint64_t* off, uint64_t* olo, uint64_t* ohi,
                 uint32_t* ocnt) {
-    __shared__ int64_t blo[kMergeWarps][32][32], bhi[kMergeWarps][32][32];
+    __shared__ int64_t blo[kMergeWarps][32][kMergeBuf], bhi[kMergeWarps][32][kMergeBuf];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < 2 * L.n_list; y += nw) {
@@ -556,12 +557,12 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
             cur = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
             end = cur + L.wcnt[2 * r + s];
         }
-        // the whole warp loads the next (up to) 32 ranges of source j into its buffer
+        // the first kMergeBuf lanes load the next (up to) kMergeBuf ranges of source j into its buffer
         auto refill = [&](uint32_t j) {
             const uint64_t c0 = __shfl_sync(kFull, cur, j), e0 = __shfl_sync(kFull, end, j);
             const int64_t mn = __shfl_sync(kFull, imin, j), mx = __shfl_sync(kFull, imax, j);
             const uint64_t e = c0 + lane;
-            if (e < e0) {
+            if (lane < kMergeBuf && e < e0) {
                 int64_t lo, hi;
                 if (j < nd) {
                     cluster_range(L, e, mn, mx, m, k, &lo, &hi);
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
                 blo[wid][j][lane] = lo;
                 bhi[wid][j][lane] = hi;
             }
-            const uint32_t got = (uint32_t)(e0 - c0 < 32 ? e0 - c0 : 32);
+            const uint32_t got = (uint32_t)(e0 - c0 < kMergeBuf ? e0 - c0 : kMergeBuf);
             if (lane == j) {
                 cnt = got;
                 rd = 0;
@@ -591,11 +592,11 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
             }
             uint64_t key = ~0ull;
             if (lane < S && rd < cnt) key = ((uint64_t)blo[wid][lane][rd] << 5) | lane;
-#pragma unroll
-            for (int x = 16; x > 0; x >>= 1) {
-                const uint64_t other = __shfl_xor_sync(kFull, key, x);
-                key = other < key ? other : key;
-            }
+            // warp minimum of the 64-bit keys: high halves first, then low halves among the ties
+            const uint32_t kh = (uint32_t)(key >> 32);
+            const uint32_t mh = __reduce_min_sync(kFull, kh);
+            const uint32_t ml = __reduce_min_sync(kFull, kh == mh ? (uint32_t)key : 0xFFFFFFFFu);
+            key = ((uint64_t)mh << 32) | ml;
             if (key == ~0ull) break;
             const uint32_t wl = (uint32_t)(key & 31);
             const int64_t lo = (int64_t)(key >> 5);
@@ -619,105 +620,6 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
             ocnt[y] = M.cnt + (M.open ? 1 : 0);
         }
         __syncwarp();
-    }
-}
-
-// ---- piece filter ----------------------------------------------------------------------------
-//
-// Pigeonhole over the pattern, exact: split the pattern into P = floor(m / 8) disjoint 8-base
-// pieces.  An edit breaks at most one piece (a deletion between two pieces breaks none), so an
-// alignment with e <= k edits leaves at least P - k pieces unbroken, and each unbroken piece occurs
-// in the reference inside the aligned text, which for an end in [lo, hi] lies in
-// [lo - (m + k) + 1, hi].  A candidate range whose text holds fewer than P - k of the pieces has no
-// end with distance <= k and is dropped before verification.
-
-struct PieceParams {
-    const uint64_t* cand_key;
-    const uint64_t* cand_hi;
-    uint64_t n_cand;
-    const uint8_t* len;
-    const uint8_t* kk;
-    const uint8_t* codes;
-    const uint64_t* base_off;
-    const uint32_t* packed;
-};
-
-__device__ __forceinline__ uint32_t piece_hash(uint32_t code) { return (code * 0x9E3779B1u) >> 26; }
-
-__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
-#pragma unroll
-    for (int x = 16; x > 0; x >>= 1) v |= __shfl_xor_sync(kFull, v, x);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t warp_or32(uint32_t v) {
-#pragma unroll
-    for (int x = 16; x > 0; x >>= 1) v |= __shfl_xor_sync(kFull, v, x);
-    return v;
-}
-
-constexpr int kPieceWarps = 8;
-
-// One warp per candidate range: lane t < P builds piece t; lanes then take the 8-base windows of
-// the range's text 32 at a time (window starts a .. hi - 7), test them against a 64-bit Bloom
-// word of the pieces not yet found, and mark found pieces.  Stops as soon as P - k are found.
-__global__ void __launch_bounds__(kPieceWarps * 32) piece_filter_k(PieceParams F, uint32_t* keep) {
-    __shared__ uint32_t spc[kPieceWarps][32];
-    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < F.n_cand; x += nw) {
-        const uint64_t key = F.cand_key[x];
-        const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
-        const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)F.cand_hi[x];
-        const int64_t m = F.len[r], k = F.kk[r];
-        const int P = (int)(m >> 3);
-        const int need = P - (int)k;
-        if (need <= 0) {
-            if (lane == 0) keep[x] = 1;
-            continue;
-        }
-        const uint8_t* rd = F.codes + F.base_off[r];
-        uint32_t code = 0;
-        if ((int)lane < P) {
-            for (int u = 0; u < 8; ++u) {
-                const int64_t i = 8 * (int64_t)lane + u;
-                code = (code << 2) | (s == 0 ? rd[i] : 3u - rd[m - 1 - i]);
-            }
-        }
-        spc[wid][lane] = code;
-        uint64_t bloom = warp_or64((int)lane < P ? 1ull << piece_hash(code) : 0ull);
-        __syncwarp();
-        int64_t a = lo - (m + k) + 1;
-        if (a < 0) a = 0;
-        uint32_t found = 0, all = 0;
-        for (int64_t j0 = a; j0 + 7 <= hi; j0 += 32) {
-            const int64_t j = j0 + lane;
-            if (j + 7 <= hi) {
-                const uint64_t w = ((uint64_t)__ldg(F.packed + (j >> 4)) << 32) | __ldg(F.packed + (j >> 4) + 1);
-                const uint32_t c8 = (uint32_t)(w >> (48 - 2 * (j & 15))) & 0xFFFFu;
-                if ((bloom >> piece_hash(c8)) & 1ull)
-                    for (int t = 0; t < P; ++t)
-                        if (spc[wid][t] == c8) found |= 1u << t;
-            }
-            const uint32_t now = warp_or32(found);
-            if (now != all) {
-                all = now;
-                if (__popc(all) >= need) break;
-                // pieces already found can no longer help: take them out of the Bloom word
-                bloom = warp_or64(((int)lane < P && !((all >> lane) & 1u)) ? 1ull << piece_hash(code) : 0ull);
-            }
-        }
-        if (lane == 0) keep[x] = __popc(all) >= need ? 1u : 0u;
-        __syncwarp();
-    }
-}
-
-__global__ void keep_compact_k(uint64_t n, const uint32_t* keep, const uint64_t* pos, const uint64_t* a,
-                               const uint64_t* b, uint64_t* oa, uint64_t* ob) {
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
-        if (!keep[x]) continue;
-        oa[pos[x]] = a[x];
-        ob[pos[x]] = b[x];
     }
 }
 
@@ -1006,6 +908,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     cudaStream_t s = R->stream;
     const uint32_t n_reads = R->n_reads, q = R->q;
     const uint64_t n = ref->n;
+    PN_REQUIRE(R->max_k < 64, PEANUT_UNSUPPORTED, "error budgets above 63 are not supported (max k = %u)", R->max_k);
     Timer tm(s);
     Timer ktm(s);
     cudaEvent_t* kev = ktm.ev;
@@ -1127,7 +1030,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     CandCount cc{wcnt.p, nl ? R->lowcx.p : nullptr, lcpos.p, lcnt.p};
     DBuf<uint64_t> coff((uint64_t)n_reads + 1, s);
     exclusive_scan(cc, ArrayOut<uint64_t>{coff.p}, n_reads, tot.p, s);
-    uint64_t NC = to_host(tot.p, s);
+    const uint64_t NC = to_host(tot.p, s);
     R->cand_key.alloc(NC ? NC : 1, s);
     R->cand_hi.alloc(NC ? NC : 1, s);
     R->n_cand = NC;
@@ -1137,27 +1040,6 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     wlo.reset();
     whi.reset();
     ktm.mark_at(6);
-    // 3d. piece filter over every candidate range, then the kept ranges in the same order
-    if (NC) {
-        DBuf<uint32_t> keep(NC, s);
-        PieceParams F{R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, R->codes.p, R->base_off.p, ref->packed.p};
-        ktm.mark_at(7);
-        piece_filter_k<<<grid_for(NC * 32, kPieceWarps * 32, (unsigned)sm_count() * 16), kPieceWarps * 32, 0, s>>>(
-            F, keep.p);
-        PN_CHECK_LAUNCH();
-        ktm.mark_at(8);
-        DBuf<uint64_t> kpos(NC, s);
-        exclusive_scan(ArrayIn<uint32_t>{keep.p}, ArrayOut<uint64_t>{kpos.p}, NC, tot.p, s);
-        const uint64_t NK = to_host(tot.p, s);
-        DBuf<uint64_t> ck(NK ? NK : 1, s), ch(NK ? NK : 1, s);
-        keep_compact_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(NC, keep.p, kpos.p, R->cand_key.p,
-                                                                                    R->cand_hi.p, ck.p, ch.p);
-        PN_CHECK_LAUNCH();
-        st.candidates_filtered = NC;
-        R->cand_key = std::move(ck);
-        R->cand_hi = std::move(ch);
-        R->n_cand = NC = NK;
-    }
     st.candidates = NC;
     tm.mark();  // 3
 
@@ -1240,8 +1122,6 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
     cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
     cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);
-    cudaEventElapsedTime(&st.ms_piece_filter, kev[6], tm.ev[3]);
-    if (NC) cudaEventElapsedTime(&st.ms_piece_kernel, kev[7], kev[8]);
     R->stats = st;
     return out;
 }

@@ -46,15 +46,13 @@ class DeviceHitsStruct(Structure):
 
 
 class MapStats(Structure):
-    _fields_ = [("hits", c_uint64), ("candidates", c_uint64), ("candidates_filtered", c_uint64),
-                ("candidate_columns", c_uint64),
+    _fields_ = [("hits", c_uint64), ("candidates", c_uint64), ("candidate_columns", c_uint64),
                 ("results", c_uint64), ("lowcx_reads", c_uint64), ("lowcx_ranges", c_uint64),
                 ("scan_retries", c_uint64),
                 ("present_probes", c_uint64), ("candidate_word_columns", c_uint64),
                 ("ms_scan", c_float), ("ms_bin", c_float), ("ms_windows", c_float), ("ms_verify", c_float),
                 ("ms_output", c_float), ("ms_scan_kernel", c_float), ("ms_verify_kernel", c_float),
-                ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float),
-                ("ms_piece_filter", c_float), ("ms_piece_kernel", c_float)]
+                ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -321,3 +321,35 @@ def test_objects_outlive_an_allocator_switch(gpu):
     assert_same_hits(gpu.map(R, gpu.index_reads(R, reads.seq, reads.offsets, 11, k=5)), want)
     assert (gpu.bitvector_columns([b"ACGT"], [b"TTACGTT"])[0].tolist()
             == oracle.semiglobal_column(b"ACGT", b"TTACGTT").tolist())
+
+
+@pytest.mark.parametrize("k", [7, 20, 40])
+def test_large_budgets_span_several_blocks(gpu, k):
+    """Long reads with large error budgets keep several 64-bit blocks of the bit-vector column
+    active at once (Myers' block cut-off starts and drops blocks along the text)."""
+    rng = random.Random(900 + k)
+    ref = rand_seq(rng, 3000)
+    reads = []
+    for _ in range(30):
+        m = rng.choice([130, 192, 200, 250])
+        p = rng.randrange(0, 3000 - m)
+        s = list(ref[p:p + m])
+        for _ in range(rng.randint(0, k)):
+            x = rng.randrange(len(s))
+            op = rng.random()
+            if op < 0.6:
+                s[x] = rng.choice("ACGT")
+            elif op < 0.8:
+                s.insert(x, rng.choice("ACGT"))
+            elif len(s) > 2:
+                del s[x]
+        s = "".join(s)[:m]
+        if rng.random() < 0.5:
+            s = synth.revcomp_ascii(s.encode()).tobytes().decode()
+        reads.append(s)
+    seq, offs = concat(reads)
+    q = max(1, min((len(r) + 1 - 1) // (k + 1) for r in reads))  # t = m + 1 - q (k + 1) >= 1
+    for mode in ("all", "best"):
+        want = oracle.map_bruteforce(ref.encode(), seq, offs, k, mode)
+        got, _ = gpu_map(gpu, ref.encode(), seq, offs, q, k=k, mode=mode)
+        assert_same_hits(got, want)
