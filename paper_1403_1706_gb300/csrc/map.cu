@@ -11,7 +11,9 @@
 // So it suffices to verify, for every window of k + 1 consecutive diagonals holding at least t
 // hits, the end range [d0 + m - 1 - k, d0 + m - 1 + k]; with sorted hit diagonals d_x this is
 // the union over x with d_{x+t-1} - d_x <= k of [d_{x+t-1} + m - 1 - 2k, d_x + m - 1 + k].
-// Overlapping or touching ranges are merged so every maximal run of end positions lies in one.
+// Overlapping or touching ranges are merged so every maximal run of end positions lies in one;
+// ranges less than m + k apart are joined too (the gap holds no end within k edits, and verifying
+// it costs fewer columns than the m + k warm-up columns a separate range needs).
 #include <cstdio>
 #include <mutex>
 
@@ -199,9 +201,10 @@ struct RangeMerger {
         }
         open = false;
     }
+    int64_t join = 1;  // ranges closer than this are verified as one
     __device__ __forceinline__ void add(int64_t l, int64_t h, uint64_t* wlo, uint64_t* whi, uint64_t base,
                                         uint32_t s, uint64_t n) {
-        if (open && l <= hi + 1) {
+        if (open && l <= hi + join) {
             if (h > hi) hi = h;
             return;
         }
@@ -228,6 +231,7 @@ __device__ void window_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const
         const uint32_t b = s == 0 ? 0 : h0, e = s == 0 ? h0 : h;
         RangeMerger mg;
         mg.cnt = total;
+        mg.join = m + k;
         for (uint32_t j0 = b; j0 + T - 1 < e; j0 += 32) {
             const uint32_t j = j0 + lane;
             bool valid = false;
@@ -457,11 +461,12 @@ struct MergeOut {
     int64_t cur_lo = 0, cur_hi = -2;
     bool open = false;
     uint32_t cnt = 0;
+    int64_t join = 1;  // ranges closer than this are verified as one
     // Consumes the next range in increasing start; returns true when a finished range must be
     // written as (wlo, whi).
     __device__ __forceinline__ bool add(int64_t lo, int64_t hi, int64_t* wlo, int64_t* whi) {
         if (lo > hi) return false;  // clipped away
-        if (open && lo <= cur_hi + 1) {
+        if (open && lo <= cur_hi + join) {
             if (hi > cur_hi) cur_hi = hi;
             return false;
         }
@@ -482,6 +487,7 @@ __device__ void lc_kmerge_serial(const LcParams& L, uint32_t r, uint32_t s, uint
     uint64_t w = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]);
     const uint64_t we = w + L.wcnt[2 * r + s];
     MergeOut M;
+    M.join = m + k;
     int64_t a, b;
     while (true) {
         int64_t lo = INT64_MAX, hi = 0;
@@ -583,6 +589,7 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
         };
         for (uint32_t j = 0; j < S; ++j) refill(j);
         MergeOut M;
+        M.join = m + k;
         while (true) {
             unsigned need = __ballot_sync(kFull, lane < S && rd == cnt && cur < end);
             while (need) {
@@ -751,8 +758,51 @@ struct VerifyParams {
     uint8_t* out_dist;
 };
 
+constexpr int kVerifyThreads = 128;
+
+// Myers' block recurrence (the same as Myers<W>) with the match masks of the current pattern in
+// shared memory, one slot per thread: eq(c, w) is read from seq[(c * kMaxWords + w) * blockDim].
+template <int W>
+struct MyersShared {
+    uint64_t Pv[W], Mv[W];
+    const uint64_t* seq;
+    int32_t score;
+    int lastbit;
+
+    __device__ __forceinline__ int32_t step(uint32_t c) {
+        int hin = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t e = seq[(c * kMaxWords + w) * kVerifyThreads];
+            const uint64_t pv = Pv[w], mv = Mv[w];
+            const uint64_t xv = e | mv;
+            if (hin < 0) e |= 1ull;
+            const uint64_t xh = (((e & pv) + pv) ^ pv) | e;
+            uint64_t ph = mv | ~(xh | pv);
+            uint64_t mh = pv & xh;
+            int hout;
+            if (w == W - 1) {
+                hout = (int)((ph >> lastbit) & 1ull) - (int)((mh >> lastbit) & 1ull);
+            } else {
+                hout = (int)(ph >> 63) - (int)(mh >> 63);
+            }
+            ph <<= 1;
+            mh <<= 1;
+            if (hin < 0) mh |= 1ull;
+            else if (hin > 0) ph |= 1ull;
+            Pv[w] = mh | ~(xv | ph);
+            Mv[w] = ph & xv;
+            hin = hout;
+        }
+        score += hin;
+        return score;
+    }
+};
+
+// Verifies one candidate range: columns a .. hi of the pattern's semiglobal matrix, runs of ends
+// with distance <= k, leftmost minimum of each run.  Returns the number of columns.
 template <int W, bool kWrite>
-__device__ void verify_one(const VerifyParams& V, uint64_t x) {
+__device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq) {
     const uint64_t key = V.cand_key[x];
     const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
     const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)V.cand_hi[x];
@@ -760,17 +810,36 @@ __device__ void verify_one(const VerifyParams& V, uint64_t x) {
     const int32_t k = V.kk[r];
     int64_t a = lo - ((int64_t)m + k) + 1;
     if (a < 0) a = 0;
-    Myers<W> M;
-    M.init(V.peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords, m);
-    uint32_t word = __ldg(V.packed + (a >> 4));
+    const uint64_t* pq = V.peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int w = 0; w < W; ++w) seq[(c * kMaxWords + w) * kVerifyThreads] = __ldg(pq + c * kMaxWords + w);
+    MyersShared<W> M;
+    M.seq = seq;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        M.Pv[w] = ~0ull;
+        M.Mv[w] = 0;
+    }
+    M.score = (int32_t)m;
+    M.lastbit = (int)((m - 1) & 63);
+    // text: the current packed word shifted so that the next base sits in its top two bits
+    uint32_t word = __ldg(V.packed + (a >> 4)) << (2 * (uint32_t)(a & 15));
+    uint32_t left = 16 - (uint32_t)(a & 15);
     uint32_t nt = 0;
     uint64_t o = kWrite ? V.toff[x] : 0;
     bool in = false;
     int32_t best = 0;
     int64_t bestj = 0;
     for (int64_t j = a; j <= hi; ++j) {
-        if ((j & 15) == 0) word = __ldg(V.packed + (j >> 4));
-        const uint32_t c = (word >> (30 - 2 * (uint32_t)(j & 15))) & 3u;
+        if (left == 0) {
+            word = __ldg(V.packed + (j >> 4));
+            left = 16;
+        }
+        const uint32_t c = word >> 30;
+        word <<= 2;
+        --left;
         const int32_t d = M.step(c);
         if (j < lo) continue;
         if (d <= k) {
@@ -794,25 +863,39 @@ __device__ void verify_one(const VerifyParams& V, uint64_t x) {
             in = false;
         }
     }
-    if (!kWrite) {
-        V.cnt[x] = nt;
-        atomicAdd(V.columns, (unsigned long long)(hi - a + 1));
-        atomicAdd(V.columns + 1, (unsigned long long)(hi - a + 1) * W);
-    }
+    if (!kWrite) V.cnt[x] = nt;
+    return (uint64_t)(hi - a + 1);
 }
 
 template <bool kWrite>
-__global__ void __launch_bounds__(128) verify_k(VerifyParams V) {
+__global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V) {
+    __shared__ uint64_t s_eq[4 * kMaxWords * kVerifyThreads];
+    uint64_t* seq = s_eq + threadIdx.x;
+    unsigned long long cols = 0, wcols = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < V.n_cand;
          x += (uint64_t)gridDim.x * blockDim.x) {
         if (kWrite && V.cnt[x] <= 2) continue;
         const uint32_t r = (uint32_t)(V.cand_key[x] >> 41);
         const uint32_t W = (V.len[r] + 63) >> 6;
+        uint64_t c = 0;
         switch (W) {
-            case 1: verify_one<1, kWrite>(V, x); break;
-            case 2: verify_one<2, kWrite>(V, x); break;
-            case 3: verify_one<3, kWrite>(V, x); break;
-            default: verify_one<4, kWrite>(V, x); break;
+            case 1: c = verify_one<1, kWrite>(V, x, seq); break;
+            case 2: c = verify_one<2, kWrite>(V, x, seq); break;
+            case 3: c = verify_one<3, kWrite>(V, x, seq); break;
+            default: c = verify_one<4, kWrite>(V, x, seq); break;
+        }
+        cols += c;
+        wcols += c * W;
+    }
+    if (!kWrite) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cols += __shfl_xor_sync(kFull, cols, o);
+            wcols += __shfl_xor_sync(kFull, wcols, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(V.columns, cols);
+            atomicAdd(V.columns + 1, wcols);
         }
     }
 }
@@ -1050,10 +1133,10 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     cols.zero();
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
-    const unsigned gv = grid_for(NC, 128, (unsigned)sm_count() * 32);
+    const unsigned gv = grid_for(NC, kVerifyThreads, (unsigned)sm_count() * 32);
     PN_CUDA(cudaEventRecord(kev[2], s));
     if (NC) {
-        verify_k<false><<<gv, 128, 0, s>>>(V);
+        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V);
         PN_CHECK_LAUNCH();
     }
     PN_CUDA(cudaEventRecord(kev[3], s));
@@ -1077,7 +1160,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         if (NC) {
             inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
             PN_CHECK_LAUNCH();
-            verify_k<true><<<gv, 128, 0, s>>>(V);
+            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V);
             PN_CHECK_LAUNCH();
         }
         tm.mark();  // 4
