@@ -680,12 +680,68 @@ __global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, 
     }
 }
 
-// ---- bit-vector verification (Myers 1999, block form; Section "Validation") ----------------
+// ---- bit-vector verification (Myers 1999 / Hyyro 2003; Section "Validation") ------------------
 //
 // Column j of the semiglobal matrix is held as vertical delta vectors Pv (+1) and Mv (-1), one
-// bit per pattern row, in W 64-bit words.  Rows enter from word 0; the horizontal delta leaving
-// the top row of one word enters the bottom row of the next.  Row 0 has E[0][j] = 0 for every j,
-// so the delta entering word 0 is 0.  Initial column (j = a - 1): E[i][a-1] = i, all Pv set.
+// bit per pattern row, as one W x 64-bit integer (word 0 = rows 1..64).  One column step is Myers'
+// single-word recurrence on that wide integer: Xv = Eq | Mv; Xh = (((Eq & Pv) + Pv) ^ Pv) | Eq with
+// the addition carried across words; Ph = Mv | ~(Xh | Pv); Mh = Pv & Xh; the horizontal delta at
+// row m is bit m-1 of Ph minus that of Mh; Ph and Mh shift up one row with 0 shifted in (row 0
+// has E[0][j] = 0 for every j); Pv = Mh | ~(Xv | Ph); Mv = Ph & Xv.  Initial column (j = a - 1):
+// E[i][a-1] = i, all Pv set, score m.
+
+// s = a + b over W 64-bit words, carries chained.
+template <int W>
+__device__ __forceinline__ void wide_add(const uint64_t (&a)[W], const uint64_t (&b)[W], uint64_t (&s)[W]) {
+    if constexpr (W == 1) {
+        s[0] = a[0] + b[0];
+    } else if constexpr (W == 2) {
+        asm("add.cc.u64 %0, %2, %4;\n\t"
+            "addc.u64 %1, %3, %5;"
+            : "=l"(s[0]), "=l"(s[1])
+            : "l"(a[0]), "l"(a[1]), "l"(b[0]), "l"(b[1]));
+    } else if constexpr (W == 3) {
+        asm("add.cc.u64 %0, %3, %6;\n\t"
+            "addc.cc.u64 %1, %4, %7;\n\t"
+            "addc.u64 %2, %5, %8;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(b[0]), "l"(b[1]), "l"(b[2]));
+    } else {
+        asm("add.cc.u64 %0, %4, %8;\n\t"
+            "addc.cc.u64 %1, %5, %9;\n\t"
+            "addc.cc.u64 %2, %6, %10;\n\t"
+            "addc.u64 %3, %7, %11;"
+            : "=l"(s[0]), "=l"(s[1]), "=l"(s[2]), "=l"(s[3])
+            : "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]), "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]));
+    }
+}
+
+// One column step on the wide vectors; returns the change of E[m][j] (lastbit = (m - 1) % 64,
+// row m lives in word W - 1).
+template <int W>
+__device__ __forceinline__ int wide_step(uint64_t (&Pv)[W], uint64_t (&Mv)[W], const uint64_t (&e)[W], int lastbit) {
+    uint64_t t[W], sum[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) t[w] = e[w] & Pv[w];
+    wide_add<W>(t, Pv, sum);
+    uint64_t ph[W], mh[W], xv[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const uint64_t xh = (sum[w] ^ Pv[w]) | e[w];
+        xv[w] = e[w] | Mv[w];
+        ph[w] = Mv[w] | ~(xh | Pv[w]);
+        mh[w] = Pv[w] & xh;
+    }
+    const int delta = (int)((ph[W - 1] >> lastbit) & 1ull) - (int)((mh[W - 1] >> lastbit) & 1ull);
+#pragma unroll
+    for (int w = W - 1; w >= 0; --w) {
+        const uint64_t p = (ph[w] << 1) | (w ? ph[w - 1] >> 63 : 0ull);
+        const uint64_t q = (mh[w] << 1) | (w ? mh[w - 1] >> 63 : 0ull);
+        Pv[w] = q | ~(xv[w] | p);
+        Mv[w] = p & xv[w];
+    }
+    return delta;
+}
 
 template <int W>
 struct Myers {
@@ -710,31 +766,10 @@ struct Myers {
 
     // Advances one text column with base code c; returns E[m][j].
     __device__ __forceinline__ int32_t step(uint32_t c) {
-        int hin = 0;
+        uint64_t e[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            uint64_t e = c == 0 ? eq[0][w] : c == 1 ? eq[1][w] : c == 2 ? eq[2][w] : eq[3][w];
-            const uint64_t pv = Pv[w], mv = Mv[w];
-            const uint64_t xv = e | mv;
-            if (hin < 0) e |= 1ull;
-            const uint64_t xh = (((e & pv) + pv) ^ pv) | e;
-            uint64_t ph = mv | ~(xh | pv);
-            uint64_t mh = pv & xh;
-            int hout;
-            if (w == W - 1) {
-                hout = (int)((ph >> lastbit) & 1ull) - (int)((mh >> lastbit) & 1ull);
-            } else {
-                hout = (int)(ph >> 63) - (int)(mh >> 63);
-            }
-            ph <<= 1;
-            mh <<= 1;
-            if (hin < 0) mh |= 1ull;
-            else if (hin > 0) ph |= 1ull;
-            Pv[w] = mh | ~(xv | ph);
-            Mv[w] = ph & xv;
-            hin = hout;
-        }
-        score += hin;
+        for (int w = 0; w < W; ++w) e[w] = c == 0 ? eq[0][w] : c == 1 ? eq[1][w] : c == 2 ? eq[2][w] : eq[3][w];
+        score += wide_step<W>(Pv, Mv, e, lastbit);
         return score;
     }
 };
@@ -760,8 +795,8 @@ struct VerifyParams {
 
 constexpr int kVerifyThreads = 128;
 
-// Myers' block recurrence (the same as Myers<W>) with the match masks of the current pattern in
-// shared memory, one slot per thread: eq(c, w) is read from seq[(c * kMaxWords + w) * blockDim].
+// The same recurrence as Myers<W> with the match masks of the current pattern in shared memory,
+// one slot per thread: eq(c, w) is read from seq[(c * kMaxWords + w) * blockDim].
 template <int W>
 struct MyersShared {
     uint64_t Pv[W], Mv[W];
@@ -770,31 +805,10 @@ struct MyersShared {
     int lastbit;
 
     __device__ __forceinline__ int32_t step(uint32_t c) {
-        int hin = 0;
+        uint64_t e[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            uint64_t e = seq[(c * kMaxWords + w) * kVerifyThreads];
-            const uint64_t pv = Pv[w], mv = Mv[w];
-            const uint64_t xv = e | mv;
-            if (hin < 0) e |= 1ull;
-            const uint64_t xh = (((e & pv) + pv) ^ pv) | e;
-            uint64_t ph = mv | ~(xh | pv);
-            uint64_t mh = pv & xh;
-            int hout;
-            if (w == W - 1) {
-                hout = (int)((ph >> lastbit) & 1ull) - (int)((mh >> lastbit) & 1ull);
-            } else {
-                hout = (int)(ph >> 63) - (int)(mh >> 63);
-            }
-            ph <<= 1;
-            mh <<= 1;
-            if (hin < 0) mh |= 1ull;
-            else if (hin > 0) ph |= 1ull;
-            Pv[w] = mh | ~(xv | ph);
-            Mv[w] = ph & xv;
-            hin = hout;
-        }
-        score += hin;
+        for (int w = 0; w < W; ++w) e[w] = seq[(c * kMaxWords + w) * kVerifyThreads];
+        score += wide_step<W>(Pv, Mv, e, lastbit);
         return score;
     }
 };
