@@ -263,8 +263,9 @@ def main():
         n_res = 0
         for bt in batches:
             RB = peanut.index_reads(R, bt["h_seq"], bt["h_off"], q, stream=stream, **kw)
-            h = peanut.map(R, RB)
-            n_res += h.size
+            h = peanut.map_arrays(R, RB)
+            n_res += h.n
+            h.free()
             RB.free()
         return n_res
 

@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "internal.cuh"
@@ -90,6 +92,56 @@ int sm_count() {
 }
 
 void free_device_hits(DeviceHits* H);
+
+// Result arrays live in page-locked host blocks so the device-to-host copy runs at link speed.
+// Freed blocks are kept (up to kPinnedKeep bytes) and reused by later calls of similar size.
+static std::mutex g_pin_mu;
+static std::multimap<size_t, void*> g_pin_free;
+static size_t g_pin_kept = 0;
+constexpr size_t kPinnedKeep = 8ull << 30;
+
+void* host_block_alloc(size_t bytes, size_t* got, bool* pinned) {
+    if (bytes == 0) bytes = 1;
+    {
+        std::lock_guard<std::mutex> lock(g_pin_mu);
+        auto it = g_pin_free.lower_bound(bytes);
+        if (it != g_pin_free.end() && it->first <= 2 * bytes + (64u << 20)) {
+            void* p = it->second;
+            *got = it->first;
+            g_pin_kept -= it->first;
+            g_pin_free.erase(it);
+            *pinned = true;
+            return p;
+        }
+    }
+    const size_t want = ((bytes + (1u << 20) - 1) >> 20) << 20;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, want, cudaHostAllocDefault) == cudaSuccess) {
+        *got = want;
+        *pinned = true;
+        return p;
+    }
+    cudaGetLastError();
+    p = malloc(bytes);
+    *got = bytes;
+    *pinned = false;
+    return p;
+}
+
+void host_block_free(void* p, size_t bytes, bool pinned) {
+    if (!p) return;
+    if (!pinned) {
+        free(p);
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (g_pin_kept + bytes <= kPinnedKeep) {
+        g_pin_free.emplace(bytes, p);
+        g_pin_kept += bytes;
+    } else {
+        cudaFreeHost(p);
+    }
+}
 
 }  // namespace pn
 
@@ -268,19 +320,19 @@ peanut_status peanut_download_hits(const peanut_device_hits* dh, void* stream, p
         const uint64_t n = dh->n;
         H->h.n = n;
         const uint64_t c = n ? n : 1;
-        H->h.read_id = (uint32_t*)malloc(c * sizeof(uint32_t));
-        H->h.strand = (uint8_t*)malloc(c);
-        H->h.end_pos = (uint64_t*)malloc(c * sizeof(uint64_t));
-        H->h.dist = (uint8_t*)malloc(c);
-        if (!H->h.read_id || !H->h.strand || !H->h.end_pos || !H->h.dist) {
-            free(H->h.read_id);
-            free(H->h.strand);
-            free(H->h.end_pos);
-            free(H->h.dist);
+        // one block: end_pos (8-byte aligned first), read_id, strand, dist
+        const size_t bytes = c * (sizeof(uint64_t) + sizeof(uint32_t) + 2);
+        H->block = host_block_alloc(bytes, &H->block_bytes, &H->pinned);
+        if (!H->block) {
             delete H;
             set_error("host allocation failed");
             throw Fail{PEANUT_NO_MEMORY};
         }
+        char* b = static_cast<char*>(H->block);
+        H->h.end_pos = reinterpret_cast<uint64_t*>(b);
+        H->h.read_id = reinterpret_cast<uint32_t*>(b + c * sizeof(uint64_t));
+        H->h.strand = reinterpret_cast<uint8_t*>(b + c * (sizeof(uint64_t) + sizeof(uint32_t)));
+        H->h.dist = H->h.strand + c;
         if (n) {
             PN_CUDA(cudaMemcpyAsync(H->h.read_id, dh->read_id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
             PN_CUDA(cudaMemcpyAsync(H->h.strand, dh->strand, n, cudaMemcpyDeviceToHost, s));
@@ -330,10 +382,7 @@ void peanut_free(void* obj) {
     // hit lists are passed by their public struct; their headers sit just before it
     HostHits* hh = hh_of(static_cast<peanut_hits*>(obj));
     if (hh->magic == kMagicHits) {
-        free(hh->h.read_id);
-        free(hh->h.strand);
-        free(hh->h.end_pos);
-        free(hh->h.dist);
+        host_block_free(hh->block, hh->block_bytes, hh->pinned);
         hh->magic = 0;
         delete hh;
         return;

@@ -189,6 +189,9 @@ struct peanut_reads {
 struct HostHits {
     uint32_t magic = pn::kMagicHits;
     peanut_hits h = {};
+    void* block = nullptr;  // one host block holding the four arrays
+    size_t block_bytes = 0;
+    bool pinned = false;
 };
 
 struct DeviceHits {
@@ -199,6 +202,9 @@ struct DeviceHits {
 };
 
 namespace pn {
+// api.cu: page-locked host blocks for results, kept for reuse after they are freed
+void* host_block_alloc(size_t bytes, size_t* got, bool* pinned);
+void host_block_free(void* p, size_t bytes, bool pinned);
 // index.cu
 void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s);
 RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s);

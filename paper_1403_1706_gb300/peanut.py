@@ -230,6 +230,39 @@ def _hits_to_numpy(hp) -> np.ndarray:
     return out
 
 
+class HostHits:
+    """A peanut_hits result held by the library: numpy views of its four arrays (read, strand,
+    end, dist), valid while this object lives."""
+
+    def __init__(self, hp):
+        self._hp = hp
+        h = hp.contents
+        self.n = int(h.n)
+        n = self.n
+        self.read = np.ctypeslib.as_array(h.read_id, (n,)) if n else np.empty(0, np.uint32)
+        self.strand = np.ctypeslib.as_array(h.strand, (n,)) if n else np.empty(0, np.uint8)
+        self.end = np.ctypeslib.as_array(h.end_pos, (n,)) if n else np.empty(0, np.uint64)
+        self.dist = np.ctypeslib.as_array(h.dist, (n,)) if n else np.empty(0, np.uint8)
+
+    def free(self):
+        if self._hp is not None:
+            load().peanut_free(ctypes.cast(self._hp, c_void_p))
+            self._hp = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def map_arrays(ref: Reference, batch: ReadBatch, mode: str = "all") -> HostHits:
+    """peanut_map without a copy: the library's host arrays as numpy views."""
+    hp = POINTER(Hits)()
+    _check(load().peanut_map(ref.ptr, batch.ptr, MODES[mode], ctypes.byref(hp)))
+    return HostHits(hp)
+
+
 def map(ref: Reference, batch: ReadBatch, mode: str = "all") -> np.ndarray:
     """peanut_map: the batch's hit set on the host."""
     hp = POINTER(Hits)()

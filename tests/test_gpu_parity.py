@@ -353,3 +353,16 @@ def test_large_budgets_span_several_blocks(gpu, k):
         want = oracle.map_bruteforce(ref.encode(), seq, offs, k, mode)
         got, _ = gpu_map(gpu, ref.encode(), seq, offs, q, k=k, mode=mode)
         assert_same_hits(got, want)
+
+
+def test_host_array_views_equal_structured_result(gpu):
+    ref, reads, w = synth.make_workload("uniform_1mbp_10k", n_reads=1500)
+    R = gpu.pack_reference(ref)
+    B = gpu.index_reads(R, reads.seq, reads.offsets, 11, k=5)
+    want = gpu.map(R, B)
+    for _ in range(2):  # the second call reuses a pooled page-locked block
+        h = gpu.map_arrays(R, B)
+        assert h.n == len(want)
+        assert np.array_equal(h.read, want["read"]) and np.array_equal(h.strand, want["strand"])
+        assert np.array_equal(h.end.astype(np.int64), want["end"]) and np.array_equal(h.dist, want["dist"])
+        h.free()
