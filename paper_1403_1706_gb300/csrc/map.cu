@@ -30,6 +30,29 @@ constexpr uint64_t kPosMask40 = (1ull << 40) - 1;
 
 // ---- reference scan ------------------------------------------------------------------------
 
+// L2 cache policies: the Bloom filter is read by every position and should stay resident; index
+// probes touch each line about once.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_stream() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t ld_u64_policy(const uint64_t* ptr, uint64_t pol) {
+    uint64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_u32x2_policy(const uint2* ptr, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ void stage_flush(uint64_t* st, uint32_t cnt, uint64_t* hits, uint64_t cap,
                                             unsigned long long* n_hits) {
     __syncwarp();
@@ -41,26 +64,47 @@ __device__ __forceinline__ void stage_flush(uint64_t* st, uint32_t cnt, uint64_t
     __syncwarp();
 }
 
-// One pass over reference positions p in [0, n - q].  Each lane handles 32 consecutive positions
-// of a chunk; the canonical code of each position is probed in the read index and every
-// occurrence becomes a hit key.  Hits are staged per warp in shared memory and appended to the
-// global buffer with one atomic per stage; rcount[r] counts each read's hits.
+// Algorithm 2 in two stages.
+//
+// probe_ref_k, one pass over reference positions p in [0, n - q]: each lane takes 32 consecutive
+// positions of a chunk, forms the canonical code of each, tests it against the L2-resident Bloom
+// word and, if it passes, probes the index word (I, S).  Positions whose code is indexed are
+// appended as (p << 2 | palindrome << 1 | orientation, S' slot), staged per warp in shared
+// memory and written with one atomic per stage.
+//
+// expand_k, one present position per lane: reads its S' pair, turns every occurrence in O into a
+// hit key (two for a palindromic q-gram), and appends the keys through the same per-warp staging;
+// rcount[r] counts each read's hits.  Splitting the stages keeps many independent loads in flight
+// in both kernels instead of one chain of dependent DRAM loads per position.
+
+__device__ __forceinline__ void stage_flush2(uint64_t* sk, uint32_t* ss, uint32_t cnt, uint64_t* okey,
+                                             uint32_t* oslot, uint64_t cap, unsigned long long* n_out) {
+    __syncwarp();
+    unsigned long long base = 0;
+    if ((threadIdx.x & 31) == 0 && cnt) base = atomicAdd(n_out, (unsigned long long)cnt);
+    base = __shfl_sync(kFull, base, 0);
+    for (uint32_t j = threadIdx.x & 31; j < cnt; j += 32)
+        if (base + j < cap) {
+            __stcs(okey + base + j, sk[j]);
+            __stcs(oslot + base + j, ss[j]);
+        }
+    __syncwarp();
+}
+
 __global__ void __launch_bounds__(kScanBlock, 4)
-    scan_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
-               const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O,
-               const uint8_t* __restrict__ len, const uint64_t* __restrict__ bloom, uint64_t bloom_mask,
-               uint64_t* __restrict__ hits, uint64_t cap, unsigned long long* n_hits, uint32_t* __restrict__ rcount,
-               unsigned long long* n_present) {
-    __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
+    probe_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
+                const uint64_t* __restrict__ bloom, uint64_t bloom_mask, uint64_t* __restrict__ okey,
+                uint32_t* __restrict__ oslot, uint64_t cap, unsigned long long* n_out) {
+    __shared__ uint64_t sk[kScanBlock / 32][kStageCap];
+    __shared__ uint32_t ss[kScanBlock / 32][kStageCap];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t* st = stage[wid];
     uint32_t scnt = 0;
-    uint32_t present = 0;
     const uint64_t npos = n >= q ? n - q + 1 : 0;
     const uint64_t nchunks = (npos + 31) / 32;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t qm = q == 16 ? 0xFFFFFFFFu : (1u << (2 * q)) - 1u;
+    const uint64_t keep = l2_policy_keep(), stream = l2_policy_stream();
     for (uint64_t ch0 = gwarp * 32; ch0 < nchunks; ch0 += nwarps * 32) {
         const uint64_t ch = ch0 + lane;
         const bool active = ch < nchunks;
@@ -74,7 +118,7 @@ __global__ void __launch_bounds__(kScanBlock, 4)
 #pragma unroll 1
         for (int o0 = 0; o0 < 32; o0 += 8) {
             uint32_t cc[8];
-            uint32_t meta[8];  // bit 0: passes the prefilter, bit 1: f_ref, bit 2: palindrome
+            uint32_t meta[8];  // bit 0: valid, bit 1: orientation, bit 2: palindrome
             uint64_t fw[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -86,74 +130,102 @@ __global__ void __launch_bounds__(kScanBlock, 4)
                 const bool valid = active && p0 + o < npos;
                 cc[u] = c;
                 meta[u] = (valid ? 1u : 0u) | (g > h ? 2u : 0u) | (g == h ? 4u : 0u);
-                fw[u] = valid ? __ldg(bloom + ((bloom_hash(c) >> 24) & bloom_mask)) : 0;
+                fw[u] = valid ? ld_u64_policy(bloom + ((bloom_hash(c) >> 24) & bloom_mask), keep) : 0;
             }
             uint2 vv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint64_t fb = bloom_bits(bloom_hash(cc[u]));
                 const bool pass = (meta[u] & 1u) && (fw[u] & fb) == fb;
-                vv[u] = pass ? __ldcs(IS + (cc[u] >> 5)) : make_uint2(0, 0);
+                vv[u] = pass ? ld_u32x2_policy(IS + (cc[u] >> 5), stream) : make_uint2(0, 0);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint32_t c = cc[u];
-                const uint2 v = vv[u];
-                uint32_t kb = 0, ke = 0;
-                if ((v.x >> (c & 31)) & 1u) {
-                    ++present;
-                    const uint32_t slot = v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
-                    kb = __ldcs(Sp + slot);
-                    ke = __ldcs(Sp + slot + 1);
-                }
-                const int64_t p = (int64_t)(p0 + o0 + u);
-                const uint32_t fref = (meta[u] >> 1) & 1u;
-                const bool pal = (meta[u] >> 2) & 1u;
-                while (true) {
-                    const bool has = kb < ke;
-                    if (!__any_sync(kFull, has)) break;
-                    uint64_t key0 = 0, key1 = 0;
-                    int nk = 0;
-                    if (has) {
-                        const uint32_t e = __ldcs(O + kb);
-                        ++kb;
-                        const uint32_t r = e >> 9, fr = (e >> 8) & 1u, i = e & 255u;
-                        const int64_t m = __ldg(len + r);
-                        const int64_t dp = p - (int64_t)i + kDiagBias;
-                        const int64_t dm = p - (m - (int64_t)q - (int64_t)i) + kDiagBias;
-                        const uint64_t rk = (uint64_t)r << 41;
-                        if (pal) {
-                            key0 = rk | (uint64_t)dp;
-                            key1 = rk | (1ull << 40) | (uint64_t)dm;
-                            nk = 2;
-                        } else if (fr == fref) {
-                            key0 = rk | (uint64_t)dp;
-                            nk = 1;
-                        } else {
-                            key0 = rk | (1ull << 40) | (uint64_t)dm;
-                            nk = 1;
-                        }
-                        atomicAdd(rcount + r, (uint32_t)nk);
-                    }
-                    const unsigned b1 = __ballot_sync(kFull, nk >= 1), b2 = __ballot_sync(kFull, nk == 2);
-                    const uint32_t tot = __popc(b1) + __popc(b2);
-                    if (scnt + tot > kStageCap) {
-                        stage_flush(st, scnt, hits, cap, n_hits);
+                const bool present = (vv[u].x >> (c & 31)) & 1u;
+                const unsigned bal = __ballot_sync(kFull, present);
+                if (bal) {
+                    if (scnt + 32 > kStageCap) {
+                        stage_flush2(sk[wid], ss[wid], scnt, okey, oslot, cap, n_out);
                         scnt = 0;
                     }
-                    const uint32_t pos = scnt + __popc(b1 & lanemask_lt()) + __popc(b2 & lanemask_lt());
-                    if (nk >= 1) st[pos] = key0;
-                    if (nk == 2) st[pos + 1] = key1;
-                    scnt += tot;
-                    __syncwarp();
+                    if (present) {
+                        const uint32_t pos = scnt + __popc(bal & lanemask_lt());
+                        sk[wid][pos] = ((p0 + o0 + u) << 2) | ((meta[u] >> 1) & 3u);
+                        ss[wid][pos] = vv[u].y + __popc(vv[u].x & ((1u << (c & 31)) - 1u));
+                    }
+                    scnt += __popc(bal);
                 }
             }
+            __syncwarp();
+        }
+    }
+    stage_flush2(sk[wid], ss[wid], scnt, okey, oslot, cap, n_out);
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+    expand_k(const uint64_t* __restrict__ pkey, const uint32_t* __restrict__ pslot, uint64_t npres, uint32_t q,
+             const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O, const uint8_t* __restrict__ len,
+             uint64_t* __restrict__ hits, uint64_t cap, unsigned long long* n_hits, uint32_t* __restrict__ rcount) {
+    __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t* st = stage[wid];
+    uint32_t scnt = 0;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b0 = gwarp * 32; b0 < npres; b0 += nwarps * 32) {
+        const uint64_t x = b0 + lane;
+        uint32_t kb = 0, ke = 0;
+        uint64_t key = 0;
+        if (x < npres) {
+            key = __ldcs(pkey + x);
+            const uint32_t slot = __ldcs(pslot + x);
+            kb = __ldg(Sp + slot);
+            ke = __ldg(Sp + slot + 1);
+        }
+        const int64_t p = (int64_t)(key >> 2);
+        const uint32_t fref = key & 1u;
+        const bool pal = (key >> 1) & 1u;
+        while (true) {
+            const bool has = kb < ke;
+            if (!__any_sync(kFull, has)) break;
+            uint64_t key0 = 0, key1 = 0;
+            int nk = 0;
+            if (has) {
+                const uint32_t e = __ldg(O + kb);
+                ++kb;
+                const uint32_t r = e >> 9, fr = (e >> 8) & 1u, i = e & 255u;
+                const int64_t m = __ldg(len + r);
+                const int64_t dp = p - (int64_t)i + kDiagBias;
+                const int64_t dm = p - (m - (int64_t)q - (int64_t)i) + kDiagBias;
+                const uint64_t rk = (uint64_t)r << 41;
+                if (pal) {
+                    key0 = rk | (uint64_t)dp;
+                    key1 = rk | (1ull << 40) | (uint64_t)dm;
+                    nk = 2;
+                } else if (fr == fref) {
+                    key0 = rk | (uint64_t)dp;
+                    nk = 1;
+                } else {
+                    key0 = rk | (1ull << 40) | (uint64_t)dm;
+                    nk = 1;
+                }
+                atomicAdd(rcount + r, (uint32_t)nk);
+            }
+            const unsigned b1 = __ballot_sync(kFull, nk >= 1), b2 = __ballot_sync(kFull, nk == 2);
+            const uint32_t tot = __popc(b1) + __popc(b2);
+            if (scnt + tot > kStageCap) {
+                stage_flush(st, scnt, hits, cap, n_hits);
+                scnt = 0;
+            }
+            const uint32_t pos = scnt + __popc(b1 & lanemask_lt()) + __popc(b2 & lanemask_lt());
+            if (nk >= 1) st[pos] = key0;
+            if (nk == 2) st[pos + 1] = key1;
+            scnt += tot;
+            __syncwarp();
         }
     }
     stage_flush(st, scnt, hits, cap, n_hits);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) present += __shfl_xor_sync(kFull, present, o);
-    if (lane == 0) atomicAdd(n_present, (unsigned long long)present);
 }
 
 // ---- binning hits by read ---------------------------------------------------------------
@@ -1012,35 +1084,53 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     peanut_map_stats st = {};
     tm.mark();  // 0
 
-    // 1. reference scan
+    // 1. reference scan: present positions, then their hits
     DBuf<uint32_t> rcount((uint64_t)n_reads + 1, s);
-    DBuf<unsigned long long> nh(2, s);  // [0] hits, [1] present probes
+    DBuf<unsigned long long> nh(2, s);  // [0] present positions, [1] hits
     const double rand_hits = 2.0 * (double)n * (double)R->n_indexed / (double)(1ull << (2 * q));
+    const double rand_present = 2.0 * (double)n * (double)R->n_distinct / (double)(1ull << (2 * q));
+    uint64_t pcap = (uint64_t)(1.5 * rand_present) + 2 * R->n_indexed + (1u << 20);
     uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
+    int per_sm = 0;
+    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k, kScanBlock, 0));
+    const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
+    DBuf<uint64_t> pkey;
+    DBuf<uint32_t> pslot;
+    uint64_t NP = 0;
+    PN_CUDA(cudaEventRecord(kev[0], s));
+    for (int attempt = 0;; ++attempt) {
+        pkey.alloc(pcap, s);
+        pslot.alloc(pcap, s);
+        nh.zero();
+        probe_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->bloom.p, R->bloom_mask, pkey.p,
+                                                 pslot.p, pcap, nh.p);
+        PN_CHECK_LAUNCH();
+        NP = to_host(nh.p, s);
+        if (NP <= pcap) break;
+        st.scan_retries++;
+        pcap = NP + (NP >> 4) + 1024;
+        PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "present-position buffer kept overflowing");
+    }
+    st.present_probes = NP;
     DBuf<uint64_t> hits;
     uint64_t H = 0;
-    int per_sm = 0;
-    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, scan_ref_k, kScanBlock, 0));
-    const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
+    const unsigned gexp = grid_for(NP * 32 / 32, kScanBlock, (unsigned)sm_count() * 8);
     for (int attempt = 0;; ++attempt) {
         hits.alloc(cap, s);
         rcount.zero();
-        nh.zero();
-        PN_CUDA(cudaEventRecord(kev[0], s));
-        scan_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->Sp.p, R->O.p, R->len.p,
-                                                R->bloom.p, R->bloom_mask, hits.p, cap, nh.p, rcount.p, nh.p + 1);
+        PN_CUDA(cudaMemsetAsync(nh.p + 1, 0, sizeof(unsigned long long), s));
+        expand_k<<<gexp, kScanBlock, 0, s>>>(pkey.p, pslot.p, NP, q, R->Sp.p, R->O.p, R->len.p, hits.p, cap, nh.p + 1,
+                                              rcount.p);
         PN_CHECK_LAUNCH();
-        PN_CUDA(cudaEventRecord(kev[1], s));
-        unsigned long long hv[2];
-        PN_CUDA(cudaMemcpyAsync(hv, nh.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
-        PN_CUDA(cudaStreamSynchronize(s));
-        H = hv[0];
-        st.present_probes = hv[1];
+        H = to_host(nh.p + 1, s);
         if (H <= cap) break;
         st.scan_retries++;
         cap = H + (H >> 4) + 1024;
         PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "hit buffer kept overflowing");
     }
+    PN_CUDA(cudaEventRecord(kev[1], s));
+    pkey.reset();
+    pslot.reset();
     st.hits = H;
     tm.mark();  // 1
 
