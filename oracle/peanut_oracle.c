@@ -323,10 +323,13 @@ oracle_hits* oracle_map_filter(const char* R, int64_t n, const char* reads, cons
             }
         }
     }
-    /* 2. scan: every reference q-gram, hits on diagonal d = p - i */
+    /* 2. scan: every reference q-gram, hits on diagonal d = p - i.  The code of the q-gram at p
+     * is that of p - 1 shifted by one base (drop the first, append R[p + q - 1]). */
     vec64* dg = (vec64*)calloc((size_t)(2 * nreads + 1), sizeof(vec64));
+    const uint64_t qmask = (q == 32) ? ~0ULL : ((1ULL << (2 * q)) - 1);
+    uint64_t g = n >= q ? qgram_code(R, q) : 0;
     for (int64_t p = 0; p + q <= n; p++) {
-        uint64_t g = qgram_code(R + p, q);
+        if (p > 0) g = ((g << 2) | (uint64_t)base_code(R[p + q - 1])) & qmask;
         uint64_t x = hash64(g) & (cap - 1);
         while (tab[x].key != UINT64_MAX && tab[x].key != g) x = (x + 1) & (cap - 1);
         if (tab[x].key != g) continue;
