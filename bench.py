@@ -130,16 +130,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_from_profile(kernel_src_sha: str):
-    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "scan_ref_k_traffic.json")
+def traffic_per_unit(name: str, kernel_src_sha: str):
+    """DRAM bytes per unit of work of a kernel, from the committed ncu summary
+    profiles/<name>_traffic.json, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("source_sha256") != kernel_src_sha:
             return None
-        return float(d["dram_bytes_per_full_launch"])
+        return float(d["dram_bytes_per_word_column"])
     except Exception:
         return None
 
@@ -327,8 +327,10 @@ def main():
     v_ops = statistics.mean(34.0 * s["candidate_word_columns"] for s in stats)
     v_ms = statistics.mean(s["ms_verify_kernel"] for s in stats)
     v_ach = v_ops / (v_ms / 1e3) / 1e12
+    per_wc = traffic_per_unit("verify_k", source_sha())
+    v_wc = statistics.mean(s["candidate_word_columns"] for s in stats)
     roof = {"bound": "alu", "achieved": v_ach, "peak": int_peak_tops, "unit": "TOP/s", "frac": v_ach / int_peak_tops,
-            "traffic": None, "kernel": "verify_k (count pass)",
+            "traffic": per_wc * v_wc if per_wc is not None else None, "kernel": "verify_k (count pass)",
             "algorithmic_int32_ops_per_launch": v_ops, "avg_launch_ms": v_ms,
             "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2070 MHz"}
     per_launch = [n_ref * (0.25 + 8.0) + s["present_probes"] * 8.0 + s["hits"] * (4.0 + 1.0 + 8.0) for s in stats]
@@ -336,7 +338,7 @@ def main():
     avg_ms = statistics.mean(s["ms_scan_kernel"] for s in stats)
     achieved = algo_bytes / (avg_ms / 1e3) / 1e9
     roof_scan = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                 "traffic": traffic_from_profile(source_sha()), "kernel": "scan_ref_k",
+                 "traffic": None, "kernel": "probe_ref_k + expand_k",
                  "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ms, "peak_source": peak_kind}
 
     cpu = None
