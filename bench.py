@@ -10,8 +10,10 @@ device-resident batches of 2^20 reads, q = 16, k = 5, all-hits mode.  One step m
           peanut_map_device), timed with CUDA events on the mapping stream.
   e2e   : reads/s through the host API (peanut_index_reads from pinned host memory +
           peanut_map returning host arrays), host<->device copies inside the timed region.
-  roofline : the reference-scan kernel (the dominant kernel), algorithmic bytes per launch over
-          its CUDA-event duration, against the measured HBM copy bandwidth.
+  roofline : the verification kernel (the largest launch-list share), algorithmic INT32
+          operations per launch over its CUDA-event duration, against the INT32 issue peak derived
+          from the SM count and clock; roofline_scan: the two reference-scan kernels, algorithmic
+          bytes per launch against the measured HBM copy bandwidth.
   cpu_baseline : the CPU oracle on a bounded sample of the same workload (see --help).
 
 Launch: `python bench.py [--gpus N --steps K --warmup W]`; for N > 1 under torchrun, each rank
@@ -275,13 +277,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_1403_1706_gb300.shard import max_over_ranks, sum_over_ranks
+    units = sum_over_ranks(reads.n, device="cuda")  # every rank maps its own read set
+    bases = sum_over_ranks(reads.seq.size, device="cuda")
 
     t0 = time.time()
     for _ in range(args.warmup):
@@ -300,8 +298,8 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = peanut.kernel_launches() - l0
-    ms = max_over_ranks(ev0.elapsed_time(ev1)) / args.steps
-    value = world * reads.n / (ms / 1e3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
+    value = units / (ms / 1e3)
     clocks = clk.summary()
 
     # end to end through the host API
@@ -314,9 +312,9 @@ def main():
             n_res_h = step_host()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        ems = max_over_ranks(e0.elapsed_time(e1), device="cuda") / args.steps
         h2d = sum(int(bt["h_seq"].nbytes) + int(bt["h_off"].nbytes) for bt in batches)
-        e2e = {"value": world * reads.n / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems}
 
     # rooflines: the verification count pass (largest launch-list share; integer-ALU bound) and the
@@ -360,7 +358,7 @@ def main():
                              "index (> 129 MB L2)"},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "roofline_scan": roof_scan, "cpu_baseline": cpu,
-            "results_per_step": int(n_res), "bases_per_s": world * int(reads.seq.size) / (ms / 1e3),
+            "results_per_step": int(n_res), "bases_per_s": bases / (ms / 1e3),
             "stage_ms_per_batch": stage,
             "hits_per_batch": statistics.mean(s["hits"] for s in stats),
             "candidates_per_batch": statistics.mean(s["candidates"] for s in stats),
