@@ -79,7 +79,13 @@ typedef struct {
     uint32_t freq_cap;   /* a canonical q-gram occurring more than freq_cap times in the
                             reference is not indexed; reads containing such q-grams are verified
                             around every occurrence cluster instead (exact either way).
-                            0 = default (256) */
+                            0 = default: max(256, 8 x the expected count 2 n / 4^q of a
+                            canonical q-gram in a uniform reference of n bases) */
+    uint32_t stride;     /* index only the q-grams at read offsets 0, stride, 2 stride, ...;
+                            the count threshold becomes the number of them an alignment with k
+                            edits keeps intact (Section "The q-group index", q-gram lemma, with
+                            at most ceil(q / stride) sampled q-grams touched per edit).  Exact
+                            for any stride the reads admit; 0 or 1 = every offset, 1..64 */
     void* stream;        /* cudaStream_t for all device work of the batch */
 } peanut_params;
 
@@ -98,6 +104,7 @@ typedef struct {
     float ms_scan_kernel;      /* the reference-scan kernel alone (CUDA events on its stream) */
     float ms_verify_kernel;    /* the verification count pass alone (CUDA events on its stream) */
     float ms_windows_sweep, ms_lowcx, ms_compact; /* parts of ms_windows */
+    float ms_probe_kernel;     /* the probe half of the reference scan (present positions) */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
@@ -223,6 +230,92 @@ peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pa
 peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat,
                                                const char* d_txt, const uint64_t* d_txt_off, int32_t* d_out,
                                                void* stream);
+
+/* ---- batched and served mapping ------------------------------------------------------------
+ *
+ * An engine maps many read sets ("submissions") against one resident reference.  The paper
+ * fixes one q and one batch per kernel sequence, with reads strided by a common length; the
+ * engine runs the same per-batch path (index, scan, windows, verification, strata) over
+ * launches it forms itself:
+ *   - every read belongs to the class of the largest q its length and budget admit (the q-gram
+ *     lemma threshold m + 1 - q(k + 1) >= 1, Section "The q-group index"), so reads of uneven
+ *     length share launches only with reads that admit the same q;
+ *   - reads of a class are coalesced across submissions, in submission order, into launches of
+ *     up to max_reads reads, sized so that the engine's device memory stays within its budget;
+ *   - up to `executors` launches are in flight at once, each on its own CUDA stream and host
+ *     thread, so one launch's memory-bound reference scan overlaps another's ALU-bound
+ *     verification; a submission is admitted (its reads copied to the device) when its
+ *     footprint fits next to the work in flight ("admission by free HBM");
+ *   - with autotune, the first launch of each class is mapped once per candidate setting
+ *     (q and q - 1, sampling strides 1..4 that every length of the class admits) and the setting
+ *     with the lowest predicted time per read at full launch size is used from then on;
+ *   - each submission's hits are renumbered to its own read ids and sorted on the device,
+ *     reduced to the best stratum if asked, and returned in one host hit list.
+ * A read's hits depend only on the read, its budget and the reference, so a submission's
+ * result is the same whether it is mapped alone, with peanut_map, or in any mix. */
+typedef struct peanut_engine peanut_engine;
+
+typedef struct {
+    uint32_t k_fixed;     /* error budget of every read; UINT32_MAX = derive from k_permille */
+    uint32_t k_permille;  /* k = ceil(length * k_permille / 1000) when k_fixed == UINT32_MAX */
+    uint32_t executors;   /* launches in flight at once, 1..4 (0 = 2) */
+    uint32_t max_reads;   /* reads per launch at most, 1 .. 2^23 (0 = 2^22) */
+    uint32_t autotune;    /* 1 = pick (q, stride) per class by timing its first launch */
+    uint32_t fixed_q;     /* 0 = per class; else every read is mapped with this q (1..16) */
+    uint64_t hbm_budget;  /* device bytes the engine may hold (0 = 90 % of the free memory at
+                             creation, less 4 GiB) */
+} peanut_engine_params;
+
+/* Per-class record of an engine (peanut_engine_get_stats). */
+typedef struct {
+    uint32_t q_class;     /* the largest q the class's reads admit */
+    uint32_t q, stride;   /* the setting in use */
+    uint32_t freq_cap;
+    uint64_t launches, reads;
+    uint64_t bytes_per_read; /* measured device footprint per read of a launch */
+    float tuned_ms_per_mread; /* autotune: predicted ms per 10^6 reads at full launch size */
+    uint32_t tune_candidates; /* settings timed by the autotuner */
+} peanut_engine_class;
+
+typedef struct {
+    uint64_t submissions, completed, reads, launches, tuning_launches;
+    uint64_t hbm_budget, hbm_reserved_peak;
+    uint32_t n_classes;
+    peanut_engine_class cls[16];
+} peanut_engine_stats;
+
+/* Creates an engine over a resident reference (which must outlive it) and starts its executor
+ * threads.  Errors: INVALID_ARG (bad reference or parameters), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_engine_create(const peanut_ref* ref, const peanut_engine_params* p, peanut_engine** out);
+
+/* Queues a submission of host reads (layout as in peanut_index_reads; n_reads 1 .. 2^24) in
+ * mode 0 (all hits) or 1 (best stratum) and returns its ticket at once.  seqs and offsets are
+ * read when the submission is admitted: they must stay valid and unchanged until
+ * peanut_engine_wait has returned its result.  Lengths, bases and thresholds are checked at
+ * admission; a bad submission fails alone (its wait returns the error).
+ * Errors: INVALID_ARG (bad engine, NULL pointer, n_reads or mode out of range). */
+peanut_status peanut_engine_submit(peanut_engine* e, const char* seqs, const uint64_t* offsets,
+                                   uint32_t n_reads, int mode, uint64_t* ticket);
+
+/* As peanut_engine_submit with the reads already in device memory (d_offsets: n_reads + 1
+ * uint64 offsets into d_seqs, total_bases bytes).  The caller's writes to them must be complete
+ * (stream synchronized) before the call, and the buffers stay valid until the wait returns. */
+peanut_status peanut_engine_submit_device(peanut_engine* e, const char* d_seqs, const uint64_t* d_offsets,
+                                          uint32_t n_reads, uint64_t total_bases, int mode, uint64_t* ticket);
+
+/* Waits up to timeout_ms (negative = without limit) for a submission.  On success *out is its
+ * host hit list (read ids are the submission's own, sorted by (read, strand, end)), released
+ * with peanut_free, and the ticket is consumed.  Returns TIMEOUT (ticket kept, *out NULL) if the
+ * submission is still running, or the submission's own error (ticket consumed).
+ * Errors: INVALID_ARG (bad engine or unknown ticket), TIMEOUT, and any error of the mapping. */
+peanut_status peanut_engine_wait(peanut_engine* e, uint64_t ticket, int64_t timeout_ms, peanut_hits** out);
+
+/* Counters and per-class settings of an engine. */
+peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out);
+
+/* An engine is released with peanut_free (from a thread not waiting on it): the launches in
+ * flight complete, submissions not yet returned by peanut_engine_wait are discarded, and its
+ * threads and streams end. */
 
 #ifdef __cplusplus
 }

@@ -143,6 +143,46 @@ void host_block_free(void* p, size_t bytes, bool pinned) {
     }
 }
 
+HostHits* download_hits(const peanut_device_hits& dh, cudaStream_t s) {
+    HostHits* H = new HostHits();
+    const uint64_t n = dh.n;
+    H->h.n = n;
+    const uint64_t c = n ? n : 1;
+    // one block: end_pos (8-byte aligned first), read_id, strand, dist
+    const size_t bytes = c * (sizeof(uint64_t) + sizeof(uint32_t) + 2);
+    H->block = host_block_alloc(bytes, &H->block_bytes, &H->pinned);
+    if (!H->block) {
+        delete H;
+        set_error("host allocation failed");
+        throw Fail{PEANUT_NO_MEMORY};
+    }
+    char* b = static_cast<char*>(H->block);
+    H->h.end_pos = reinterpret_cast<uint64_t*>(b);
+    H->h.read_id = reinterpret_cast<uint32_t*>(b + c * sizeof(uint64_t));
+    H->h.strand = reinterpret_cast<uint8_t*>(b + c * (sizeof(uint64_t) + sizeof(uint32_t)));
+    H->h.dist = H->h.strand + c;
+    try {
+        if (n) {
+            PN_CUDA(cudaMemcpyAsync(H->h.read_id, dh.read_id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.strand, dh.strand, n, cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.end_pos, dh.end_pos, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+            PN_CUDA(cudaMemcpyAsync(H->h.dist, dh.dist, n, cudaMemcpyDeviceToHost, s));
+        }
+        PN_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        free_host_hits(H);
+        throw;
+    }
+    return H;
+}
+
+void free_host_hits(HostHits* H) {
+    if (!H) return;
+    host_block_free(H->block, H->block_bytes, H->pinned);
+    H->magic = 0;
+    delete H;
+}
+
 }  // namespace pn
 
 using namespace pn;
@@ -203,11 +243,57 @@ uint64_t peanut_ref_length(const peanut_ref* ref) {
     return ref && ref->magic == kMagicRef ? ref->n : 0;
 }
 
+
+}  // extern "C"
+
+namespace pn {
+
 static void check_params(const peanut_params* p) {
     PN_REQUIRE(p, PEANUT_INVALID_ARG, "NULL params");
     PN_REQUIRE(p->q >= 1 && p->q <= 16, PEANUT_UNSUPPORTED, "q = %u outside 1..16", p->q);
     PN_REQUIRE(p->k_fixed != 0xFFFFFFFFu || p->k_permille <= 1000, PEANUT_INVALID_ARG, "k_permille > 1000");
+    PN_REQUIRE(p->stride <= 64, PEANUT_INVALID_ARG, "stride = %u outside 0..64", p->stride);
 }
+
+peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets, uint32_t n_reads,
+                          uint64_t total, const peanut_params* p) {
+    PN_REQUIRE(ref && ref->magic == kMagicRef, PEANUT_INVALID_ARG, "bad reference");
+    check_params(p);
+    PN_REQUIRE(n_reads >= 1 && n_reads <= kMaxReads, PEANUT_INVALID_ARG, "n_reads = %u outside 1..2^23", n_reads);
+    cudaStream_t s = (cudaStream_t)p->stream;
+    const uint32_t cap = p->freq_cap ? p->freq_cap : default_freq_cap(ref->n, p->q);
+    peanut_ref* mref = const_cast<peanut_ref*>(ref);
+    std::shared_ptr<RefPrep> prep;
+    {
+        std::lock_guard<std::mutex> lock(mref->prep_mu);
+        if (!mref->prep[p->q] || mref->prep[p->q]->cap != cap) {
+            std::shared_ptr<RefPrep> P(prepare_reference(ref, p->q, cap, s), free_prep);
+            PN_CUDA(cudaStreamSynchronize(s));
+            P->rehome();
+            mref->prep[p->q] = P;
+        }
+        prep = mref->prep[p->q];
+    }
+    peanut_reads* R = new peanut_reads();
+    try {
+        R->prep = prep;
+        R->ref = ref;
+        R->stream = s;
+        R->q = p->q;
+        R->n_reads = n_reads;
+        R->freq_cap = cap;
+        R->total_bases = total;
+        index_reads(R, d_seqs, d_offsets, p->k_fixed, p->k_permille, p->stride ? p->stride : 1);
+    } catch (...) {
+        delete R;
+        throw;
+    }
+    return R;
+}
+
+}  // namespace pn
+
+extern "C" {
 
 static peanut_status index_common(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets,
                                   uint32_t n_reads, uint64_t total, const peanut_params* p, peanut_reads** out,
@@ -217,39 +303,17 @@ static peanut_status index_common(const peanut_ref* ref, const char* d_seqs, con
         check_params(p);
         PN_REQUIRE(n_reads >= 1 && n_reads <= kMaxReads, PEANUT_INVALID_ARG, "n_reads = %u outside 1..2^23", n_reads);
         *out = nullptr;
-        cudaStream_t s = (cudaStream_t)p->stream;
-        const uint32_t cap = p->freq_cap ? p->freq_cap : kDefaultFreqCap;
-        peanut_ref* mref = const_cast<peanut_ref*>(ref);
-        if (!mref->prep[p->q] || mref->prep[p->q]->cap != cap) {
-            if (mref->prep[p->q]) {
-                free_prep(mref->prep[p->q]);
-                mref->prep[p->q] = nullptr;
-            }
-            mref->prep[p->q] = prepare_reference(ref, p->q, cap, s);
+        if (host_input) {
+            cudaStream_t s = (cudaStream_t)p->stream;
+            DBuf<char> ds(total ? total : 1, s);
+            DBuf<uint64_t> doff((uint64_t)n_reads + 1, s);
+            if (total) PN_CUDA(cudaMemcpyAsync(ds.p, h_seqs, total, cudaMemcpyHostToDevice, s));
+            PN_CUDA(cudaMemcpyAsync(doff.p, h_offsets, ((uint64_t)n_reads + 1) * sizeof(uint64_t),
+                                    cudaMemcpyHostToDevice, s));
+            *out = index_batch(ref, ds.p, doff.p, n_reads, total, p);
+        } else {
+            *out = index_batch(ref, d_seqs, d_offsets, n_reads, total, p);
         }
-        peanut_reads* R = new peanut_reads();
-        try {
-            R->ref = ref;
-            R->stream = s;
-            R->q = p->q;
-            R->n_reads = n_reads;
-            R->freq_cap = cap;
-            R->total_bases = total;
-            if (host_input) {
-                DBuf<char> ds(total ? total : 1, s);
-                DBuf<uint64_t> doff((uint64_t)n_reads + 1, s);
-                if (total) PN_CUDA(cudaMemcpyAsync(ds.p, h_seqs, total, cudaMemcpyHostToDevice, s));
-                PN_CUDA(cudaMemcpyAsync(doff.p, h_offsets, ((uint64_t)n_reads + 1) * sizeof(uint64_t),
-                                        cudaMemcpyHostToDevice, s));
-                index_reads(R, ds.p, doff.p, p->k_fixed, p->k_permille);
-            } else {
-                index_reads(R, d_seqs, d_offsets, p->k_fixed, p->k_permille);
-            }
-        } catch (...) {
-            delete R;
-            throw;
-        }
-        *out = R;
     });
 }
 
@@ -315,32 +379,7 @@ peanut_status peanut_download_hits(const peanut_device_hits* dh, void* stream, p
     return guarded([&] {
         PN_REQUIRE(dh && out && dh_of(dh)->magic == kMagicDHits, PEANUT_INVALID_ARG, "bad device hits");
         *out = nullptr;
-        cudaStream_t s = (cudaStream_t)stream;
-        HostHits* H = new HostHits();
-        const uint64_t n = dh->n;
-        H->h.n = n;
-        const uint64_t c = n ? n : 1;
-        // one block: end_pos (8-byte aligned first), read_id, strand, dist
-        const size_t bytes = c * (sizeof(uint64_t) + sizeof(uint32_t) + 2);
-        H->block = host_block_alloc(bytes, &H->block_bytes, &H->pinned);
-        if (!H->block) {
-            delete H;
-            set_error("host allocation failed");
-            throw Fail{PEANUT_NO_MEMORY};
-        }
-        char* b = static_cast<char*>(H->block);
-        H->h.end_pos = reinterpret_cast<uint64_t*>(b);
-        H->h.read_id = reinterpret_cast<uint32_t*>(b + c * sizeof(uint64_t));
-        H->h.strand = reinterpret_cast<uint8_t*>(b + c * (sizeof(uint64_t) + sizeof(uint32_t)));
-        H->h.dist = H->h.strand + c;
-        if (n) {
-            PN_CUDA(cudaMemcpyAsync(H->h.read_id, dh->read_id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-            PN_CUDA(cudaMemcpyAsync(H->h.strand, dh->strand, n, cudaMemcpyDeviceToHost, s));
-            PN_CUDA(cudaMemcpyAsync(H->h.end_pos, dh->end_pos, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-            PN_CUDA(cudaMemcpyAsync(H->h.dist, dh->dist, n, cudaMemcpyDeviceToHost, s));
-        }
-        PN_CUDA(cudaStreamSynchronize(s));
-        *out = &H->h;
+        *out = &download_hits(*dh, (cudaStream_t)stream)->h;
     });
 }
 
@@ -366,10 +405,13 @@ void peanut_free(void* obj) {
     if (magic == kMagicRef) {
         peanut_ref* r = static_cast<peanut_ref*>(obj);
         cudaStreamSynchronize(r->stream);
-        for (auto& p : r->prep)
-            if (p) free_prep(p);
+        for (auto& p : r->prep) p.reset();
         r->magic = 0;
         delete r;
+        return;
+    }
+    if (magic == kMagicEngine) {
+        destroy_engine(static_cast<peanut_engine*>(obj));
         return;
     }
     if (magic == kMagicReads) {
@@ -382,9 +424,7 @@ void peanut_free(void* obj) {
     // hit lists are passed by their public struct; their headers sit just before it
     HostHits* hh = hh_of(static_cast<peanut_hits*>(obj));
     if (hh->magic == kMagicHits) {
-        host_block_free(hh->block, hh->block_bytes, hh->pinned);
-        hh->magic = 0;
-        delete hh;
+        free_host_hits(hh);
         return;
     }
     DeviceHits* dh = dh_of(static_cast<peanut_device_hits*>(obj));

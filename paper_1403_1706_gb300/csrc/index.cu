@@ -4,7 +4,9 @@
 // with its first base most significant.  The index is Algorithm 1 run over the CANONICAL code
 // c = min(g, revcomp(g)) of every read q-gram, so one index serves both strands; each
 // occurrence records whether the read holds c itself or its reverse complement.
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "prims.cuh"
 
@@ -13,8 +15,11 @@ namespace pn {
 __constant__ uint8_t kCodeLut[256];
 
 static void init_lut() {
-    static bool done = false;
-    if (done) return;
+    static std::mutex mu;
+    static std::atomic<bool> done{false};
+    if (done.load()) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.load()) return;
     uint8_t lut[256];
     for (int i = 0; i < 256; ++i) lut[i] = 0xFF;
     lut['A'] = 0;
@@ -176,6 +181,15 @@ __global__ void cluster_write_k(const uint64_t* occ, uint64_t n, const uint32_t*
 
 void free_prep(RefPrep* p) { delete p; }
 
+// Default frequency cap: eight times the expected occurrences of a canonical q-gram in a uniform
+// reference of this length (both strands), and at least 256, so that short q-grams on long
+// references are not all declared frequent.
+uint32_t default_freq_cap(uint64_t ref_len, uint32_t q) {
+    const double expect = 2.0 * (double)ref_len / (double)(1ull << (2 * q));
+    const double cap = 8.0 * expect;
+    return cap > (double)kDefaultFreqCap ? (cap < 4e9 ? (uint32_t)cap : 4000000000u) : kDefaultFreqCap;
+}
+
 RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s) {
     RefPrep* P = new RefPrep();
     try {
@@ -276,9 +290,18 @@ __device__ __forceinline__ int phi_lookup(uint32_t c, const uint32_t* __restrict
     return lo < n && codes[lo] == c ? (int)lo : -1;
 }
 
+// Sampled offsets 0, s, 2s, ... below nq; an edit touches at most ceil(q / s) of their q-grams,
+// and k windows of q offsets can hold at most k ceil(q / s) of them (packed from offset 0), so at
+// least the returned number stay intact (the q-gram lemma for s = 1).
+__host__ __device__ __forceinline__ int64_t sampled_threshold(uint32_t nq, uint32_t q, uint32_t k, uint32_t s) {
+    const int64_t na = (nq + s - 1) / s;
+    const int64_t cover = (int64_t)k * ((q + s - 1) / s);
+    return na - (cover < na ? cover : na);
+}
+
 __global__ void read_meta_k(const uint64_t* __restrict__ off, uint32_t n_reads, uint64_t total,
-                            uint32_t q, uint32_t k_fixed, uint32_t k_permille, uint8_t* len, uint8_t* kk,
-                            uint64_t* nq, uint32_t* status, uint32_t* maxes) {
+                            uint32_t q, uint32_t stride, uint32_t k_fixed, uint32_t k_permille, uint8_t* len,
+                            uint8_t* kk, uint64_t* nq, uint32_t* status, uint32_t* maxes) {
     const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_reads) return;
     const uint64_t a = off[r], b = off[r + 1];
@@ -292,7 +315,7 @@ __global__ void read_meta_k(const uint64_t* __restrict__ off, uint32_t n_reads, 
     const uint32_t m = (uint32_t)(b - a);
     uint64_t k = k_fixed != 0xFFFFFFFFu ? k_fixed : ((uint64_t)m * k_permille + 999) / 1000;
     const int64_t t = (int64_t)m + 1 - (int64_t)q * (int64_t)(k + 1);
-    if (t < 1 || k > 255) {
+    if (t < 1 || k > 255 || (stride > 1 && sampled_threshold(m - q + 1, q, (uint32_t)k, stride) < 1)) {
         atomicOr(status, kStBadThreshold);
         k = 0;
     }
@@ -324,7 +347,7 @@ __global__ void read_codes_k(const uint8_t* __restrict__ ascii, uint64_t total, 
 __global__ void __launch_bounds__(256)
     read_qgrams_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ off,
                   const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk,
-                  const uint64_t* __restrict__ qoff, uint32_t n_reads, uint32_t q,
+                  const uint64_t* __restrict__ qoff, uint32_t n_reads, uint32_t q, uint32_t stride,
                   const uint32_t* __restrict__ filter, uint32_t shift, const uint32_t* __restrict__ phi,
                   uint32_t n_phi, uint32_t* tcode, uint32_t* tpay, uint64_t* fent, uint32_t* fcnt,
                   uint16_t* thr, uint8_t* lowcx, uint32_t* lowcx_list, uint32_t* n_lowcx) {
@@ -336,15 +359,17 @@ __global__ void __launch_bounds__(256)
         const uint8_t* rd = codes + off[r];
         const uint64_t qb = qoff[r];
         uint32_t nf = 0;
-        uint32_t fmask[8];
+        uint32_t imask[8];  // offsets whose q-gram is indexed (sampled and not frequent)
 #pragma unroll
-        for (int t = 0; t < 8; ++t) fmask[t] = 0;
+        for (int t = 0; t < 8; ++t) imask[t] = 0;
 #pragma unroll 1
         for (uint32_t t = 0; t * 32 < nq; ++t) {
             const uint32_t i = t * 32 + lane;
-            bool freq = false;
+            bool freq = false, indexed = false;
             uint64_t fe = 0;
-            if (i < nq) {
+            if (i < nq && i % stride != 0) {
+                tcode[qb + i] = kSentinel;
+            } else if (i < nq) {
                 uint32_t g = 0;
                 for (uint32_t x = 0; x < q; ++x) g = (g << 2) | rd[i + x];
                 const uint32_t h = revcomp_code(g, q);
@@ -354,6 +379,7 @@ __global__ void __launch_bounds__(256)
                 if (ph < 0) {
                     tcode[qb + i] = c;
                     tpay[qb + i] = (r << 9) | (f << 8) | i;
+                    indexed = true;
                 } else {
                     tcode[qb + i] = kSentinel;
                     freq = true;
@@ -363,20 +389,21 @@ __global__ void __launch_bounds__(256)
             const unsigned bal = __ballot_sync(kFull, freq);
             if (freq) fent[qb + nf + __popc(bal & lanemask_lt())] = fe;
             nf += __popc(bal);
-            if (t < 8) fmask[t] = bal;
+            const unsigned ibal = __ballot_sync(kFull, indexed);
+            if (t < 8) imask[t] = ibal;
         }
         if (lane == 0) {
-            const int32_t tlemma = (int32_t)m + 1 - (int32_t)(q * (k + 1));
+            // intact sampled q-grams guaranteed by the lemma (all offsets when stride = 1)
+            const int32_t tsampled = (int32_t)sampled_threshold(nq, q, k, stride);
             fcnt[r] = nf;
             if (nf == 0) {
-                thr[r] = (uint16_t)tlemma;
+                thr[r] = (uint16_t)tsampled;
                 lowcx[r] = 0;
             } else {
-                // maximum coverage of the non-frequent offsets by k windows of q offsets
+                // maximum coverage of the indexed offsets by k windows of q offsets
                 uint16_t pre[257], f0[257], f1[257];
                 pre[0] = 0;
-                for (uint32_t x = 0; x < nq; ++x)
-                    pre[x + 1] = pre[x] + (((fmask[x >> 5] >> (x & 31)) & 1u) ? 0 : 1);
+                for (uint32_t x = 0; x < nq; ++x) pre[x + 1] = pre[x] + ((imask[x >> 5] >> (x & 31)) & 1u);
                 for (uint32_t x = 0; x <= nq; ++x) f0[x] = 0;
                 uint16_t* prev = f0;
                 uint16_t* cur = f1;
@@ -396,7 +423,7 @@ __global__ void __launch_bounds__(256)
                     thr[r] = (uint16_t)tstar;
                     lowcx[r] = 0;
                 } else {
-                    thr[r] = (uint16_t)tlemma;
+                    thr[r] = (uint16_t)tsampled;
                     lowcx[r] = 1;
                     lowcx_list[atomicAdd(n_lowcx, 1u)] = r;
                 }
@@ -480,7 +507,7 @@ __global__ void peq_k(const uint8_t* __restrict__ codes, const uint64_t* __restr
 }
 
 void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
-                 uint32_t k_permille) {
+                 uint32_t k_permille, uint32_t stride) {
     init_lut();
     cudaStream_t s = R->stream;
     const uint32_t n = R->n_reads, q = R->q;
@@ -493,8 +520,9 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     DBuf<uint64_t> nq(n, s);
     DBuf<uint32_t> status(3, s);  // [0] status, [1] max len, [2] max k
     status.zero();
-    read_meta_k<<<grid_for(n, 256), 256, 0, s>>>(R->base_off.p, n, total, q, k_fixed, k_permille, R->len.p,
-                                                  R->kk.p, nq.p, status.p, status.p + 1);
+    R->stride = stride;
+    read_meta_k<<<grid_for(n, 256), 256, 0, s>>>(R->base_off.p, n, total, q, stride, k_fixed, k_permille,
+                                                  R->len.p, R->kk.p, nq.p, status.p, status.p + 1);
     PN_CHECK_LAUNCH();
     R->codes.alloc(total ? total : 1, s);
     read_codes_k<<<grid_for(total, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
@@ -507,7 +535,8 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
                "read offsets must ascend within the sequence buffer and give lengths 1..%d", kMaxReadLen);
     PN_REQUIRE(!(st[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T");
     PN_REQUIRE(!(st[0] & kStBadThreshold), PEANUT_INVALID_ARG,
-               "a read violates the q-gram lemma threshold m + 1 - q(k + 1) >= 1 (q = %u)", q);
+               "a read violates the q-gram lemma threshold m + 1 - q(k + 1) >= 1 (q = %u), or keeps no "
+               "guaranteed intact q-gram at sampling stride %u", q, stride);
     R->max_len = st[1];
     R->max_k = st[2];
 
@@ -520,7 +549,7 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     R->n_qgrams = nqg;
     nq.reset();
 
-    const RefPrep* P = R->ref->prep[q];
+    const RefPrep* P = R->prep.get();
     DBuf<uint32_t> tcode(nqg ? nqg : 1, s), tpay(nqg ? nqg : 1, s);
     R->fent.alloc(nqg ? nqg : 1, s);
     R->fcnt.alloc(n, s);
@@ -530,7 +559,7 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     DBuf<uint32_t> nlc(1, s);
     nlc.zero();
     read_qgrams_k<<<grid_for((uint64_t)n * 32, 256, (unsigned)sm_count() * 8), 256, 0, s>>>(
-        R->codes.p, R->base_off.p, R->len.p, R->kk.p, R->qoff.p, n, q, P->filter.p, P->filter_shift,
+        R->codes.p, R->base_off.p, R->len.p, R->kk.p, R->qoff.p, n, q, stride, P->filter.p, P->filter_shift,
         P->phi_codes.p, P->n_phi, tcode.p, tpay.p, R->fent.p, R->fcnt.p, R->thr.p, R->lowcx.p,
         R->lowcx_list.p, nlc.p);
     PN_CHECK_LAUNCH();

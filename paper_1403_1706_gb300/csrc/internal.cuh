@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
 #include <string>
 
 #include "peanut.h"
@@ -24,6 +26,7 @@ constexpr uint32_t kMagicRef = 0x50524546u;    // 'PREF'
 constexpr uint32_t kMagicReads = 0x50524453u;  // 'PRDS'
 constexpr uint32_t kMagicHits = 0x50484954u;   // 'PHIT'
 constexpr uint32_t kMagicDHits = 0x50444854u;  // 'PDHT'
+constexpr uint32_t kMagicEngine = 0x50454E47u; // 'PENG'
 
 // device status bits (written by kernels, read at synchronization points)
 enum : uint32_t {
@@ -139,6 +142,12 @@ struct RefPrep {
     uint32_t filter_shift = 0;
     DBuf<uint64_t> grp_off;      // 2*n_phi + 1: cluster range of (phi, orientation)
     DBuf<uint64_t> cl_lo, cl_hi; // first / last occurrence position of each cluster
+    // The table outlives the stream it was built on (batches of any stream share it): once its
+    // work is complete its buffers are released on the legacy default stream.
+    void rehome() {
+        phi_codes.s = filter.s = nullptr;
+        grp_off.s = cl_lo.s = cl_hi.s = nullptr;
+    }
 };
 
 }  // namespace pn
@@ -149,15 +158,17 @@ struct peanut_ref {
     uint64_t n_words = 0;       // packed 32-bit words (16 bases each), plus padding
     pn::DBuf<uint32_t> packed;  // base p at bits 30 - 2 (p % 16) of word p / 16
     cudaStream_t stream = nullptr;
-    pn::RefPrep* prep[17] = {};
+    std::shared_ptr<pn::RefPrep> prep[17];  // per q; batches share the table they were indexed with
+    std::mutex prep_mu;
 };
 
 struct peanut_reads {
     uint32_t magic = pn::kMagicReads;
     const peanut_ref* ref = nullptr;
     cudaStream_t stream = nullptr;
-    uint32_t q = 0, n_reads = 0, max_len = 0, max_k = 0, freq_cap = 0;
+    uint32_t q = 0, n_reads = 0, max_len = 0, max_k = 0, freq_cap = 0, stride = 1;
     uint64_t total_bases = 0;
+    std::shared_ptr<const pn::RefPrep> prep;  // frequent q-grams of the reference at this q and cap
     // per read
     pn::DBuf<uint64_t> base_off;  // n+1 offsets into codes
     pn::DBuf<uint8_t> codes;      // 2-bit codes, one per byte
@@ -205,14 +216,26 @@ namespace pn {
 // api.cu: page-locked host blocks for results, kept for reuse after they are freed
 void* host_block_alloc(size_t bytes, size_t* got, bool* pinned);
 void host_block_free(void* p, size_t bytes, bool pinned);
+HostHits* download_hits(const peanut_device_hits& dh, cudaStream_t s);  // synchronizes s
+void free_host_hits(HostHits* H);
 // index.cu
 void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s);
 RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s);
 void free_prep(RefPrep* p);
 void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
-                 uint32_t k_permille);
+                 uint32_t k_permille, uint32_t stride);
+uint32_t default_freq_cap(uint64_t ref_len, uint32_t q);
+// engine.cu: joins the executor threads and releases everything the engine holds
+void destroy_engine(peanut_engine* E);
+// api.cu: a new batch indexed from reads in device memory (throws Fail on error)
+peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets, uint32_t n_reads,
+                          uint64_t total, const peanut_params* p);
 // map.cu
 DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode);
+// keeps, per read, the results at the read's smallest distance over both strands (in: sorted)
+void best_stratum(const peanut_device_hits& in, uint32_t n_reads, DeviceHits* out, cudaStream_t s);
+void alloc_device_hits(DeviceHits* H, uint64_t n, cudaStream_t s);
+void free_device_hits(DeviceHits* H);
 void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
                        const uint64_t* txt_off, int32_t* out, cudaStream_t s);
 void bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat, const char* d_txt,

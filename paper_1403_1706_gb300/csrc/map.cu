@@ -1035,6 +1035,29 @@ __global__ void keep_best_k(KeepBest kb, uint64_t n, const uint64_t* pos, const 
 
 // ---- driver -------------------------------------------------------------------------------
 
+static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s);
+
+void best_stratum(const peanut_device_hits& in, uint32_t n_reads, DeviceHits* out, cudaStream_t s) {
+    const uint64_t NT = in.n;
+    if (!NT) {
+        alloc_hits(out, 0, s);
+        return;
+    }
+    DBuf<uint32_t> mind(n_reads ? n_reads : 1, s);
+    PN_CUDA(cudaMemsetAsync(mind.p, 0xFF, (uint64_t)mind.n * sizeof(uint32_t), s));
+    DBuf<uint64_t> tot(1, s);
+    min_dist_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(in.read_id, in.dist, NT, mind.p);
+    PN_CHECK_LAUNCH();
+    KeepBest kb{in.read_id, in.dist, mind.p};
+    DBuf<uint64_t> pos(NT, s);
+    exclusive_scan(kb, ArrayOut<uint64_t>{pos.p}, NT, tot.p, s);
+    alloc_hits(out, to_host(tot.p, s), s);
+    keep_best_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+        kb, NT, pos.p, in.read_id, in.strand, in.end_pos, in.dist, out->h.read_id, out->h.strand, out->h.end_pos,
+        out->h.dist);
+    PN_CHECK_LAUNCH();
+}
+
 struct Timer {
     cudaEvent_t ev[12];
     int n = 0;
@@ -1064,6 +1087,8 @@ static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s) {
     H->h.end_pos = static_cast<uint64_t*>(dalloc(c * sizeof(uint64_t), s));
     H->h.dist = static_cast<uint8_t*>(dalloc(c, s));
 }
+
+void alloc_device_hits(DeviceHits* H, uint64_t n, cudaStream_t s) { alloc_hits(H, n, s); }
 
 static void free_hits_arrays(DeviceHits* H) {
     if (H->h.read_id) dfree(H->h.read_id, H->stream, H->a);
@@ -1112,6 +1137,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "present-position buffer kept overflowing");
     }
     st.present_probes = NP;
+    PN_CUDA(cudaEventRecord(kev[7], s));
     DBuf<uint64_t> hits;
     uint64_t H = 0;
     const unsigned gexp = grid_for(NP * 32 / 32, kScanBlock, (unsigned)sm_count() * 8);
@@ -1175,7 +1201,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
 
     // 3b. low-complexity reads: their counting-filter ranges and a range around every cluster of
     // their frequent q-grams, merged per (read, strand)
-    const RefPrep* P = ref->prep[q];
+    const RefPrep* P = R->prep.get();
     const uint32_t nl = R->n_lowcx;
     DBuf<uint32_t> lcpos, lcnt;
     DBuf<uint64_t> lc_off, lc_keys, lc_vals;
@@ -1270,20 +1296,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         tm.mark();  // 4
         // 5. best stratum
         if (mode == 1 && NT) {
-            DBuf<uint32_t> mind(n_reads, s);
-            PN_CUDA(cudaMemsetAsync(mind.p, 0xFF, (uint64_t)n_reads * sizeof(uint32_t), s));
-            min_dist_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(all.h.read_id, all.h.dist, NT,
-                                                                                     mind.p);
-            PN_CHECK_LAUNCH();
-            KeepBest kb{all.h.read_id, all.h.dist, mind.p};
-            DBuf<uint64_t> pos(NT, s);
-            exclusive_scan(kb, ArrayOut<uint64_t>{pos.p}, NT, tot.p, s);
-            const uint64_t NB = to_host(tot.p, s);
-            alloc_hits(out, NB, s);
-            keep_best_k<<<grid_for(NT, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
-                kb, NT, pos.p, all.h.read_id, all.h.strand, all.h.end_pos, all.h.dist, out->h.read_id,
-                out->h.strand, out->h.end_pos, out->h.dist);
-            PN_CHECK_LAUNCH();
+            best_stratum(all.h, n_reads, out, s);
             free_hits_arrays(&all);
         } else {
             out->stream = s;
@@ -1306,6 +1319,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.ms_output = tm.ms(4, 5);
     cudaEventElapsedTime(&st.ms_scan_kernel, kev[0], kev[1]);
     cudaEventElapsedTime(&st.ms_verify_kernel, kev[2], kev[3]);
+    cudaEventElapsedTime(&st.ms_probe_kernel, kev[0], kev[7]);
     cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
     cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
     cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);

@@ -32,7 +32,7 @@ class PeanutError(RuntimeError):
 
 class Params(Structure):
     _fields_ = [("q", c_uint32), ("k_fixed", c_uint32), ("k_permille", c_uint32), ("freq_cap", c_uint32),
-                ("stream", c_void_p)]
+                ("stride", c_uint32), ("stream", c_void_p)]
 
 
 class Hits(Structure):
@@ -52,10 +52,28 @@ class MapStats(Structure):
                 ("present_probes", c_uint64), ("candidate_word_columns", c_uint64),
                 ("ms_scan", c_float), ("ms_bin", c_float), ("ms_windows", c_float), ("ms_verify", c_float),
                 ("ms_output", c_float), ("ms_scan_kernel", c_float), ("ms_verify_kernel", c_float),
-                ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float)]
+                ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float),
+                ("ms_probe_kernel", c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class EngineParams(Structure):
+    _fields_ = [("k_fixed", c_uint32), ("k_permille", c_uint32), ("executors", c_uint32), ("max_reads", c_uint32),
+                ("autotune", c_uint32), ("fixed_q", c_uint32), ("hbm_budget", c_uint64)]
+
+
+class EngineClass(Structure):
+    _fields_ = [("q_class", c_uint32), ("q", c_uint32), ("stride", c_uint32), ("freq_cap", c_uint32),
+                ("launches", c_uint64), ("reads", c_uint64), ("bytes_per_read", c_uint64),
+                ("tuned_ms_per_mread", c_float), ("tune_candidates", c_uint32)]
+
+
+class EngineStats(Structure):
+    _fields_ = [("submissions", c_uint64), ("completed", c_uint64), ("reads", c_uint64), ("launches", c_uint64),
+                ("tuning_launches", c_uint64), ("hbm_budget", c_uint64), ("hbm_reserved_peak", c_uint64),
+                ("n_classes", c_uint32), ("cls", EngineClass * 16)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -94,6 +112,12 @@ def load():
                                                 c_void_p]),
         "peanut_bitvector_columns_noalloc": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
                                                   c_void_p]),
+        "peanut_engine_create": (st, [c_void_p, POINTER(EngineParams), POINTER(c_void_p)]),
+        "peanut_engine_submit": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_int, POINTER(c_uint64)]),
+        "peanut_engine_submit_device": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint64, c_int,
+                                             POINTER(c_uint64)]),
+        "peanut_engine_wait": (st, [c_void_p, c_uint64, ctypes.c_int64, POINTER(POINTER(Hits))]),
+        "peanut_engine_get_stats": (st, [c_void_p, POINTER(EngineStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,19 +212,19 @@ def pack_reference(seq, stream=None) -> Reference:
     return Reference(out.value)
 
 
-def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None) -> Params:
+def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None, stride: int = 1) -> Params:
     if k is None and k_permille is None:
         raise ValueError("give k or k_permille")
     return Params(q, K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(freq_cap),
-                  _stream_ptr(stream))
+                  int(stride), _stream_ptr(stream))
 
 
 def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                stream=None) -> ReadBatch:
+                stream=None, stride: int = 1) -> ReadBatch:
     """peanut_index_reads: host reads (concatenated ASCII + n+1 offsets) -> indexed batch."""
     s = _host_u8(seq)
     o = np.ascontiguousarray(offsets, dtype=np.uint64)
-    p = make_params(q, k, k_permille, freq_cap, stream)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride)
     out = c_void_p()
     _check(load().peanut_index_reads(ref.ptr, s.ctypes.data, o.ctypes.data, o.size - 1, ctypes.byref(p),
                                      ctypes.byref(out)))
@@ -208,9 +232,9 @@ def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, f
 
 
 def index_reads_device(ref: Reference, d_seq, d_offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                       stream=None) -> ReadBatch:
+                       stream=None, stride: int = 1) -> ReadBatch:
     """peanut_index_reads_device: reads already in device memory (torch uint8 / int64 tensors)."""
-    p = make_params(q, k, k_permille, freq_cap, stream)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride)
     out = c_void_p()
     n = int(d_offsets.numel()) - 1
     _check(load().peanut_index_reads_device(ref.ptr, d_seq.data_ptr(), d_offsets.data_ptr(), n,
@@ -373,3 +397,83 @@ def bitvector_columns_noalloc(d_pat, d_pat_off, d_txt, d_txt_off, d_out, stream=
     _check(load().peanut_bitvector_columns_noalloc(d_pat.data_ptr(), d_pat_off.data_ptr(), int(d_pat_off.numel()) - 1,
                                                    d_txt.data_ptr(), d_txt_off.data_ptr(), d_out.data_ptr(),
                                                    _stream_ptr(stream)))
+
+
+# ---- batched and served mapping ------------------------------------------------------------
+
+TIMEOUT = 4  # peanut_status PEANUT_TIMEOUT
+
+
+class Engine(_Handle):
+    """peanut_engine: submissions of any size and length mix, coalesced into per-q-class launches
+    on `executors` concurrent streams, admitted by a device-memory budget.  Inputs passed to
+    submit() are kept referenced here until their result is taken with wait()."""
+
+    def __init__(self, ref: Reference, k=None, k_permille=None, executors: int = 2, max_reads: int = 0,
+                 autotune: bool = True, fixed_q: int = 0, hbm_budget: int = 0):
+        if k is None and k_permille is None:
+            raise ValueError("give k or k_permille")
+        p = EngineParams(K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(executors),
+                         int(max_reads), int(bool(autotune)), int(fixed_q), int(hbm_budget))
+        out = c_void_p()
+        _check(load().peanut_engine_create(ref.ptr, ctypes.byref(p), ctypes.byref(out)))
+        super().__init__(out.value)
+        self.ref = ref
+        self._inputs = {}
+
+    def submit(self, seq, offsets, mode: str = "all") -> int:
+        """peanut_engine_submit: host reads; returns the ticket."""
+        s = _host_u8(seq)
+        o = np.ascontiguousarray(offsets, dtype=np.uint64)
+        t = c_uint64()
+        _check(load().peanut_engine_submit(self.ptr, s.ctypes.data, o.ctypes.data, o.size - 1, MODES[mode],
+                                           ctypes.byref(t)))
+        self._inputs[t.value] = (s, o)
+        return int(t.value)
+
+    def submit_device(self, d_seq, d_offsets, mode: str = "all") -> int:
+        """peanut_engine_submit_device: reads in device memory (torch uint8 / int64 tensors, writes
+        complete)."""
+        t = c_uint64()
+        _check(load().peanut_engine_submit_device(self.ptr, d_seq.data_ptr(), d_offsets.data_ptr(),
+                                                  int(d_offsets.numel()) - 1, int(d_seq.numel()), MODES[mode],
+                                                  ctypes.byref(t)))
+        self._inputs[t.value] = (d_seq, d_offsets)
+        return int(t.value)
+
+    def wait_arrays(self, ticket: int, timeout_ms: int = -1) -> HostHits | None:
+        """peanut_engine_wait: the submission's hits as library-held numpy views, or None on
+        timeout."""
+        hp = POINTER(Hits)()
+        st = load().peanut_engine_wait(self.ptr, int(ticket), int(timeout_ms), ctypes.byref(hp))
+        if st == TIMEOUT:
+            return None
+        self._inputs.pop(int(ticket), None)
+        _check(st)
+        return HostHits(hp)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> np.ndarray | None:
+        """peanut_engine_wait: the submission's hit set (structured array), or None on timeout."""
+        h = self.wait_arrays(ticket, timeout_ms)
+        if h is None:
+            return None
+        try:
+            out = np.empty(h.n, HIT_DTYPE)
+            out["read"] = h.read
+            out["strand"] = h.strand
+            out["end"] = h.end.astype(np.int64)
+            out["dist"] = h.dist
+            return out
+        finally:
+            h.free()
+
+    def stats(self) -> dict:
+        s = EngineStats()
+        _check(load().peanut_engine_get_stats(self.ptr, ctypes.byref(s)))
+        d = {f: getattr(s, f) for f, _ in EngineStats._fields_ if f != "cls"}
+        d["classes"] = [{f: getattr(s.cls[i], f) for f, _ in EngineClass._fields_} for i in range(s.n_classes)]
+        return d
+
+    def free(self):
+        super().free()
+        self._inputs = {}
