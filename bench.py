@@ -57,6 +57,13 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slice", type=int, default=30_000_000,
                     help="reference prefix (bp) of the CPU-baseline sample")
+    ap.add_argument("--mode", choices=["plain", "batched", "serve"], default="plain",
+                    help="plain: one batch per launch sequence (the headline); batched: uneven batches of "
+                         "50-250 bp reads through the engine vs the plain path; serve: a Poisson request "
+                         "stream through the engine vs one request at a time")
+    ap.add_argument("--requests", type=int, default=None, help="serve: number of requests")
+    ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
+    ap.add_argument("--no-check", action="store_true", help="batched: skip the identical-output check")
     return ap.parse_args()
 
 
@@ -213,6 +220,315 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _k_of(m):
+    return (int(m) * 50 + 999) // 1000
+
+
+def _q_class(m):
+    return min(int(m) // (_k_of(m) + 1), 16)
+
+
+def run_batched(args, rank, world, local):
+    """Uneven batches (2^16-2^21 reads, log-uniform sizes) of reads of 50, 75, 100, 150 and 250 bp
+    (2 % errors, k = ceil(0.05 L)) on the 3.1 Gbp reference.  Plain arm: every batch mapped
+    with one launch sequence per q class (the largest q its reads admit: 12 for 50 bp, 15 for
+    75 bp, 16 for the rest), reads resident in HBM.  Batched arm: the engine, every batch one
+    device submission, coalesced into autotuned launches on `executors` streams."""
+    import torch
+    import synth
+    from paper_1403_1706_gb300 import peanut
+    from paper_1403_1706_gb300.shard import max_over_ranks, sum_over_ranks
+    torch.cuda.set_device(local)
+    peanut.load()
+    w = synth.WORKLOADS["uneven_3g1_10m"]
+    n_ref = args.ref_len or w["ref_len"]
+    n_reads = args.reads or w["n_reads"]
+    t0 = time.time()
+    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
+    lengths = w["lengths"]
+    per = [n_reads // len(lengths) + (1 if i < n_reads % len(lengths) else 0) for i in range(len(lengths))]
+    cls_reads = [synth.make_reads(ref, per[i], 4000 + 10 * i + 1000 * rank, lengths=(L,),
+                                  rate_range=w["rate_range"], random_frac=w["random_frac"])
+                 for i, L in enumerate(lengths)]
+    bounds = synth.uneven_batches(n_reads, 77 + rank)
+    # batch b holds, of every length, its share of the batch size (reads grouped by length)
+    cum = np.cumsum([0] + per)
+    cuts = [[int(round(bb * p / n_reads)) for p in per] for bb in bounds]
+    cuts[-1] = list(per)
+    seqs, offs, groups = [], [], []
+    for b in range(len(bounds) - 1):
+        parts, o = [], [np.zeros(1, np.uint64)]
+        grp = []  # (q, first read, end read) within the batch
+        at_read, at_base = 0, 0
+        for i, L in enumerate(lengths):
+            a, e = cuts[b][i], cuts[b + 1][i]
+            sub = cls_reads[i].slice(a, e)
+            parts.append(sub.seq)
+            o.append(sub.offsets[1:] + np.uint64(at_base))
+            q = _q_class(L)
+            if grp and grp[-1][0] == q:
+                grp[-1] = (q, grp[-1][1], at_read + sub.n)
+            else:
+                grp.append((q, at_read, at_read + sub.n))
+            at_read += sub.n
+            at_base += int(sub.seq.size)
+        seqs.append(np.concatenate(parts))
+        offs.append(np.concatenate(o))
+        groups.append(grp)
+    t_gen = time.time() - t0
+    stream = torch.cuda.current_stream()
+    R = peanut.pack_reference(ref, stream=stream)
+    d_batches, h_batches = [], []
+    for sq, of, grp in zip(seqs, offs, groups):
+        d_seq = torch.from_numpy(sq).to("cuda")
+        d_off = torch.from_numpy(of.astype(np.int64)).to("cuda")
+        h_seq = torch.empty(sq.size, dtype=torch.uint8, pin_memory=True)
+        h_seq.numpy()[:] = sq
+        h_off = torch.empty(of.size, dtype=torch.int64, pin_memory=True)
+        h_off.numpy()[:] = of.astype(np.int64)
+        sub_dev = []
+        for q, a, e in grp:
+            # the plain path maps a q class in as few launch sequences as keep a launch's expected
+            # q-gram hits (random hits of the class's longest reads, twice for repeats) below 2^31
+            lmax = max(L for L in lengths if _q_class(L) == q)
+            nq = lmax - q + 1
+            hpr = nq * 2.0 * 2.0 * n_ref / float(1 << (2 * q)) + nq
+            cap = max(1, min(1 << 21, int(2.0 ** 31 / hpr)))
+            for x in range(a, e, cap):
+                y = min(e, x + cap)
+                o0 = int(of[x])
+                sub_dev.append((q, x, d_seq[o0:int(of[y])], (d_off[x:y + 1] - o0).contiguous()))
+        d_batches.append((d_seq, d_off, sub_dev))
+        h_batches.append((h_seq, h_off))
+    torch.cuda.synchronize()
+
+    def plain_step(collect=False):
+        n_res, out = 0, []
+        for d_seq, d_off, sub_dev in d_batches:
+            parts = []
+            for q, a, ds, do in sub_dev:
+                B = peanut.index_reads_device(R, ds, do, q, k_permille=50, stream=stream)
+                H = peanut.map_device(R, B)
+                n_res += H.n
+                if collect:
+                    h = H.to_numpy()
+                    h["read"] += a
+                    parts.append(h)
+                H.free()
+                B.free()
+            if collect:
+                out.append(np.concatenate(parts))
+        return n_res, out
+
+    E = peanut.Engine(R, k_permille=50, executors=args.executors, autotune=True)
+
+    def engine_step(collect=False):
+        tickets = [E.submit_device(d_seq, d_off, "all") for d_seq, d_off, _ in d_batches]
+        n_res, out = 0, []
+        for t in tickets:
+            h = E.wait_arrays(t)
+            n_res += h.n
+            if collect:
+                a = np.empty(h.n, peanut.HIT_DTYPE)
+                a["read"], a["strand"], a["end"], a["dist"] = h.read, h.strand, h.end, h.dist
+                out.append(a)
+            h.free()
+        return n_res, out
+
+    def engine_host_step():
+        tickets = [E.submit(h_seq.numpy(), h_off.numpy().view(np.uint64), "all") for h_seq, h_off in h_batches]
+        n_res = 0
+        for t in tickets:
+            h = E.wait_arrays(t)
+            n_res += h.n
+            h.free()
+        return n_res
+
+    # warm-up: tunes the engine; the first step checks that both arms return the same hits
+    t0 = time.time()
+    identical = None
+    for i in range(args.warmup):
+        check = i == 0 and not args.no_check
+        _, a = plain_step(check)
+        _, b = engine_step(check)
+        if check:
+            identical = all(np.array_equal(x, y) for x, y in zip(a, b)) and len(a) == len(b)
+            del a, b
+    t_warm = time.time() - t0
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        l0 = peanut.kernel_launches()
+        t = time.perf_counter()
+        n = 0
+        for _ in range(args.steps):
+            n = fn()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t) / args.steps
+        return max_over_ranks(dt, device="cuda"), n, (peanut.kernel_launches() - l0) // args.steps
+
+    units = sum_over_ranks(n_reads, device="cuda")
+    with ClockSampler(local) as clk:
+        dt_b, n_b, launches_b = timed(lambda: engine_step()[0])
+    clocks = clk.summary()
+    dt_p, n_p, launches_p = timed(lambda: plain_step()[0])
+    dt_e, n_e, _ = timed(engine_host_step)
+    st = E.stats()
+    bases = sum_over_ranks(sum(int(x.size) for x in seqs), device="cuda")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": units / dt_b, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "mode": "batched",
+            "config": {"workload": "uneven_3g1_10m", "reference_bp": int(n_ref), "reads_per_gpu": int(n_reads),
+                       "read_len": list(lengths), "k": "ceil(0.05 L)", "errors": "2% of length",
+                       "batches": len(bounds) - 1, "batch_reads": [int(min(np.diff(bounds))), int(max(np.diff(bounds)))],
+                       "order": "reads of a batch grouped by length", "executors": args.executors,
+                       "parallelism": f"read-sharded x{world}", "l2": "no flush: 0.78 GB packed reference + "
+                       "index probes per launch (> 129 MB L2)"},
+            "plain": {"value": units / dt_p, "ms_per_step": 1e3 * dt_p, "gpu_launches": int(launches_p),
+                      "launch_sequences_per_step": sum(len(d[2]) for d in d_batches),
+                      "q": {str(L): _q_class(L) for L in lengths}, "stride": 1},
+            "vs_plain": dt_p / dt_b, "identical_output": identical,
+            "e2e": {"value": units / dt_e, "unit": UNIT, "ms_per_step": 1e3 * dt_e,
+                    "h2d_bytes_per_step": int(sum(h.numel() + 8 * o.numel() for h, o in h_batches)),
+                    "d2h_bytes_per_step": int(n_e) * HIT_BYTES},
+            "gpu_launches": int(launches_b), "clocks": clocks, "results_per_step": int(n_b),
+            "bases_per_s": bases / dt_b, "engine": st,
+            "setup_s": {"generate": t_gen, "warmup": t_warm},
+        }
+        print(json.dumps(line), flush=True)
+    E.free()
+    return 0
+
+
+def run_serve(args, rank, world, local):
+    """A Poisson request stream (50 requests/s, sizes log-uniform in 10^3..10^6 reads, lengths
+    75-250 bp, 1-4 % errors, k = ceil(0.05 L), half in best-stratum mode) on the resident 3.1 Gbp
+    reference.  Engine: requests submitted from host memory at their arrival times, results
+    waited for on their own threads.  Baseline: one request at a time through the plain path
+    (peanut_index_reads + peanut_map per q class of the request), queued in arrival order."""
+    import torch
+    import synth
+    from paper_1403_1706_gb300 import peanut
+    torch.cuda.set_device(local)
+    peanut.load()
+    w = synth.WORKLOADS["serve_3g1"]
+    n_ref = args.ref_len or w["ref_len"]
+    n_req = args.requests or w["n_requests"]
+    t0 = time.time()
+    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
+    arrivals, sizes, modes = synth.request_stream(91 + rank, n_req, w["rate_per_s"], w["req_min"], w["req_max"])
+    if args.reads:  # scale the request sizes down
+        sizes = np.maximum(1, (sizes * (args.reads / max(1, int(sizes.sum()))))).astype(np.int64)
+    reqs = []
+    for i in range(n_req):
+        rd = synth.make_reads(ref, int(sizes[i]), 9000 + i + 100000 * rank, lengths=w["lengths"],
+                              rate_range=w["rate_range"], random_frac=w["random_frac"])
+        h_seq = torch.empty(rd.seq.size, dtype=torch.uint8, pin_memory=True)
+        h_seq.numpy()[:] = rd.seq
+        # the baseline maps each q class of the request as its own batch
+        cls = np.array([_q_class(m) for m in range(256)])[rd.lengths]
+        order = np.argsort(cls, kind="stable")
+        groups = []
+        for q in np.unique(cls):
+            idx = order[cls[order] == q]
+            sub = rd.subset(idx)
+            groups.append((int(q), idx.astype(np.int64), sub.seq, sub.offsets))
+        reqs.append((h_seq, rd.offsets, groups, rd.n))
+    t_gen = time.time() - t0
+    R = peanut.pack_reference(ref)
+    E = peanut.Engine(R, k_permille=50, executors=args.executors, autotune=True)
+    # warm-up: one request of every class through both paths (tunes the engine, builds the
+    # reference's per-q tables)
+    warm = int(np.argmax(sizes))
+    for _ in range(max(1, args.warmup)):
+        E.wait(E.submit(reqs[warm][0].numpy(), reqs[warm][1], "all"))
+    for q, idx, sq, of in reqs[warm][2]:
+        B = peanut.index_reads(R, sq, of, q, k_permille=50)
+        peanut.map(R, B, "all")
+        B.free()
+
+    # engine: real-time arrivals
+    done = [0.0] * n_req
+    nres = [0] * n_req
+    waiters = []
+
+    def waiter(i, t):
+        h = E.wait_arrays(t)
+        done[i] = time.perf_counter()
+        nres[i] = h.n
+        h.free()
+
+    l0 = peanut.kernel_launches()
+    with ClockSampler(local) as clk:
+        start = time.perf_counter()
+        for i in range(n_req):
+            delay = start + float(arrivals[i]) - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            t = E.submit(reqs[i][0].numpy(), reqs[i][1], str(modes[i]))
+            th = threading.Thread(target=waiter, args=(i, t))
+            th.start()
+            waiters.append(th)
+        for th in waiters:
+            th.join()
+    clocks = clk.summary()
+    launches = peanut.kernel_launches() - l0
+    lat = np.array([done[i] - (start + float(arrivals[i])) for i in range(n_req)])
+    span = max(done) - (start + float(arrivals[0]))
+    total_reads = int(sum(r[3] for r in reqs))
+    st = E.stats()
+
+    # baseline: the plain path, one request at a time, FIFO in arrival order
+    service = []
+    for i in range(n_req):
+        t = time.perf_counter()
+        for q, idx, sq, of in reqs[i][2]:
+            B = peanut.index_reads(R, sq, of, q, k_permille=50)
+            h = peanut.map_arrays(R, B, str(modes[i]))  # a read's stratum lies within its class
+            h.free()
+            B.free()
+        service.append(time.perf_counter() - t)
+    fin, plain_lat = 0.0, []
+    for i in range(n_req):
+        fin = max(float(arrivals[i]), fin) + service[i]
+        plain_lat.append(fin - float(arrivals[i]))
+    plain_lat = np.array(plain_lat)
+    plain_span = fin - float(arrivals[0])
+    E.free()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": total_reads / span, "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "mode": "serve",
+            "config": {"workload": "serve_3g1", "reference_bp": int(n_ref), "requests": n_req,
+                       "rate_per_s": w["rate_per_s"], "request_reads": [int(sizes.min()), int(sizes.max())],
+                       "reads": total_reads, "read_len": [75, 250], "k": "ceil(0.05 L)",
+                       "modes": {m: int((modes == m).sum()) for m in ("all", "best")},
+                       "executors": args.executors, "offered_reads_per_s": total_reads / float(arrivals[-1])},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+            "one_at_a_time": {"value": total_reads / plain_span,
+                              "latency_s": {"p50": float(np.percentile(plain_lat, 50)),
+                                            "p99": float(np.percentile(plain_lat, 99)),
+                                            "max": float(plain_lat.max())},
+                              "service_s_total": float(sum(service)),
+                              "note": "plain path per q class of each request, FIFO queue from measured "
+                                      "service times"},
+            "e2e": {"value": total_reads / span, "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(r[0].numel() + 8 * (r[3] + 1) for r in reqs)),
+                    "d2h_bytes_per_step": int(sum(nres)) * HIT_BYTES},
+            "gpu_launches": int(launches), "clocks": clocks, "results": int(sum(nres)), "engine": st,
+            "setup_s": {"generate": t_gen},
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -221,6 +537,17 @@ def main():
         dist.init_process_group(backend="nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "batched":
+        rc = run_batched(args, rank, world, local)
+    elif args.mode == "serve":
+        rc = run_serve(args, rank, world, local)
+    else:
+        rc = None
+    if rc is not None:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
 
     import torch
     torch.cuda.set_device(local)
@@ -281,91 +608,156 @@ def main():
     units = sum_over_ranks(reads.n, device="cuda")  # every rank maps its own read set
     bases = sum_over_ranks(reads.seq.size, device="cuda")
 
+    # the engine over the same device-resident batches of 2^20 reads: launches of at most one
+    # batch, (q, stride) autotuned, `executors` launches in flight
+    E = peanut.Engine(R, **kw, executors=args.executors, max_reads=B, autotune=True)
+
+    def step_engine():
+        tickets = [E.submit_device(bt["d_seq"], bt["d_off"], "all") for bt in batches]
+        n = 0
+        for t in tickets:
+            h = E.wait_arrays(t)
+            n += h.n
+            h.free()
+        return n
+
+    def step_engine_host():
+        tickets = [E.submit(bt["h_seq"], bt["h_off"], "all") for bt in batches]
+        n = 0
+        for t in tickets:
+            h = E.wait_arrays(t)
+            n += h.n
+            h.free()
+        return n
+
     t0 = time.time()
-    for _ in range(args.warmup):
+    identical = None
+    for i in range(args.warmup):
         n_res = step_device()
+        n_eng = step_engine()
+        if i == 0 and not args.no_check:  # both paths return the same hits, batch by batch
+            identical = True
+            tickets = [E.submit_device(bt["d_seq"], bt["d_off"], "all") for bt in batches]
+            for bt, t in zip(batches, tickets):
+                RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], q, stream=stream, **kw)
+                want = peanut.map_device(R, RB)
+                a = want.to_numpy()
+                want.free()
+                RB.free()
+                h = E.wait_arrays(t)
+                identical &= (h.n == a.size and np.array_equal(h.read, a["read"]) and
+                              np.array_equal(h.strand, a["strand"]) and
+                              np.array_equal(h.end.astype(np.int64), a["end"]) and
+                              np.array_equal(h.dist, a["dist"].astype(np.uint8)))
+                h.free()
+            identical = bool(identical)
     t_warm = time.time() - t0
 
-    # timed: device-resident inputs
-    stats = []
-    barrier()
-    l0 = peanut.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    def timed(fn, clocks=False):
+        barrier()
+        l0 = peanut.kernel_launches()
+        e0 = E.stats()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local) if clocks else None
+        if clk:
+            clk.__enter__()
         ev0.record(stream)
+        n = 0
         for _ in range(args.steps):
-            n_res = step_device(stats)
+            n = fn()
         ev1.record(stream)
         torch.cuda.synchronize()
-    launches = peanut.kernel_launches() - l0
-    ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
-    value = units / (ms / 1e3)
-    clocks = clk.summary()
+        if clk:
+            clk.__exit__()
+        e1 = E.stats()
+        delta = {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
+                                               "bases_scanned", "ms_verify_kernel", "ms_scan_kernel")}
+        ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
+        return ms, n, peanut.kernel_launches() - l0, delta, (clk.summary() if clk else None)
 
-    # end to end through the host API
+    # timed: plain path (one launch sequence per batch, q = 16, every q-gram), device-resident
+    stats = []
+    ms_p, n_res, launches_p, _, _ = timed(lambda: step_device(stats))
+    # timed: engine, device-resident (the headline)
+    ms, n_eng, launches, edelta, clocks = timed(step_engine, clocks=True)
+    value = units / (ms / 1e3)
+
+    # end to end through the host API (engine submissions from pinned host memory)
     e2e = None
     if not args.no_e2e:
-        barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            n_res_h = step_host()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(e0.elapsed_time(e1), device="cuda") / args.steps
+        ems, n_res_h, _, _, _ = timed(step_engine_host)
         h2d = sum(int(bt["h_seq"].nbytes) + int(bt["h_off"].nbytes) for bt in batches)
         e2e = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems}
+               "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems,
+               "api": "peanut_engine_submit + peanut_engine_wait"}
+    est = E.stats()
+    E.free()
 
     # rooflines: the verification count pass (largest launch-list share; integer-ALU bound) and the
-    # reference scan (the memory-bound kernel)
+    # reference scan (the memory-bound kernels), from the runs' CUDA-event kernel times
     peak, peak_kind = load_peaks()
     n_ref = ref.size
     int_peak_tops = INT32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
-    v_ops = statistics.mean(34.0 * s["candidate_word_columns"] for s in stats)
-    v_ms = statistics.mean(s["ms_verify_kernel"] for s in stats)
-    v_ach = v_ops / (v_ms / 1e3) / 1e12
     per_wc = traffic_per_unit("verify_k", source_sha())
-    v_wc = statistics.mean(s["candidate_word_columns"] for s in stats)
-    roof = {"bound": "alu", "achieved": v_ach, "peak": int_peak_tops, "unit": "TOP/s", "frac": v_ach / int_peak_tops,
-            "traffic": per_wc * v_wc if per_wc is not None else None, "kernel": "verify_k (count pass)",
-            "algorithmic_int32_ops_per_launch": v_ops, "avg_launch_ms": v_ms,
-            "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2070 MHz"}
-    per_launch = [n_ref * (0.25 + 8.0) + s["present_probes"] * 8.0 + s["hits"] * (4.0 + 1.0 + 8.0) for s in stats]
-    algo_bytes = statistics.mean(per_launch)
-    avg_ms = statistics.mean(s["ms_scan_kernel"] for s in stats)
-    achieved = algo_bytes / (avg_ms / 1e3) / 1e9
-    roof_scan = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                 "traffic": None, "kernel": "probe_ref_k + expand_k",
-                 "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ms, "peak_source": peak_kind}
+
+    def rooflines(runs, wc, ms_v, probes, hits, bases, ms_s, note):
+        v_ops = 34.0 * wc / runs
+        v_ms = ms_v / runs
+        v_ach = v_ops / (v_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": v_ach, "peak": int_peak_tops, "unit": "TOP/s",
+                "frac": v_ach / int_peak_tops,
+                "traffic": per_wc * wc / runs if per_wc is not None else None, "kernel": "verify_k (count pass)",
+                "algorithmic_int32_ops_per_launch": v_ops, "avg_launch_ms": v_ms, "launches": runs,
+                "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2070 MHz", "timing": note}
+        algo = (bases * (0.25 + 8.0) + probes * 8.0 + hits * (4.0 + 1.0 + 8.0)) / runs
+        s_ms = ms_s / runs
+        ach = algo / (s_ms / 1e3) / 1e9
+        scan = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "probe_ref_k + expand_k", "algorithmic_bytes_per_launch": algo,
+                "avg_launch_ms": s_ms, "launches": runs, "peak_source": peak_kind, "timing": note}
+        return roof, scan
+
+    roof, roof_scan = rooflines(
+        edelta["map_runs"], edelta["candidate_word_columns"], edelta["ms_verify_kernel"], edelta["present_probes"],
+        edelta["hits"], edelta["bases_scanned"], edelta["ms_scan_kernel"],
+        f"engine runs, {args.executors} launches in flight: kernels share the GPU with the other stream's work")
+    roof_p, roof_scan_p = rooflines(
+        len(stats), sum(s["candidate_word_columns"] for s in stats), sum(s["ms_verify_kernel"] for s in stats),
+        sum(s["present_probes"] for s in stats), sum(s["hits"] for s in stats), n_ref * len(stats),
+        sum(s["ms_scan_kernel"] for s in stats), "plain path, one launch sequence at a time")
+    plain = {"value": units / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": int(launches_p),
+             "q": q, "stride": 1, "roofline": roof_p, "roofline_scan": roof_scan_p,
+             "results_per_step": int(n_res),
+             "stage_ms_per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
+                                    ("ms_scan", "ms_scan_kernel", "ms_probe_kernel", "ms_bin", "ms_windows",
+                                     "ms_windows_sweep", "ms_lowcx", "ms_compact", "ms_verify",
+                                     "ms_verify_kernel", "ms_output")},
+             "per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
+                           ("hits", "present_probes", "candidates", "candidate_columns", "lowcx_reads",
+                            "lowcx_ranges", "results")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ref, reads, w, args.cpu_slice, args.batch)
 
-    stage = {k2: statistics.mean(s[k2] for s in stats) for k2 in
-             ("ms_scan", "ms_scan_kernel", "ms_bin", "ms_windows", "ms_windows_sweep", "ms_lowcx", "ms_compact",
-              "ms_verify", "ms_verify_kernel", "ms_output")}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "reference_bp": int(n_ref), "reads_per_gpu": int(reads.n),
-                       "read_len": list(w["lengths"]), "k": k, "q": q, "batch_reads": B, "mode": "all",
+                       "read_len": list(w["lengths"]), "k": k, "q": "autotuned per q class (plain: 16)",
+                       "batch_reads": B, "mode": "all", "executors": args.executors,
                        "parallelism": f"read-sharded x{world}",
                        "l2": "no flush: every batch streams a 0.78 GB packed reference and probes a 1 GiB "
                              "index (> 129 MB L2)"},
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "roofline_scan": roof_scan, "cpu_baseline": cpu,
-            "results_per_step": int(n_res), "bases_per_s": bases / (ms / 1e3),
-            "stage_ms_per_batch": stage,
-            "hits_per_batch": statistics.mean(s["hits"] for s in stats),
-            "candidates_per_batch": statistics.mean(s["candidates"] for s in stats),
-            "candidate_columns_per_batch": statistics.mean(s["candidate_columns"] for s in stats),
-            "lowcx_reads_per_batch": statistics.mean(s["lowcx_reads"] for s in stats),
-            "lowcx_ranges_per_batch": statistics.mean(s["lowcx_ranges"] for s in stats),
-            "present_probes_per_batch": statistics.mean(s["present_probes"] for s in stats),
+            "path": "engine (peanut_engine_submit_device / peanut_engine_wait)",
+            "plain": plain, "vs_plain": ms_p / ms, "identical_output": identical,
+            "engine": {"classes": est["classes"], "launches": est["launches"],
+                       "hbm_reserved_peak": est["hbm_reserved_peak"]},
+            "results_per_step": int(n_eng), "bases_per_s": bases / (ms / 1e3),
             "setup_s": {"generate": t_gen, "pack": t_pack, "warmup": t_warm},
         }
         print(json.dumps(line), flush=True)

@@ -282,6 +282,10 @@ typedef struct {
     uint64_t hbm_budget, hbm_reserved_peak;
     uint32_t n_classes;
     peanut_engine_class cls[16];
+    /* totals over every mapping run (tuning runs included), as in peanut_map_stats */
+    uint64_t map_runs, hits, candidates, candidate_word_columns, present_probes, results;
+    uint64_t bases_scanned;   /* reference bases streamed by the scans */
+    double ms_verify_kernel, ms_scan_kernel, ms_probe_kernel; /* CUDA-event sums per kernel */
 } peanut_engine_stats;
 
 /* Creates an engine over a resident reference (which must outlive it) and starts its executor

@@ -28,6 +28,7 @@ namespace pn {
 constexpr uint32_t kEngineMaxReads = 1u << 24;  // per submission: read id fits 24 bits of a sort key
 constexpr uint32_t kTuneReads = 1u << 17;       // reads of a class's first (timed) launch
 constexpr uint32_t kMinLaunch = 1u << 12;       // smallest launch formed while others are in flight
+constexpr double kMaxLaunchHits = 2147483648.0; // expected q-gram hits of one launch at most
 constexpr int kMaxExecutors = 4;
 constexpr int kQSlots = 17;                     // classes are indexed by q (1..16)
 
@@ -230,6 +231,7 @@ struct ClassState {
     uint64_t waiting = 0;
     uint32_t lenmask[8] = {};
     double bytes_per_read = 0;      // measured (largest seen), 0 = not yet
+    double hits_per_read = 0;       // q-gram hits per read, measured (largest seen), 0 = not yet
     uint64_t launches = 0, reads = 0;
     float tuned_ms_per_mread = 0;
     uint32_t tune_candidates = 0;
@@ -259,6 +261,11 @@ struct peanut_engine {
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;
     uint64_t n_submitted = 0, n_completed = 0, n_reads = 0, n_launches = 0, n_tuning = 0;
+    struct {
+        uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
+        uint64_t bases_scanned = 0, runs = 0;
+        double ms_verify = 0, ms_scan = 0, ms_probe = 0;
+    } sum;
 };
 
 namespace pn {
@@ -269,6 +276,17 @@ static uint32_t k_of(const peanut_engine_params& p, uint32_t m) {
 
 // Device bytes of a launch of n reads of class c before any measurement: the index tables plus a
 // generous per-read allowance that grows with the expected random q-gram hits.
+// Expected q-gram hits per read of a class: measured, else the random hits of its longest reads
+// in a uniform reference (twice, for repeats) plus their own q-grams.
+static double hits_per_read(const peanut_engine* E, const ClassState& C, uint32_t q) {
+    if (C.hits_per_read > 0) return C.hits_per_read;
+    uint32_t mmax = 0;
+    for (uint32_t m = 1; m <= (uint32_t)kMaxReadLen; ++m)
+        if ((C.lenmask[m >> 5] >> (m & 31)) & 1u) mmax = m;
+    const double nq = mmax >= q ? (double)(mmax - q + 1) : 1.0;
+    return nq / C.stride * (2.0 * 2.0 * (double)E->ref->n / (double)(1ull << (2 * q))) + nq;
+}
+
 static double launch_bytes(const peanut_engine* E, const ClassState& C, uint32_t q, uint64_t n) {
     const double fixed = (double)(((1ull << (2 * q)) + 31) / 32) * 8.0 + (80u << 20);
     double per = C.bytes_per_read;
@@ -416,6 +434,7 @@ struct LaunchOut {
     std::shared_ptr<Launch> launch;
     std::vector<uint64_t> bounds;  // result row of each segment start, plus the total
     peanut_map_stats st = {};
+    std::vector<peanut_map_stats> runs;  // every mapping run of the launch (several when tuning)
     uint64_t n_qgrams = 0, total = 0;
 };
 
@@ -455,7 +474,7 @@ static std::shared_ptr<Launch> map_setting(peanut_engine* E, const char* d_seq, 
 }
 
 static double launch_measured_bytes(const peanut_map_stats& st, uint32_t n, uint64_t total, uint64_t nqg) {
-    return 32.0 * st.hits + 12.0 * st.present_probes + 48.0 * st.candidates + 32.0 * st.results +
+    return 48.0 * st.hits + 12.0 * st.present_probes + 48.0 * st.candidates + 32.0 * st.results +
            40.0 * st.lowcx_ranges + 3.0 * total + 330.0 * n + 28.0 * nqg;
 }
 
@@ -491,6 +510,7 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
     if (!tune) {
         float ms = 0;
         out.launch = map_setting(E, buf.p, noff.p, n, total, q_use, stride_use, s, &out.st, &out.n_qgrams, &ms);
+        out.runs.push_back(out.st);
     } else {
         // candidate settings: q and q - 1 (if its random hits stay moderate), strides 1..4 that
         // every length of the class admits; the first (q, 1) is the plain setting and its
@@ -519,6 +539,7 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
             const double fixed = st.ms_probe_kernel;
             const double pred = (fixed + ((double)ms - fixed) * plan / (double)n) / plan * 1e6;
             tried->push_back(cand[i]);
+            out.runs.push_back(st);
             if (pred < best) {
                 best = (float)pred;
                 *best_q = cand[i].first;
@@ -661,6 +682,9 @@ static void executor(peanut_engine* E, int idx) {
         }
         const bool tune = E->p.autotune && !C.tuned;
         uint64_t n = std::min<uint64_t>(C.waiting, tune ? std::min(kTuneReads, E->p.max_reads) : E->p.max_reads);
+        // at most kMaxLaunchHits expected q-gram hits (the sorts of one launch index 32 bits)
+        const double hpr = hits_per_read(E, C, C.q);
+        if ((double)n * hpr > kMaxLaunchHits) n = std::max<uint64_t>(1, (uint64_t)(kMaxLaunchHits / hpr));
         const double avail = (double)E->budget - (double)E->reserved;
         while (n > kMinLaunch && launch_bytes(E, C, C.q, n) > avail) n >>= 1;
         if (launch_bytes(E, C, C.q, n) > avail && E->running > 0) {
@@ -730,6 +754,19 @@ static void executor(peanut_engine* E, int idx) {
             C.cap = default_freq_cap(E->ref->n, q_use);
             const double per = launch_measured_bytes(L.st, taken, L.total, L.n_qgrams) / std::max<uint32_t>(taken, 1);
             C.bytes_per_read = std::max(C.bytes_per_read, 1.25 * per);
+            C.hits_per_read = std::max(C.hits_per_read, 1.25 * (double)L.st.hits / std::max<uint32_t>(taken, 1));
+            for (const peanut_map_stats& m : L.runs) {
+                E->sum.hits += m.hits;
+                E->sum.candidates += m.candidates;
+                E->sum.word_columns += m.candidate_word_columns;
+                E->sum.present_probes += m.present_probes;
+                E->sum.results += m.results;
+                E->sum.ms_verify += m.ms_verify_kernel;
+                E->sum.ms_scan += m.ms_scan_kernel;
+                E->sum.ms_probe += m.ms_probe_kernel;
+                E->sum.bases_scanned += E->ref->n;
+                E->sum.runs += 1;
+            }
         }
         for (size_t i = 0; i < segs.size(); ++i) {
             Submission* S = segs[i].sub;
@@ -975,6 +1012,16 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->tuning_launches = E->n_tuning;
         out->hbm_budget = E->budget;
         out->hbm_reserved_peak = E->reserved_peak;
+        out->map_runs = E->sum.runs;
+        out->hits = E->sum.hits;
+        out->candidates = E->sum.candidates;
+        out->candidate_word_columns = E->sum.word_columns;
+        out->present_probes = E->sum.present_probes;
+        out->results = E->sum.results;
+        out->bases_scanned = E->sum.bases_scanned;
+        out->ms_verify_kernel = E->sum.ms_verify;
+        out->ms_scan_kernel = E->sum.ms_scan;
+        out->ms_probe_kernel = E->sum.ms_probe;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

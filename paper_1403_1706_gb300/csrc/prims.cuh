@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(kSortThreads)
 inline void radix_sort_pairs(uint64_t* keys, uint64_t* vals, uint64_t* tmp, uint64_t* vtmp, uint64_t n, int bits,
                              cudaStream_t s) {
     if (n <= 1 || bits <= 0) return;
-    PN_REQUIRE(n < (1ull << 32), PEANUT_UNSUPPORTED, "radix sort of %llu keys", (unsigned long long)n);
+    PN_REQUIRE(n < (1ull << 32), PEANUT_UNSUPPORTED,
+               "radix sort of %llu keys (2^32 at most): too many q-gram hits in one batch; map fewer reads "
+               "per batch or use a larger q", (unsigned long long)n);
     const uint32_t nb = (uint32_t)((n + kSortTile - 1) / kSortTile);
     DBuf<uint32_t> hist((uint64_t)256 * nb, s), offs((uint64_t)256 * nb, s);
     uint64_t *a = keys, *b = tmp, *va = vals, *vb = vtmp;

@@ -73,7 +73,11 @@ class EngineClass(Structure):
 class EngineStats(Structure):
     _fields_ = [("submissions", c_uint64), ("completed", c_uint64), ("reads", c_uint64), ("launches", c_uint64),
                 ("tuning_launches", c_uint64), ("hbm_budget", c_uint64), ("hbm_reserved_peak", c_uint64),
-                ("n_classes", c_uint32), ("cls", EngineClass * 16)]
+                ("n_classes", c_uint32), ("cls", EngineClass * 16),
+                ("map_runs", c_uint64), ("hits", c_uint64), ("candidates", c_uint64),
+                ("candidate_word_columns", c_uint64), ("present_probes", c_uint64), ("results", c_uint64),
+                ("bases_scanned", c_uint64), ("ms_verify_kernel", ctypes.c_double),
+                ("ms_scan_kernel", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)

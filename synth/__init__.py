@@ -12,6 +12,8 @@ from .generate import (  # noqa: F401
     make_reads,
     make_reference,
     make_workload,
+    request_stream,
     revcomp_ascii,
+    uneven_batches,
     uniform_reference,
 )

@@ -187,7 +187,34 @@ WORKLOADS = {
                            n_reads=10_000_000, lengths=(50, 75, 100, 150, 250),
                            rate_range=(0.02, 0.02), random_frac=0.0, q=12, k="5pct",
                            modes=("all",)),
+    # request stream: Poisson arrivals (mean rate), request sizes log-uniform in [min, max] reads,
+    # read lengths uniform in 75..250 bp, half the requests in best-stratum mode
+    "serve_3g1": dict(ref_len=3_100_000_000, repeat_frac=0.45, tandem_frac=0.01,
+                      lengths=tuple(range(75, 251)), rate_range=(0.01, 0.04), random_frac=0.0,
+                      k="5pct", rate_per_s=50.0, req_min=1_000, req_max=1_000_000, n_requests=100,
+                      modes=("all", "best")),
 }
+
+
+def uneven_batches(n_reads: int, seed: int, lo: int = 1 << 16, hi: int = 1 << 21):
+    """Split n_reads into consecutive batches whose sizes are log-uniform in [lo, hi] (the last
+    one takes the remainder); returns the batch boundaries."""
+    rng = np.random.default_rng(seed)
+    b = [0]
+    while b[-1] < n_reads:
+        size = int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+        b.append(min(n_reads, b[-1] + size))
+    return b
+
+
+def request_stream(seed: int, n_requests: int, rate_per_s: float, req_min: int, req_max: int):
+    """Arrival times (s, Poisson process), sizes (reads, log-uniform) and modes of a request
+    stream."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_per_s, n_requests))
+    sizes = np.exp(rng.uniform(np.log(req_min), np.log(req_max), n_requests)).round().astype(np.int64)
+    modes = np.where(rng.random(n_requests) < 0.5, "all", "best")
+    return arrivals, sizes, modes
 
 
 def make_workload(name: str, ref_len: int | None = None, n_reads: int | None = None,
