@@ -322,16 +322,14 @@ def run_batched(args, rank, world, local):
 
     E = peanut.Engine(R, k_permille=50, executors=args.executors, autotune=True)
 
-    def engine_step(collect=False):
-        tickets = [E.submit_device(d_seq, d_off, "all") for d_seq, d_off, _ in d_batches]
+    def engine_step(collect=False):  # results stay in device memory, as in the plain arm
+        tickets = [E.submit_device(d_seq, d_off, "all", result_on_device=True) for d_seq, d_off, _ in d_batches]
         n_res, out = 0, []
         for t in tickets:
-            h = E.wait_arrays(t)
+            h = E.wait_device(t)
             n_res += h.n
             if collect:
-                a = np.empty(h.n, peanut.HIT_DTYPE)
-                a["read"], a["strand"], a["end"], a["dist"] = h.read, h.strand, h.end, h.dist
-                out.append(a)
+                out.append(h.to_numpy())
             h.free()
         return n_res, out
 
@@ -612,11 +610,11 @@ def main():
     # batch, (q, stride) autotuned, `executors` launches in flight
     E = peanut.Engine(R, **kw, executors=args.executors, max_reads=B, autotune=True)
 
-    def step_engine():
-        tickets = [E.submit_device(bt["d_seq"], bt["d_off"], "all") for bt in batches]
+    def step_engine():  # results stay in device memory, as in the plain arm
+        tickets = [E.submit_device(bt["d_seq"], bt["d_off"], "all", result_on_device=True) for bt in batches]
         n = 0
         for t in tickets:
-            h = E.wait_arrays(t)
+            h = E.wait_device(t)
             n += h.n
             h.free()
         return n

@@ -288,12 +288,17 @@ typedef struct {
     double ms_verify_kernel, ms_scan_kernel, ms_probe_kernel; /* CUDA-event sums per kernel */
 } peanut_engine_stats;
 
+/* Mode flag of engine submissions: keep the result in device memory (take it with
+ * peanut_engine_wait_device; peanut_engine_wait copies it to the host instead). */
+#define PEANUT_RESULT_ON_DEVICE 0x100
+
 /* Creates an engine over a resident reference (which must outlive it) and starts its executor
  * threads.  Errors: INVALID_ARG (bad reference or parameters), NO_MEMORY, CUDA_ERROR. */
 peanut_status peanut_engine_create(const peanut_ref* ref, const peanut_engine_params* p, peanut_engine** out);
 
 /* Queues a submission of host reads (layout as in peanut_index_reads; n_reads 1 .. 2^24) in
- * mode 0 (all hits) or 1 (best stratum) and returns its ticket at once.  seqs and offsets are
+ * mode 0 (all hits) or 1 (best stratum), optionally | PEANUT_RESULT_ON_DEVICE, and returns its
+ * ticket at once.  seqs and offsets are
  * read when the submission is admitted: they must stay valid and unchanged until
  * peanut_engine_wait has returned its result.  Lengths, bases and thresholds are checked at
  * admission; a bad submission fails alone (its wait returns the error).
@@ -313,6 +318,14 @@ peanut_status peanut_engine_submit_device(peanut_engine* e, const char* d_seqs, 
  * submission is still running, or the submission's own error (ticket consumed).
  * Errors: INVALID_ARG (bad engine or unknown ticket), TIMEOUT, and any error of the mapping. */
 peanut_status peanut_engine_wait(peanut_engine* e, uint64_t ticket, int64_t timeout_ms, peanut_hits** out);
+
+/* As peanut_engine_wait for a submission made with PEANUT_RESULT_ON_DEVICE: *out is its hit list
+ * in device memory (read ids are the submission's own, sorted by (read, strand, end)), released
+ * with peanut_free; it stays valid after the engine is released.
+ * Errors: INVALID_ARG (bad engine, unknown ticket, or a submission without the flag), TIMEOUT,
+ * and any error of the mapping. */
+peanut_status peanut_engine_wait_device(peanut_engine* e, uint64_t ticket, int64_t timeout_ms,
+                                        peanut_device_hits** out);
 
 /* Counters and per-class settings of an engine. */
 peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out);

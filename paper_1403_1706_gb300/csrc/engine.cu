@@ -220,7 +220,9 @@ struct Submission {
     std::vector<Part> parts;
     peanut_status status = PEANUT_OK;
     std::string err;
-    HostHits* result = nullptr;
+    HostHits* result = nullptr;      // host result, or
+    DeviceHits* dresult = nullptr;   // device result (PEANUT_RESULT_ON_DEVICE)
+    bool on_device = false;
     bool done = false, queued = false;
 };
 
@@ -409,25 +411,35 @@ static void assemble(peanut_engine* E, Submission* S, cudaStream_t s) {
     // every row is read: the launches' arrays may go
     PN_CUDA(cudaStreamSynchronize(s));
     S->parts.clear();
+    DeviceHits* fin = new DeviceHits();
     try {
         if (S->mode == 1) {
-            DeviceHits best;
-            try {
-                best_stratum(all.h, S->n_reads, &best, s);
-                S->result = download_hits(best.h, s);
-            } catch (...) {
-                free_device_hits(&best);
-                throw;
-            }
-            free_device_hits(&best);
+            best_stratum(all.h, S->n_reads, fin, s);
+            free_device_hits(&all);
         } else {
-            S->result = download_hits(all.h, s);
+            fin->stream = s;
+            fin->a = all.a;
+            fin->h = all.h;
+            all.h = peanut_device_hits{};
+        }
+        if (S->on_device) {
+            PN_CUDA(cudaStreamSynchronize(s));
+            fin->stream = nullptr;  // the caller may free it after the engine (and its streams) are gone
+            S->dresult = fin;
+            fin = nullptr;
+        } else {
+            S->result = download_hits(fin->h, s);
+            free_device_hits(fin);
+            delete fin;
         }
     } catch (...) {
         free_device_hits(&all);
+        if (fin) {
+            free_device_hits(fin);
+            delete fin;
+        }
         throw;
     }
-    free_device_hits(&all);
 }
 
 struct LaunchOut {
@@ -823,6 +835,10 @@ static void destroy_engine_impl(peanut_engine* E) {
     for (auto& kv : E->subs) {
         Submission* S = kv.second;
         if (S->result) free_host_hits(S->result);
+        if (S->dresult) {
+            free_device_hits(S->dresult);
+            delete S->dresult;
+        }
         delete S;
     }
     for (auto& s : E->streams) {
@@ -925,11 +941,13 @@ static peanut_status submit_common(peanut_engine* e, const char* hs, const uint6
     return eguard([&] {
         peanut_engine* E = engine_of(e);
         PN_REQUIRE(ticket, PEANUT_INVALID_ARG, "NULL ticket");
-        PN_REQUIRE(mode == 0 || mode == 1, PEANUT_INVALID_ARG, "mode must be 0 (all) or 1 (best stratum)");
+        PN_REQUIRE((mode & 0xFF) <= 1 && (mode & ~0x1FF) == 0, PEANUT_INVALID_ARG,
+                   "mode must be 0 (all) or 1 (best stratum), optionally | PEANUT_RESULT_ON_DEVICE");
         PN_REQUIRE(n_reads >= 1 && n_reads <= kEngineMaxReads, PEANUT_INVALID_ARG, "n_reads = %u outside 1..2^24",
                    n_reads);
         Submission* S = new Submission();
-        S->mode = mode;
+        S->mode = mode & 0xFF;
+        S->on_device = (mode & PEANUT_RESULT_ON_DEVICE) != 0;
         S->n_reads = n_reads;
         S->h_seq = hs;
         S->h_off = ho;
@@ -972,30 +990,66 @@ peanut_status peanut_engine_submit_device(peanut_engine* e, const char* d_seqs, 
     return submit_common(e, nullptr, nullptr, d_seqs, d_offsets, n_reads, total_bases, mode, ticket);
 }
 
+// Waits for a submission and takes it out of the engine (engine lock taken here).
+static std::unique_ptr<Submission> take(peanut_engine* E, uint64_t ticket, int64_t timeout_ms, int want_device) {
+    std::unique_lock<std::mutex> lk(E->mu);
+    auto it = E->subs.find(ticket);
+    PN_REQUIRE(it != E->subs.end(), PEANUT_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Submission* S = it->second;
+    PN_REQUIRE(!(want_device && !S->on_device), PEANUT_INVALID_ARG,
+               "submission %llu was not made with PEANUT_RESULT_ON_DEVICE", (unsigned long long)ticket);
+    auto ready = [&] { return S->done; };
+    if (timeout_ms < 0) {
+        E->cv_done.wait(lk, ready);
+    } else if (!E->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+        set_error("submission %llu still running", (unsigned long long)ticket);
+        throw Fail{PEANUT_TIMEOUT};
+    }
+    E->subs.erase(it);
+    std::unique_ptr<Submission> own(S);
+    if (S->status != PEANUT_OK) {
+        set_error("%s", S->err.c_str());
+        throw Fail{S->status};
+    }
+    return own;
+}
+
 peanut_status peanut_engine_wait(peanut_engine* e, uint64_t ticket, int64_t timeout_ms, peanut_hits** out) {
     return eguard([&] {
         peanut_engine* E = engine_of(e);
         PN_REQUIRE(out, PEANUT_INVALID_ARG, "NULL out");
         *out = nullptr;
-        std::unique_lock<std::mutex> lk(E->mu);
-        auto it = E->subs.find(ticket);
-        PN_REQUIRE(it != E->subs.end(), PEANUT_INVALID_ARG, "unknown ticket %llu", (unsigned long long)ticket);
-        Submission* S = it->second;
-        auto ready = [&] { return S->done; };
-        if (timeout_ms < 0) {
-            E->cv_done.wait(lk, ready);
-        } else if (!E->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
-            set_error("submission %llu still running", (unsigned long long)ticket);
-            throw Fail{PEANUT_TIMEOUT};
-        }
-        E->subs.erase(it);
-        std::unique_ptr<Submission> own(S);
-        if (S->status != PEANUT_OK) {
-            set_error("%s", S->err.c_str());
-            throw Fail{S->status};
+        std::unique_ptr<Submission> S = take(E, ticket, timeout_ms, 0);
+        if (S->dresult) {  // a device result asked for on the host: copy it down on the legacy stream
+            HostHits* h = nullptr;
+            try {
+                h = download_hits(S->dresult->h, nullptr);
+            } catch (...) {
+                free_device_hits(S->dresult);
+                delete S->dresult;
+                S->dresult = nullptr;
+                throw;
+            }
+            free_device_hits(S->dresult);
+            delete S->dresult;
+            S->dresult = nullptr;
+            *out = &h->h;
+            return;
         }
         *out = &S->result->h;
         S->result = nullptr;
+    });
+}
+
+peanut_status peanut_engine_wait_device(peanut_engine* e, uint64_t ticket, int64_t timeout_ms,
+                                        peanut_device_hits** out) {
+    return eguard([&] {
+        peanut_engine* E = engine_of(e);
+        PN_REQUIRE(out, PEANUT_INVALID_ARG, "NULL out");
+        *out = nullptr;
+        std::unique_ptr<Submission> S = take(E, ticket, timeout_ms, 1);
+        *out = &S->dresult->h;
+        S->dresult = nullptr;
     });
 }
 

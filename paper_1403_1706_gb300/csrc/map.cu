@@ -886,7 +886,8 @@ struct MyersShared {
 };
 
 // Verifies one candidate range: columns a .. hi of the pattern's semiglobal matrix, runs of ends
-// with distance <= k, leftmost minimum of each run.  Returns the number of columns.
+// with distance <= k, leftmost minimum of each run.  Returns the number of columns.  Columns
+// before lo only warm the recurrence up; whole packed words (16 bases) are stepped unrolled.
 template <int W, bool kWrite>
 __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq) {
     const uint64_t key = V.cand_key[x];
@@ -910,56 +911,120 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
     }
     M.score = (int32_t)m;
     M.lastbit = (int)((m - 1) & 63);
-    // text: the current packed word shifted so that the next base sits in its top two bits
-    uint32_t word = __ldg(V.packed + (a >> 4)) << (2 * (uint32_t)(a & 15));
-    uint32_t left = 16 - (uint32_t)(a & 15);
     uint32_t nt = 0;
     uint64_t o = kWrite ? V.toff[x] : 0;
     bool in = false;
     int32_t best = 0;
     int64_t bestj = 0;
-    for (int64_t j = a; j <= hi; ++j) {
-        if (left == 0) {
-            word = __ldg(V.packed + (j >> 4));
-            left = 16;
+    auto emit = [&]() {
+        if (kWrite) {
+            V.out_read[o] = r;
+            V.out_strand[o] = (uint8_t)s;
+            V.out_end[o] = (uint64_t)bestj;
+            V.out_dist[o] = (uint8_t)best;
+            ++o;
+        } else if (nt < 2) {
+            V.inl[2 * x + nt] = ((uint64_t)bestj << 8) | (uint64_t)best;
         }
-        const uint32_t c = word >> 30;
-        word <<= 2;
-        --left;
+        ++nt;
+    };
+    auto column = [&](uint32_t c, int64_t jj) {
         const int32_t d = M.step(c);
-        if (j < lo) continue;
         if (d <= k) {
             if (!in || d < best) {
                 best = d;
-                bestj = j;
+                bestj = jj;
             }
             in = true;
-        }
-        if (in && (d > k || j == hi)) {
-            if (kWrite) {
-                V.out_read[o] = r;
-                V.out_strand[o] = (uint8_t)s;
-                V.out_end[o] = (uint64_t)bestj;
-                V.out_dist[o] = (uint8_t)best;
-                ++o;
-            } else if (nt < 2) {
-                V.inl[2 * x + nt] = ((uint64_t)bestj << 8) | (uint64_t)best;
-            }
-            ++nt;
+        } else if (in) {
+            emit();
             in = false;
         }
+    };
+    int64_t j = a;
+    // warm-up: head of the first word, then whole words, then the tail
+    if (j < lo) {
+        uint32_t word = __ldg(V.packed + (j >> 4)) << (2 * (uint32_t)(j & 15));
+        while (j < lo && (j & 15)) {
+            M.step(word >> 30);
+            word <<= 2;
+            ++j;
+        }
+#pragma unroll 1
+        while (j + 16 <= lo) {
+            uint32_t wd = __ldg(V.packed + (j >> 4));
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                M.step(wd >> 30);
+                wd <<= 2;
+            }
+            j += 16;
+        }
+        if (j < lo) {
+            word = __ldg(V.packed + (j >> 4));
+            while (j < lo) {
+                M.step(word >> 30);
+                word <<= 2;
+                ++j;
+            }
+        }
     }
+    // reported columns lo .. hi
+    while (j <= hi && (j & 15)) {
+        column((__ldg(V.packed + (j >> 4)) >> (30 - 2 * (uint32_t)(j & 15))) & 3u, j);
+        ++j;
+    }
+#pragma unroll 1
+    while (j + 16 <= hi + 1) {
+        uint32_t wd = __ldg(V.packed + (j >> 4));
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            column(wd >> 30, j + u);
+            wd <<= 2;
+        }
+        j += 16;
+    }
+    if (j <= hi) {
+        uint32_t word = __ldg(V.packed + (j >> 4));
+        while (j <= hi) {
+            column(word >> 30, j);
+            word <<= 2;
+            ++j;
+        }
+    }
+    if (in) emit();
     if (!kWrite) V.cnt[x] = nt;
     return (uint64_t)(hi - a + 1);
 }
 
+// Work order of the verification: candidates grouped by words per column and by length (16-column
+// steps up to 4096), so that the 32 ranges of a warp take about the same number of steps.
+constexpr int kOrderBits = 10;
+__global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_t* __restrict__ cand_hi, uint64_t n,
+                            const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk, uint64_t* keys,
+                            uint64_t* vals) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = cand_key[x];
+        const uint32_t r = (uint32_t)(key >> 41);
+        const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)cand_hi[x];
+        const uint32_t m = len[r];
+        int64_t a = lo - ((int64_t)m + kk[r]) + 1;
+        if (a < 0) a = 0;
+        const uint64_t cols = (uint64_t)(hi - a + 1) >> 4;
+        const uint64_t w = (m + 63) >> 6;
+        keys[x] = ((w - 1) << 8) | (cols < 255 ? cols : 255);
+        vals[x] = x;
+    }
+}
+
 template <bool kWrite>
-__global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V) {
+__global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V, const uint64_t* __restrict__ order) {
     __shared__ uint64_t s_eq[4 * kMaxWords * kVerifyThreads];
     uint64_t* seq = s_eq + threadIdx.x;
     unsigned long long cols = 0, wcols = 0;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < V.n_cand;
-         x += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V.n_cand;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = order[i];
         if (kWrite && V.cnt[x] <= 2) continue;
         const uint32_t r = (uint32_t)(V.cand_key[x] >> 41);
         const uint32_t W = (V.len[r] + 63) >> 6;
@@ -1264,9 +1329,18 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
     const unsigned gv = grid_for(NC, kVerifyThreads, (unsigned)sm_count() * 32);
+    DBuf<uint64_t> okey(NC ? NC : 1, s), order(NC ? NC : 1, s);
+    if (NC) {
+        DBuf<uint64_t> t1(NC, s), t2(NC, s);
+        order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+            R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
+        PN_CHECK_LAUNCH();
+        radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
+    }
+    okey.reset();
     PN_CUDA(cudaEventRecord(kev[2], s));
     if (NC) {
-        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V);
+        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p);
         PN_CHECK_LAUNCH();
     }
     PN_CUDA(cudaEventRecord(kev[3], s));
@@ -1290,7 +1364,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         if (NC) {
             inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
             PN_CHECK_LAUNCH();
-            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V);
+            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p);
             PN_CHECK_LAUNCH();
         }
         tm.mark();  // 4

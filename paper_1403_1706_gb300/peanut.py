@@ -121,6 +121,8 @@ def load():
         "peanut_engine_submit_device": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint64, c_int,
                                              POINTER(c_uint64)]),
         "peanut_engine_wait": (st, [c_void_p, c_uint64, ctypes.c_int64, POINTER(POINTER(Hits))]),
+        "peanut_engine_wait_device": (st, [c_void_p, c_uint64, ctypes.c_int64,
+                                           POINTER(POINTER(DeviceHitsStruct))]),
         "peanut_engine_get_stats": (st, [c_void_p, POINTER(EngineStats)]),
     }
     for name, (res, args) in sig.items():
@@ -406,6 +408,7 @@ def bitvector_columns_noalloc(d_pat, d_pat_off, d_txt, d_txt_off, d_out, stream=
 # ---- batched and served mapping ------------------------------------------------------------
 
 TIMEOUT = 4  # peanut_status PEANUT_TIMEOUT
+RESULT_ON_DEVICE = 0x100  # PEANUT_RESULT_ON_DEVICE
 
 
 class Engine(_Handle):
@@ -435,13 +438,14 @@ class Engine(_Handle):
         self._inputs[t.value] = (s, o)
         return int(t.value)
 
-    def submit_device(self, d_seq, d_offsets, mode: str = "all") -> int:
+    def submit_device(self, d_seq, d_offsets, mode: str = "all", result_on_device: bool = False) -> int:
         """peanut_engine_submit_device: reads in device memory (torch uint8 / int64 tensors, writes
-        complete)."""
+        complete); with result_on_device the hits stay on the device (wait_device)."""
         t = c_uint64()
+        flags = RESULT_ON_DEVICE if result_on_device else 0
         _check(load().peanut_engine_submit_device(self.ptr, d_seq.data_ptr(), d_offsets.data_ptr(),
-                                                  int(d_offsets.numel()) - 1, int(d_seq.numel()), MODES[mode],
-                                                  ctypes.byref(t)))
+                                                  int(d_offsets.numel()) - 1, int(d_seq.numel()),
+                                                  MODES[mode] | flags, ctypes.byref(t)))
         self._inputs[t.value] = (d_seq, d_offsets)
         return int(t.value)
 
@@ -470,6 +474,17 @@ class Engine(_Handle):
             return out
         finally:
             h.free()
+
+    def wait_device(self, ticket: int, timeout_ms: int = -1) -> DeviceHits | None:
+        """peanut_engine_wait_device: the submission's hits left in device memory, or None on
+        timeout."""
+        hp = POINTER(DeviceHitsStruct)()
+        st = load().peanut_engine_wait_device(self.ptr, int(ticket), int(timeout_ms), ctypes.byref(hp))
+        if st == TIMEOUT:
+            return None
+        self._inputs.pop(int(ticket), None)
+        _check(st)
+        return DeviceHits(hp)
 
     def stats(self) -> dict:
         s = EngineStats()

@@ -124,6 +124,35 @@ def test_engine_device_submission(gpu, world, expected):
         E.free()
 
 
+def test_engine_device_results(gpu, world, expected):
+    """Results left on the device, taken after the engine is gone; a host wait on such a ticket
+    copies it down; a device wait on a host-result ticket is refused."""
+    import torch
+    ref, R, subs = world
+    E = gpu.Engine(R, k_permille=50, executors=2)
+    keep = []
+    try:
+        d = []
+        for s in subs:
+            ds = torch.from_numpy(s.seq.copy()).cuda()
+            do = torch.from_numpy(s.offsets.astype(np.int64)).cuda()
+            d.append((ds, do))
+        torch.cuda.synchronize()
+        t_dev = [E.submit_device(ds, do, m, result_on_device=True) for (ds, do), m in zip(d, ("all", "best") * 3)]
+        t_host = E.submit_device(d[3][0], d[3][1], "best", result_on_device=True)
+        t_plain = E.submit(subs[2].seq, subs[2].offsets, "all")
+        with pytest.raises(gpu.PeanutError, match="RESULT_ON_DEVICE"):
+            E.wait_device(t_plain)
+        assert np.array_equal(E.wait(t_plain), expected[2, "all"])
+        keep = [E.wait_device(t) for t in t_dev]
+        assert np.array_equal(E.wait(t_host), expected[3, "best"])
+    finally:
+        E.free()
+    for i, (h, m) in enumerate(zip(keep, ("all", "best") * 3)):
+        assert np.array_equal(h.to_numpy(), expected[i, m]), (i, m)
+        h.free()
+
+
 def test_engine_bad_submission_fails_alone(gpu, world, expected):
     ref, R, subs = world
     bad_seq = subs[2].seq.copy()
