@@ -105,6 +105,8 @@ typedef struct {
     float ms_verify_kernel;    /* the verification count pass alone (CUDA events on its stream) */
     float ms_windows_sweep, ms_lowcx, ms_compact; /* parts of ms_windows */
     float ms_probe_kernel;     /* the probe half of the reference scan (present positions) */
+    float ms_windows_med, ms_windows_big; /* window paths of reads with many hits (block / global) */
+    uint64_t med_reads, big_reads;        /* reads taking those paths */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first

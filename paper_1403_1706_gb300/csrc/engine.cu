@@ -259,6 +259,7 @@ struct peanut_engine {
     uint64_t budget = 0, reserved = 0, reserved_peak = 0;
     uint64_t next_ticket = 1, next_order = 0;
     int running = 0;  // admissions and launches in progress
+    int tuning_active = 0;  // tuning runs in progress (they run alone)
     bool stop = false;
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;
@@ -539,7 +540,6 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
                 if (setting_ok(E, mask, q, st)) cand.push_back({q, st});
             if (q == 1) break;
         }
-        const double plan = (double)std::max<uint32_t>(E->p.max_reads, n);
         float best = 1e30f;
         for (size_t i = 0; i < cand.size(); ++i) {
             peanut_map_stats st = {};
@@ -547,6 +547,12 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
             float ms = 0;
             std::shared_ptr<Launch> L =
                 map_setting(E, buf.p, noff.p, n, total, cand[i].first, cand[i].second, s, &st, &nqg, &ms);
+            // the launch size this setting would run at: max_reads, or fewer where its hits per
+            // read or device bytes per read (as measured here, with the model's margin) cap it
+            const double hpr = 1.25 * (double)st.hits / n + 1.0;
+            const double bpr = 1.25 * launch_measured_bytes(st, n, total, nqg) / n + 1.0;
+            const double plan = std::max((double)n, std::min({(double)E->p.max_reads, kMaxLaunchHits / hpr,
+                                                             0.5 * (double)E->budget / bpr}));
             // the probe pass costs the same for any batch size; the rest grows with the reads
             const double fixed = st.ms_probe_kernel;
             const double pred = (fixed + ((double)ms - fixed) * plan / (double)n) / plan * 1e6;
@@ -608,8 +614,8 @@ static void fail_and_maybe_finish(peanut_engine* E, Submission* S, peanut_status
 }
 
 static int pick_class(peanut_engine* E) {
-    int best = -1;
-    uint64_t order = UINT64_MAX;
+    int best = -1, best_untuned = -1;
+    uint64_t order = UINT64_MAX, order_untuned = UINT64_MAX;
     for (int c = 1; c < kQSlots; ++c) {
         ClassState& C = E->cls[c];
         while (!C.queue.empty() && C.queue.front()->status != PEANUT_OK) {  // drop failed submissions
@@ -625,8 +631,12 @@ static int pick_class(peanut_engine* E) {
             order = C.queue.front()->order;
             best = c;
         }
+        if (E->p.autotune && !C.tuned && C.queue.front()->order < order_untuned) {
+            order_untuned = C.queue.front()->order;
+            best_untuned = c;
+        }
     }
-    return best;
+    return best_untuned >= 0 ? best_untuned : best;  // classes still to be tuned go first
 }
 
 static void executor(peanut_engine* E, int idx) {
@@ -634,6 +644,11 @@ static void executor(peanut_engine* E, int idx) {
     cudaStream_t s = E->streams[idx];
     std::unique_lock<std::mutex> lk(E->mu);
     while (!E->stop) {
+        // a tuning run has the GPU to itself: nothing else starts meanwhile
+        if (E->tuning_active) {
+            E->cv_work.wait(lk);
+            continue;
+        }
         // 1. admission, in submission order, while the footprint fits
         if (!E->pending.empty()) {
             Submission* S = E->pending.front();
@@ -693,6 +708,10 @@ static void executor(peanut_engine* E, int idx) {
             C.stride = 1;
         }
         const bool tune = E->p.autotune && !C.tuned;
+        if (tune && E->running > 0) {  // wait for the work in flight to drain first
+            E->cv_work.wait(lk);
+            continue;
+        }
         uint64_t n = std::min<uint64_t>(C.waiting, tune ? std::min(kTuneReads, E->p.max_reads) : E->p.max_reads);
         // at most kMaxLaunchHits expected q-gram hits (the sorts of one launch index 32 bits)
         const double hpr = hits_per_read(E, C, C.q);
@@ -718,7 +737,10 @@ static void executor(peanut_engine* E, int idx) {
             if (S->next[c] == S->cnt[c]) C.queue.pop_front();
         }
         C.waiting -= taken;
-        if (tune) C.tuning = true;
+        if (tune) {
+            C.tuning = true;
+            E->tuning_active++;
+        }
         // the class's setting, unless a length in this launch does not admit it
         const bool keep = setting_ok(E, mask, C.q, C.stride);
         const uint32_t q_use = keep ? C.q : (uint32_t)c, stride_use = keep ? C.stride : 1;
@@ -748,6 +770,7 @@ static void executor(peanut_engine* E, int idx) {
         E->reserved -= need;
         if (tune) {
             C.tuning = false;
+            E->tuning_active--;
             if (st == PEANUT_OK) {
                 C.tuned = true;
                 C.q = bq;

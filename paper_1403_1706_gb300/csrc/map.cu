@@ -25,6 +25,11 @@ constexpr int kScanBlock = 256;
 constexpr int kStageCap = 256;  // staged hits per warp before one global append
 constexpr int kWinWarps = 4;
 constexpr int kWinCap = 1024;   // hits per read sorted in shared memory by one warp
+constexpr uint32_t kMedCap = 12288;  // hits per read sorted in shared memory by one block
+constexpr int kMedThreads = 1024;
+constexpr int kMedWarps = kMedThreads / 32;
+constexpr int kMedRounds = kMedCap / (kMedWarps * 32);  // 32-key rounds per warp
+constexpr size_t kMedSmem = 2 * kMedCap * sizeof(uint64_t) + kMedWarps * 256 * sizeof(uint16_t);
 constexpr uint64_t kKeyMask41 = (1ull << 41) - 1;
 constexpr uint64_t kPosMask40 = (1ull << 40) - 1;
 
@@ -288,11 +293,18 @@ struct RangeMerger {
 };
 
 // Sweep of one read's sorted hit keys (both strands) by one warp; writes the merged end ranges.
+// Window j (T hits within k + 1 diagonals) covers ends [lo_j, hi_j]; both bounds grow with j, so
+// a window opens a new range exactly when its lo lies beyond the previous window's hi by more
+// than the join distance, and a range's hi is its last window's hi.  Each chunk of 32 windows
+// decides this with one ballot and one shuffle.  Windows entirely outside the reference are
+// dropped first (they cannot hold an end, and every range stays non-empty after clamping).
 __device__ void window_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const WinParams& P) {
     const int lane = threadIdx.x & 31;
     const int64_t m = P.len[r], k = P.kk[r];
     const uint32_t T = P.thr[r];
     const uint64_t base = P.roff[r];
+    const int64_t n = (int64_t)P.n;
+    const int64_t join = m + k;  // ranges closer than this are verified as one
     // number of strand-0 keys
     uint32_t h0 = 0;
     for (uint32_t x = lane; x < h; x += 32) h0 += (keys[x] & kKeyMask41) < (1ull << 40) ? 1 : 0;
@@ -301,38 +313,49 @@ __device__ void window_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const
     uint32_t total = 0;
     for (uint32_t s = 0; s < 2; ++s) {
         const uint32_t b = s == 0 ? 0 : h0, e = s == 0 ? h0 : h;
-        RangeMerger mg;
-        mg.cnt = total;
-        mg.join = m + k;
+        uint32_t cnt = total;   // ranges written so far (uniform)
+        bool have = false;      // a range is open (uniform)
+        int64_t open_hi = 0;    // hi of the last valid window (uniform)
         for (uint32_t j0 = b; j0 + T - 1 < e; j0 += 32) {
             const uint32_t j = j0 + lane;
             bool valid = false;
-            if (j + T - 1 < e) valid = key_diag(keys[j + T - 1]) - key_diag(keys[j]) <= k;
-            unsigned bal = __ballot_sync(kFull, valid);
-            if (lane == 0) {
-                while (bal) {
-                    const int bit = __ffs(bal) - 1;
-                    bal &= bal - 1;
-                    const uint32_t jj = j0 + bit;
-                    const int64_t lo = key_diag(keys[jj + T - 1]) + m - 1 - 2 * k;
-                    const int64_t hi = key_diag(keys[jj]) + m - 1 + k;
-                    mg.add(lo, hi, P.wlo, P.whi, base, s, P.n);
+            int64_t lo = 0, hi = 0;
+            if (j + T - 1 < e) {
+                const int64_t dj = key_diag(keys[j]), dl = key_diag(keys[j + T - 1]);
+                if (dl - dj <= k) {
+                    lo = dl + m - 1 - 2 * k;
+                    hi = dj + m - 1 + k;
+                    valid = hi >= 0 && lo <= n - 1;
                 }
             }
+            const unsigned bal = __ballot_sync(kFull, valid);
+            if (!bal) continue;
+            const unsigned below = bal & lanemask_lt();
+            const int64_t hin = __shfl_sync(kFull, hi, below ? 31 - __clz(below) : lane);
+            const bool has_prev = below != 0 || have;
+            const int64_t hprev = below ? hin : open_hi;
+            const bool start = valid && (!has_prev || lo > hprev + join);
+            const unsigned sb = __ballot_sync(kFull, start);
+            if (start) {
+                const uint32_t idx = cnt + __popc(sb & lanemask_lt());
+                P.wlo[base + idx] = (uint64_t)(lo < 0 ? 0 : lo) | ((uint64_t)s << 40);
+                if (has_prev) P.whi[base + idx - 1] = (uint64_t)(hprev > n - 1 ? n - 1 : hprev);
+            }
+            cnt += __popc(sb);
+            have = true;
+            open_hi = __shfl_sync(kFull, hi, 31 - __clz(bal));
         }
-        if (lane == 0) {
-            mg.flush(P.wlo, P.whi, base, s, P.n);
-            P.wcnt[2 * r + s] = mg.cnt - total;
-        }
-        total = __shfl_sync(kFull, mg.cnt, 0);
+        if (have && lane == 0) P.whi[base + cnt - 1] = (uint64_t)(open_hi > n - 1 ? n - 1 : open_hi);
+        if (lane == 0) P.wcnt[2 * r + s] = cnt - total;
+        total = cnt;
     }
 }
 
 // One warp per read: sort its hits in shared memory (bitonic), then sweep.  Reads with more
-// than kWinCap hits are deferred to the global-memory path.
+// than kWinCap hits go to the block path (up to kMedCap) or the global-memory path.
 __global__ void __launch_bounds__(kWinWarps * 32)
     windows_k(const uint64_t* __restrict__ binned, uint32_t n_reads, WinParams P, uint32_t* big_list,
-              uint32_t* n_big) {
+              uint32_t* n_big, uint32_t* med_list) {
     __shared__ uint64_t sk[kWinWarps][kWinCap];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t* s = sk[wid];
@@ -345,7 +368,10 @@ __global__ void __launch_bounds__(kWinWarps * 32)
             continue;
         }
         if (h > (uint32_t)kWinCap) {
-            if (lane == 0) big_list[atomicAdd(n_big, 1u)] = r;
+            if (lane == 0) {
+                if (h <= kMedCap) med_list[atomicAdd(n_big + 1, 1u)] = r;
+                else big_list[atomicAdd(n_big, 1u)] = r;
+            }
             continue;
         }
         uint32_t np = 32;
@@ -369,6 +395,291 @@ __global__ void __launch_bounds__(kWinWarps * 32)
         }
         window_sweep(s, h, r, P);
         __syncwarp();
+    }
+}
+
+// Block-wide exclusive scans over one value per thread (kMedThreads threads; sc: 32 ints).
+__device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t* sc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl = max(incl, t);
+    }
+    if (lane == 31) sc[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int32_t x = sc[lane], y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(kFull, y, o);
+            if (lane >= o) y = max(y, t);
+        }
+        sc[lane] = y;  // inclusive over warps
+        (void)x;
+    }
+    __syncthreads();
+    int32_t before = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) before = -1;
+    const int32_t r = max(before, w ? sc[w - 1] : -1);
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t* sc, uint32_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sc[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t y = sc[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, y, o);
+            if (lane >= o) y += t;
+        }
+        sc[lane] = y;
+    }
+    __syncthreads();
+    const uint32_t r = incl - v + (w ? sc[w - 1] : 0u);
+    *total = sc[31];
+    __syncthreads();
+    return r;
+}
+
+// The sweep of window_sweep by a whole block over one read's sorted keys in shared memory: each
+// thread takes a run of consecutive windows; the previous valid window of every window comes from
+// an exclusive max-scan, range indices from an exclusive sum-scan of the range starts.
+__device__ void block_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const WinParams& P, int32_t* sci,
+                            uint32_t* scu, uint32_t* s_h0) {
+    const int64_t m = P.len[r], k = P.kk[r];
+    const uint32_t T = P.thr[r];
+    const uint64_t base = P.roff[r];
+    const int64_t n = (int64_t)P.n, join = m + k;
+    if (threadIdx.x == 0) *s_h0 = h;
+    __syncthreads();
+    const uint32_t E = (h + kMedThreads - 1) / kMedThreads;  // windows per thread (<= kMedRounds)
+    const uint32_t j0 = threadIdx.x * E;
+    for (uint32_t e = 0; e < E; ++e) {
+        const uint32_t j = j0 + e;
+        if (j < h && (keys[j] >> 40) & 1ull && (j == 0 || !((keys[j - 1] >> 40) & 1ull))) *s_h0 = j;
+    }
+    __syncthreads();
+    const uint32_t h0 = *s_h0;
+    auto seg = [&](uint32_t j) { return j < h0 ? 0u : 1u; };
+    auto hi_of = [&](uint32_t j) { return key_diag(keys[j]) + m - 1 + k; };
+    auto lo_of = [&](uint32_t j) { return key_diag(keys[j + T - 1]) + m - 1 - 2 * k; };
+    auto valid = [&](uint32_t j) {
+        const uint32_t e = j < h0 ? h0 : h;
+        if (j + T - 1 >= e) return false;
+        if (key_diag(keys[j + T - 1]) - key_diag(keys[j]) > k) return false;
+        return hi_of(j) >= 0 && lo_of(j) <= n - 1;
+    };
+    // valid windows of this thread, and its last one
+    uint32_t vmask = 0;
+    int32_t last = -1;
+    for (uint32_t e = 0; e < E; ++e) {
+        const uint32_t j = j0 + e;
+        if (j < h && valid(j)) {
+            vmask |= 1u << e;
+            last = (int32_t)j;
+        }
+    }
+    const int32_t pre = block_excl_max(last, sci);
+    // range starts
+    uint32_t smask = 0, ns = 0, ns0 = 0;
+    int32_t cur = pre;
+    for (uint32_t e = 0; e < E; ++e) {
+        if (!((vmask >> e) & 1u)) continue;
+        const uint32_t j = j0 + e;
+        const bool start = cur < 0 || seg((uint32_t)cur) != seg(j) || lo_of(j) > hi_of((uint32_t)cur) + join;
+        if (start) {
+            smask |= 1u << e;
+            ++ns;
+            ns0 += seg(j) == 0 ? 1u : 0u;
+        }
+        cur = (int32_t)j;
+    }
+    uint32_t total = 0, total0 = 0;
+    uint32_t idx = block_excl_sum(ns, scu, &total);
+    block_excl_sum(ns0, scu, &total0);
+    // the last valid window of each strand closes its strand's last range
+    int32_t last0 = -1, last1 = -1;
+    if (last >= 0) {
+        for (uint32_t e = 0; e < E; ++e)
+            if ((vmask >> e) & 1u) {
+                if (seg(j0 + e) == 0) last0 = (int32_t)(j0 + e);
+                else last1 = (int32_t)(j0 + e);
+            }
+    }
+    // block-wide max of last0 / last1: an exclusive max-scan of the values shifted by one thread
+    const int32_t m0 = block_excl_max(last0, sci), m1 = block_excl_max(last1, sci);
+    __shared__ int32_t s_last[2];
+    if (threadIdx.x == kMedThreads - 1) {
+        s_last[0] = max(m0, last0);
+        s_last[1] = max(m1, last1);
+    }
+    __syncthreads();
+    const int32_t lastv0 = s_last[0], lastv1 = s_last[1];
+    cur = pre;
+    for (uint32_t e = 0; e < E; ++e) {
+        if (!((vmask >> e) & 1u)) continue;
+        const uint32_t j = j0 + e;
+        if ((smask >> e) & 1u) {
+            const int64_t lo = lo_of(j);
+            P.wlo[base + idx] = (uint64_t)(lo < 0 ? 0 : lo) | ((uint64_t)seg(j) << 40);
+            if (cur >= 0 && seg((uint32_t)cur) == seg(j)) {
+                const int64_t hp = hi_of((uint32_t)cur);
+                P.whi[base + idx - 1] = (uint64_t)(hp > n - 1 ? n - 1 : hp);
+            }
+            ++idx;
+        }
+        if ((int32_t)j == lastv0 || (int32_t)j == lastv1) {
+            const int64_t hp = hi_of(j);
+            P.whi[base + idx - 1] = (uint64_t)(hp > n - 1 ? n - 1 : hp);
+        }
+        cur = (int32_t)j;
+    }
+    if (threadIdx.x == 0) {
+        P.wcnt[2 * r] = total0;
+        P.wcnt[2 * r + 1] = total - total0;
+    }
+    __syncthreads();
+}
+
+// Reads with kWinCap < hits <= kMedCap: one block each sorts them in shared memory, then the
+// block sweeps them.  The sort is a stable LSD radix sort on 8-bit digits of (strand << sbit | biased
+// diagonal): every warp ranks a contiguous chunk of keys in 32-key rounds (__match_any_sync for
+// equal digits, a per-warp counter per digit), the counters become digit-major, warp-minor
+// offsets, and the keys are scattered to the other buffer.
+__global__ void __launch_bounds__(kMedThreads, 1)
+    windows_med_k(const uint64_t* __restrict__ binned, const uint32_t* __restrict__ list, uint32_t n_list,
+                  WinParams P, uint32_t* cursor, int sbit) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* bufA = sm;
+    uint64_t* bufB = sm + kMedCap;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(sm + 2 * kMedCap);  // [warp][256]
+    __shared__ uint32_t s_next, s_h0;
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_part[4 * 256];
+    __shared__ int32_t s_sci[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t low = (1ull << sbit) - 1;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(cursor, 1u);  // reads of uneven size: dynamic order
+        __syncthreads();
+        const uint32_t x = s_next;
+        if (x >= n_list) break;
+        const uint32_t r = list[x];
+        const uint64_t b = P.roff[r];
+        const uint32_t h = (uint32_t)(P.roff[r + 1] - b);
+        for (uint32_t i = threadIdx.x; i < h; i += blockDim.x) {
+            const uint64_t k0 = binned[b + i];
+            bufA[i] = (((k0 >> 40) & 1ull) << sbit) | (k0 & kPosMask40);
+        }
+        const uint32_t chunk = ((h + kMedWarps * 32 - 1) / (kMedWarps * 32)) * 32;  // keys per warp
+        const uint32_t w0 = (uint32_t)w * chunk, w1 = min(h, w0 + chunk);
+        uint64_t* src = bufA;
+        uint64_t* dst = bufB;
+        for (int shift = 0; shift <= sbit; shift += 8) {
+            for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x) cnt[i] = 0;
+            __syncthreads();
+            uint32_t lr[kMedRounds];
+            const int nrounds = (int)((w1 > w0 ? w1 - w0 : 0) + 31) / 32;
+#pragma unroll
+            for (int i = 0; i < kMedRounds; ++i) {
+                if (i >= nrounds) break;  // warp-uniform
+                const uint32_t idx = w0 + 32 * i + lane;
+                const bool valid = idx < w1;
+                const uint32_t dig = valid ? (uint32_t)(src[idx] >> shift) & 255u : 0u;
+                // lanes with the same digit: intersect the eight bit-ballots
+                unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+                for (int bb = 0; bb < 8; ++bb) {
+                    const unsigned bal = __ballot_sync(kFull, (dig >> bb) & 1u);
+                    peers &= ((dig >> bb) & 1u) ? bal : ~bal;
+                }
+                const uint32_t base = valid ? cnt[w * 256 + dig] : 0u;
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1) cnt[w * 256 + dig] = (uint16_t)(base + __popc(peers));
+                __syncwarp();
+                lr[i] = base + __popc(peers & lanemask_lt());
+            }
+            __syncthreads();
+            {  // per digit: exclusive prefix over the warps, four groups of eight warps in parallel
+                const int d = threadIdx.x & 255, g = threadIdx.x >> 8;
+                uint32_t run = 0;
+#pragma unroll
+                for (int ww = 8 * g; ww < 8 * g + 8; ++ww) {
+                    const uint32_t c = cnt[ww * 256 + d];
+                    cnt[ww * 256 + d] = (uint16_t)run;
+                    run += c;
+                }
+                s_part[g * 256 + d] = run;
+            }
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                const int d = threadIdx.x;
+                uint32_t run = 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const uint32_t c = s_part[g * 256 + d];
+                    s_part[g * 256 + d] = run;
+                    run += c;
+                }
+                s_tot[d] = run;
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {  // exclusive prefix over the digits, 8 per lane
+                uint32_t v[8], sum = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = s_tot[lane * 8 + j];
+                    sum += v[j];
+                }
+                uint32_t incl = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                uint32_t run = incl - sum;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    s_tot[lane * 8 + j] = run;
+                    run += v[j];
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x)
+                cnt[i] = (uint16_t)(cnt[i] + s_tot[i & 255] + s_part[(i >> 11) * 256 + (i & 255)]);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kMedRounds; ++i) {
+                if (i >= nrounds) break;
+                const uint32_t idx = w0 + 32 * i + lane;
+                if (idx < w1) {
+                    const uint64_t key = src[idx];
+                    dst[cnt[w * 256 + ((uint32_t)(key >> shift) & 255u)] + lr[i]] = key;
+                }
+            }
+            __syncthreads();
+            uint64_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        for (uint32_t i = threadIdx.x; i < h; i += blockDim.x) {  // back to strand << 40
+            const uint64_t k1 = src[i];
+            src[i] = ((k1 >> sbit) << 40) | (k1 & low);
+        }
+        __syncthreads();
+        block_sweep(src, h, r, P, s_sci, s_tot, &s_h0);
     }
 }
 
@@ -1239,13 +1550,32 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     // 3. windows
     DBuf<uint64_t> wlo(H ? H : 1, s), whi(H ? H : 1, s);
     DBuf<uint32_t> wcnt(2 * (uint64_t)n_reads, s);
-    DBuf<uint32_t> big_list(n_reads, s), nbig(1, s);
+    DBuf<uint32_t> big_list(n_reads, s), med_list(n_reads, s), nbig(3, s);  // big, medium, cursor
     nbig.zero();
     WinParams WP{roff.p, R->len.p, R->kk.p, R->thr.p, n, wlo.p, whi.p, wcnt.p};
     windows_k<<<grid_for((uint64_t)n_reads * 32, kWinWarps * 32, (unsigned)sm_count() * 16), kWinWarps * 32, 0, s>>>(
-        binned.p, n_reads, WP, big_list.p, nbig.p);
+        binned.p, n_reads, WP, big_list.p, nbig.p, med_list.p);
     PN_CHECK_LAUNCH();
-    const uint32_t n_big = to_host(nbig.p, s);
+    uint32_t nbm[2];
+    PN_CUDA(cudaMemcpyAsync(nbm, nbig.p, sizeof(nbm), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    const uint32_t n_big = nbm[0], n_med = nbm[1];
+    st.med_reads = n_med;
+    st.big_reads = n_big;
+    PN_CUDA(cudaEventRecord(kev[8], s));
+    if (n_med) {
+        static bool attr_set = false;  // opt in to the block path's shared memory once per process
+        if (!attr_set) {
+            PN_CUDA(cudaFuncSetAttribute(windows_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmem));
+            attr_set = true;
+        }
+        // keys as strand << sbit | biased diagonal: 33 bits when the reference allows
+        const int sbit = (n + (uint64_t)kDiagBias + 1) < (1ull << 32) ? 32 : 40;
+        windows_med_k<<<grid_for(n_med, 1, (unsigned)sm_count()), kMedThreads, kMedSmem, s>>>(
+            binned.p, med_list.p, n_med, WP, nbig.p + 2, sbit);
+        PN_CHECK_LAUNCH();
+    }
+    PN_CUDA(cudaEventRecord(kev[9], s));
     if (n_big) {
         DBuf<uint64_t> goff((uint64_t)n_big + 1, s);
         exclusive_scan(BigSize{big_list.p, roff.p}, ArrayOut<uint64_t>{goff.p}, n_big, tot.p, s);
@@ -1394,6 +1724,8 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     cudaEventElapsedTime(&st.ms_scan_kernel, kev[0], kev[1]);
     cudaEventElapsedTime(&st.ms_verify_kernel, kev[2], kev[3]);
     cudaEventElapsedTime(&st.ms_probe_kernel, kev[0], kev[7]);
+    cudaEventElapsedTime(&st.ms_windows_med, kev[8], kev[9]);
+    cudaEventElapsedTime(&st.ms_windows_big, kev[9], kev[4]);
     cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
     cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
     cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);

@@ -195,6 +195,20 @@ def test_uneven_lengths_scaled(gpu):
     assert_same_hits(got, want)
 
 
+@pytest.mark.parametrize("q,stride", [(8, 1), (8, 2), (6, 1), (6, 3)])
+def test_hit_heavy_reads_take_every_window_path(gpu, q, stride):
+    """Short q on a 1 Mbp reference: ~2,800 (q = 8) and ~46,000 (q = 6) q-gram hits per read, so
+    reads go through the warp, block (<= 16,384 hits) and global (radix-sorted) window paths."""
+    ref, reads, w = synth.make_workload("repeat_100mbp_1m", ref_len=1_000_000, n_reads=300)
+    for mode in ("all", "best"):
+        want = oracle.map_filter(ref, reads.seq, reads.offsets, 5, q, mode)
+        B = gpu.index_reads(gpu.pack_reference(ref), reads.seq, reads.offsets, q, k=5, stride=stride)
+        got = gpu.map(B.ref, B, mode)
+        assert_same_hits(got, want)
+    st = gpu.get_map_stats(B)
+    assert st["hits"] > reads.n * (2000 if q == 8 else 20000) / stride
+
+
 def test_candidates_cover_every_true_end(gpu):
     ref, reads, w = synth.make_workload("repeat_100mbp_1m", ref_len=500_000, n_reads=800)
     ends = oracle.map_filter(ref, reads.seq, reads.offsets, 5, 16, "ends")
