@@ -154,8 +154,15 @@ def traffic_per_unit(name: str, kernel_src_sha: str):
 
 
 def source_sha() -> str:
+    """Hash of the verification kernel's source: the bit-vector verification section of map.cu
+    (up to the best-stratum section) and the shared primitives."""
     h = hashlib.sha256()
-    for f in ("map.cu", "prims.cuh", "internal.cuh"):
+    with open(os.path.join(ROOT, "paper_1403_1706_gb300", "csrc", "map.cu"), "rb") as fh:
+        src = fh.read()
+    a = src.index(b"// ---- bit-vector verification")
+    b = src.index(b"// ---- best stratum", a)
+    h.update(src[a:b])
+    for f in ("prims.cuh", "internal.cuh"):
         with open(os.path.join(ROOT, "paper_1403_1706_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
