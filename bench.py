@@ -55,7 +55,7 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=1 << 20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-slice", type=int, default=30_000_000,
+    ap.add_argument("--cpu-slice", type=int, default=100_000_000,
                     help="reference prefix (bp) of the CPU-baseline sample")
     ap.add_argument("--mode", choices=["plain", "batched", "serve"], default="plain",
                     help="plain: one batch per launch sequence (the headline); batched: uneven batches of "
@@ -380,6 +380,7 @@ def run_batched(args, rank, world, local):
         dt_b, n_b, launches_b = timed(lambda: engine_step()[0])
     clocks = clk.summary()
     dt_p, n_p, launches_p = timed(lambda: plain_step()[0])
+    engine_host_step()  # warm-up of the host path (page-locked result blocks)
     dt_e, n_e, _ = timed(engine_host_step)
     st = E.stats()
     bases = sum_over_ranks(sum(int(x.size) for x in seqs), device="cuda")
@@ -676,7 +677,8 @@ def main():
             clk.__exit__()
         e1 = E.stats()
         delta = {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
-                                               "bases_scanned", "ms_verify_kernel", "ms_scan_kernel")}
+                                               "bases_scanned", "ms_verify_kernel", "ms_scan_kernel",
+                                               "ms_admit", "ms_launch", "ms_assemble")}
         ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
         return ms, n, peanut.kernel_launches() - l0, delta, (clk.summary() if clk else None)
 
@@ -690,11 +692,13 @@ def main():
     # end to end through the host API (engine submissions from pinned host memory)
     e2e = None
     if not args.no_e2e:
-        ems, n_res_h, _, _, _ = timed(step_engine_host)
+        step_engine_host()  # warm-up of the host path (page-locked result blocks)
+        ems, n_res_h, _, hdelta, _ = timed(step_engine_host)
         h2d = sum(int(bt["h_seq"].nbytes) + int(bt["h_off"].nbytes) for bt in batches)
         e2e = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems,
-               "api": "peanut_engine_submit + peanut_engine_wait"}
+               "api": "peanut_engine_submit + peanut_engine_wait",
+               "executor_ms_per_step": {f[3:]: hdelta[f] / args.steps for f in ("ms_admit", "ms_launch", "ms_assemble")}}
     est = E.stats()
     E.free()
 
@@ -761,7 +765,9 @@ def main():
             "path": "engine (peanut_engine_submit_device / peanut_engine_wait)",
             "plain": plain, "vs_plain": ms_p / ms, "identical_output": identical,
             "engine": {"classes": est["classes"], "launches": est["launches"],
-                       "hbm_reserved_peak": est["hbm_reserved_peak"]},
+                       "hbm_reserved_peak": est["hbm_reserved_peak"],
+                       "executor_ms_per_step": {f[3:]: edelta[f] / args.steps
+                                                for f in ("ms_admit", "ms_launch", "ms_assemble")}},
             "results_per_step": int(n_eng), "bases_per_s": bases / (ms / 1e3),
             "setup_s": {"generate": t_gen, "pack": t_pack, "warmup": t_warm},
         }

@@ -288,6 +288,9 @@ typedef struct {
     uint64_t map_runs, hits, candidates, candidate_word_columns, present_probes, results;
     uint64_t bases_scanned;   /* reference bases streamed by the scans */
     double ms_verify_kernel, ms_scan_kernel, ms_probe_kernel; /* CUDA-event sums per kernel */
+    /* executor wall time (ms, summed over executors): admitting submissions (copy in, classify),
+       launches (gather, index, map), assembling results (renumber, sort, strata, copy out) */
+    double ms_admit, ms_launch, ms_assemble;
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with

@@ -244,6 +244,10 @@ struct Segment {
     uint32_t cls, x0, n, base;
 };
 
+static double wall_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 }  // namespace pn
 
 struct peanut_engine {
@@ -268,6 +272,7 @@ struct peanut_engine {
         uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
         uint64_t bases_scanned = 0, runs = 0;
         double ms_verify = 0, ms_scan = 0, ms_probe = 0;
+        double ms_admit = 0, ms_launch = 0, ms_assemble = 0;  // executor wall time per phase
     } sum;
 };
 
@@ -668,6 +673,7 @@ static void executor(peanut_engine* E, int idx) {
                 lk.unlock();
                 peanut_status st = PEANUT_OK;
                 std::string msg;
+                const double t0 = wall_ms();
                 try {
                     admit(E, S, s);
                 } catch (const Fail& f) {
@@ -678,6 +684,7 @@ static void executor(peanut_engine* E, int idx) {
                     msg = "admission failed";
                 }
                 lk.lock();
+                E->sum.ms_admit += wall_ms() - t0;
                 E->running--;
                 if (st != PEANUT_OK) {
                     set_failed(S, st, msg.c_str());
@@ -755,6 +762,7 @@ static void executor(peanut_engine* E, int idx) {
         std::vector<std::pair<uint32_t, uint32_t>> tried;
         uint32_t bq = C.q, bs = C.stride;
         float bpred = 0;
+        const double t_launch = wall_ms();
         try {
             L = run_launch(E, c, segs, taken, tune, q_use, stride_use, s, &tried, &bq, &bs, &bpred);
         } catch (const Fail& f) {
@@ -766,6 +774,7 @@ static void executor(peanut_engine* E, int idx) {
         }
 
         lk.lock();
+        E->sum.ms_launch += wall_ms() - t_launch;
         E->running--;
         E->reserved -= need;
         if (tune) {
@@ -827,6 +836,7 @@ static void executor(peanut_engine* E, int idx) {
             E->running++;
             lk.unlock();
             std::vector<std::pair<peanut_status, std::string>> res(ready.size());
+            const double t_asm = wall_ms();
             for (size_t i = 0; i < ready.size(); ++i) {
                 try {
                     assemble(E, ready[i], s);
@@ -837,6 +847,7 @@ static void executor(peanut_engine* E, int idx) {
                 }
             }
             lk.lock();
+            E->sum.ms_assemble += wall_ms() - t_asm;
             E->running--;
             for (size_t i = 0; i < ready.size(); ++i) {
                 if (res[i].first != PEANUT_OK) set_failed(ready[i], res[i].first, res[i].second.c_str());
@@ -1099,6 +1110,9 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->ms_verify_kernel = E->sum.ms_verify;
         out->ms_scan_kernel = E->sum.ms_scan;
         out->ms_probe_kernel = E->sum.ms_probe;
+        out->ms_admit = E->sum.ms_admit;
+        out->ms_launch = E->sum.ms_launch;
+        out->ms_assemble = E->sum.ms_assemble;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;
