@@ -153,6 +153,53 @@ def test_engine_device_results(gpu, world, expected):
         h.free()
 
 
+def test_engine_concurrent_clients(gpu, world, expected):
+    """Eight host threads submit and wait at the same time; every result is its own."""
+    import threading
+    ref, R, subs = world
+    E = gpu.Engine(R, k_permille=50, executors=3, max_reads=900)
+    errors, got = [], {}
+
+    def client(c):
+        try:
+            for rep in range(3):
+                i = (c + rep) % len(subs)
+                m = ("all", "best")[(c + rep) % 2]
+                t = E.submit(subs[i].seq, subs[i].offsets, m)
+                got[c, rep] = (i, m, E.wait(t))
+        except Exception as e:  # surfaced below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=client, args=(c,)) for c in range(8)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    E.free()
+    assert not errors, errors
+    assert len(got) == 24
+    for (c, rep), (i, m, h) in got.items():
+        assert np.array_equal(h, expected[i, m]), (c, rep)
+
+
+def test_engine_release_with_work_in_flight(gpu, world, expected):
+    """Releasing an engine with submissions queued, running or unclaimed neither hangs nor
+    leaks into a later engine."""
+    ref, R, subs = world
+    for executors in (1, 2):
+        E = gpu.Engine(R, k_permille=50, executors=executors, max_reads=300)
+        for s in subs:
+            E.submit(s.seq, s.offsets, "all")
+        E.submit(subs[1].seq, subs[1].offsets, "best")
+        E.free()
+    E = gpu.Engine(R, k_permille=50, executors=2)
+    try:
+        assert np.array_equal(E.wait(E.submit(subs[4].seq, subs[4].offsets, "best")), expected[4, "best"])
+        assert E.wait(E.submit(subs[0].seq, subs[0].offsets, "all"), timeout_ms=60000) is not None
+    finally:
+        E.free()
+
+
 def test_engine_bad_submission_fails_alone(gpu, world, expected):
     ref, R, subs = world
     bad_seq = subs[2].seq.copy()
