@@ -678,7 +678,7 @@ def main():
         e1 = E.stats()
         delta = {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
                                                "bases_scanned", "ms_verify_kernel", "ms_scan_kernel",
-                                               "ms_admit", "ms_launch", "ms_assemble")}
+                                               "ms_admit", "ms_launch", "ms_assemble", "ms_download")}
         ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
         return ms, n, peanut.kernel_launches() - l0, delta, (clk.summary() if clk else None)
 
@@ -698,7 +698,8 @@ def main():
         e2e = {"value": units / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems,
                "api": "peanut_engine_submit + peanut_engine_wait",
-               "executor_ms_per_step": {f[3:]: hdelta[f] / args.steps for f in ("ms_admit", "ms_launch", "ms_assemble")}}
+               "engine_ms_per_step": {f[3:]: hdelta[f] / args.steps
+                                      for f in ("ms_admit", "ms_launch", "ms_assemble", "ms_download")}}
     est = E.stats()
     E.free()
 
@@ -766,8 +767,8 @@ def main():
             "plain": plain, "vs_plain": ms_p / ms, "identical_output": identical,
             "engine": {"classes": est["classes"], "launches": est["launches"],
                        "hbm_reserved_peak": est["hbm_reserved_peak"],
-                       "executor_ms_per_step": {f[3:]: edelta[f] / args.steps
-                                                for f in ("ms_admit", "ms_launch", "ms_assemble")}},
+                       "engine_ms_per_step": {f[3:]: edelta[f] / args.steps
+                                              for f in ("ms_admit", "ms_launch", "ms_assemble", "ms_download")}},
             "results_per_step": int(n_eng), "bases_per_s": bases / (ms / 1e3),
             "setup_s": {"generate": t_gen, "pack": t_pack, "warmup": t_warm},
         }

@@ -288,9 +288,10 @@ typedef struct {
     uint64_t map_runs, hits, candidates, candidate_word_columns, present_probes, results;
     uint64_t bases_scanned;   /* reference bases streamed by the scans */
     double ms_verify_kernel, ms_scan_kernel, ms_probe_kernel; /* CUDA-event sums per kernel */
-    /* executor wall time (ms, summed over executors): admitting submissions (copy in, classify),
-       launches (gather, index, map), assembling results (renumber, sort, strata, copy out) */
-    double ms_admit, ms_launch, ms_assemble;
+    /* wall time (ms): the I/O thread admitting submissions (copy in, classify) and copying
+       results to the host; the executors (summed) running launches (gather, index, map) and
+       assembling results (renumber, sort, strata) */
+    double ms_admit, ms_launch, ms_assemble, ms_download;
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with
@@ -298,7 +299,7 @@ typedef struct {
 #define PEANUT_RESULT_ON_DEVICE 0x100
 
 /* Creates an engine over a resident reference (which must outlive it) and starts its executor
- * threads.  Errors: INVALID_ARG (bad reference or parameters), NO_MEMORY, CUDA_ERROR. */
+ * threads and its I/O thread (every host<->device copy: admissions and results).  Errors: INVALID_ARG (bad reference or parameters), NO_MEMORY, CUDA_ERROR. */
 peanut_status peanut_engine_create(const peanut_ref* ref, const peanut_engine_params* p, peanut_engine** out);
 
 /* Queues a submission of host reads (layout as in peanut_index_reads; n_reads 1 .. 2^24) in

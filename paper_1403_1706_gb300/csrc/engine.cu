@@ -244,6 +244,12 @@ struct Segment {
     uint32_t cls, x0, n, base;
 };
 
+struct Download {  // an assembled result on its way to the host
+    Submission* sub = nullptr;
+    DeviceHits* fin = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded after the assembly on the executor's stream
+};
+
 static double wall_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -267,12 +273,14 @@ struct peanut_engine {
     bool stop = false;
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;
+    cudaStream_t io_stream = nullptr;
+    std::deque<pn::Download> downloads;  // results waiting for the I/O thread
     uint64_t n_submitted = 0, n_completed = 0, n_reads = 0, n_launches = 0, n_tuning = 0;
     struct {
         uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
         uint64_t bases_scanned = 0, runs = 0;
         double ms_verify = 0, ms_scan = 0, ms_probe = 0;
-        double ms_admit = 0, ms_launch = 0, ms_assemble = 0;  // executor wall time per phase
+        double ms_admit = 0, ms_launch = 0, ms_assemble = 0, ms_download = 0;  // wall time per phase
     } sum;
 };
 
@@ -382,8 +390,9 @@ static void admit(peanut_engine* E, Submission* S, cudaStream_t s) {
     S->remaining = n;
 }
 
-// Renumbers, sorts and downloads a submission's results (no engine lock held).
-static void assemble(peanut_engine* E, Submission* S, cudaStream_t s) {
+// Renumbers and sorts a submission's results into its own read ids and applies the best stratum
+// if asked (no engine lock held); returns them in device memory, complete when s is.
+static DeviceHits* assemble(peanut_engine* E, Submission* S, cudaStream_t s) {
     std::sort(S->parts.begin(), S->parts.end(), [](const Part& a, const Part& b) {
         return a.cls != b.cls ? a.cls < b.cls : a.x0 < b.x0;
     });
@@ -428,24 +437,13 @@ static void assemble(peanut_engine* E, Submission* S, cudaStream_t s) {
             fin->h = all.h;
             all.h = peanut_device_hits{};
         }
-        if (S->on_device) {
-            PN_CUDA(cudaStreamSynchronize(s));
-            fin->stream = nullptr;  // the caller may free it after the engine (and its streams) are gone
-            S->dresult = fin;
-            fin = nullptr;
-        } else {
-            S->result = download_hits(fin->h, s);
-            free_device_hits(fin);
-            delete fin;
-        }
     } catch (...) {
         free_device_hits(&all);
-        if (fin) {
-            free_device_hits(fin);
-            delete fin;
-        }
+        free_device_hits(fin);
+        delete fin;
         throw;
     }
+    return fin;
 }
 
 struct LaunchOut {
@@ -654,56 +652,7 @@ static void executor(peanut_engine* E, int idx) {
             E->cv_work.wait(lk);
             continue;
         }
-        // 1. admission, in submission order, while the footprint fits
-        if (!E->pending.empty()) {
-            Submission* S = E->pending.front();
-            const uint64_t need = admission_bytes(S);
-            if (need > E->budget) {
-                E->pending.pop_front();
-                set_failed(S, PEANUT_NO_MEMORY, "submission does not fit the engine's device-memory budget");
-                finish(E, S);
-                continue;
-            }
-            if (E->reserved + need <= E->budget || E->running == 0) {
-                E->pending.pop_front();
-                E->reserved += need;
-                E->reserved_peak = std::max(E->reserved_peak, E->reserved);
-                S->reserved = need;
-                E->running++;
-                lk.unlock();
-                peanut_status st = PEANUT_OK;
-                std::string msg;
-                const double t0 = wall_ms();
-                try {
-                    admit(E, S, s);
-                } catch (const Fail& f) {
-                    st = f.st;
-                    msg = peanut_last_error();
-                } catch (...) {
-                    st = PEANUT_CUDA_ERROR;
-                    msg = "admission failed";
-                }
-                lk.lock();
-                E->sum.ms_admit += wall_ms() - t0;
-                E->running--;
-                if (st != PEANUT_OK) {
-                    set_failed(S, st, msg.c_str());
-                    finish(E, S);
-                } else {
-                    S->order = E->next_order++;
-                    for (int c = 1; c < kQSlots; ++c) {
-                        if (!S->cnt[c]) continue;
-                        ClassState& C = E->cls[c];
-                        C.queue.push_back(S);
-                        C.waiting += S->cnt[c];
-                        for (int w = 0; w < 8; ++w) C.lenmask[w] |= S->lenmask[c][w];
-                    }
-                }
-                E->cv_work.notify_all();
-                continue;
-            }
-        }
-        // 2. a launch from the class with the oldest waiting reads
+        // a launch from the class with the oldest waiting reads
         const int c = pick_class(E);
         if (c < 0) {
             E->cv_work.wait(lk);
@@ -836,10 +785,19 @@ static void executor(peanut_engine* E, int idx) {
             E->running++;
             lk.unlock();
             std::vector<std::pair<peanut_status, std::string>> res(ready.size());
+            std::vector<Download> outs(ready.size());
             const double t_asm = wall_ms();
             for (size_t i = 0; i < ready.size(); ++i) {
                 try {
-                    assemble(E, ready[i], s);
+                    DeviceHits* fin = assemble(E, ready[i], s);
+                    outs[i].fin = fin;
+                    if (ready[i]->on_device) {
+                        PN_CUDA(cudaStreamSynchronize(s));
+                        fin->stream = nullptr;  // the caller may free it after the engine is gone
+                    } else {
+                        PN_CUDA(cudaEventCreateWithFlags(&outs[i].ready, cudaEventDisableTiming));
+                        PN_CUDA(cudaEventRecord(outs[i].ready, s));
+                    }
                 } catch (const Fail& f) {
                     res[i] = {f.st, peanut_last_error()};
                 } catch (...) {
@@ -850,11 +808,114 @@ static void executor(peanut_engine* E, int idx) {
             E->sum.ms_assemble += wall_ms() - t_asm;
             E->running--;
             for (size_t i = 0; i < ready.size(); ++i) {
-                if (res[i].first != PEANUT_OK) set_failed(ready[i], res[i].first, res[i].second.c_str());
-                finish(E, ready[i]);
+                Submission* S = ready[i];
+                if (res[i].first != PEANUT_OK) {
+                    if (outs[i].fin) {
+                        free_device_hits(outs[i].fin);
+                        delete outs[i].fin;
+                    }
+                    if (outs[i].ready) cudaEventDestroy(outs[i].ready);
+                    set_failed(S, res[i].first, res[i].second.c_str());
+                    finish(E, S);
+                } else if (S->on_device) {
+                    S->dresult = outs[i].fin;
+                    finish(E, S);
+                } else {
+                    outs[i].sub = S;  // the copy to the host runs on the I/O thread
+                    E->downloads.push_back(outs[i]);
+                }
             }
         }
         E->cv_work.notify_all();
+    }
+}
+
+// The I/O thread: every host<->device copy of the engine, so that executors only launch work.
+// Results waiting to go to the host come first (they hold device memory), then admissions in
+// submission order while their footprint fits (none while a tuning run has the GPU).
+static void io_loop(peanut_engine* E) {
+    cudaSetDevice(E->device);
+    cudaStream_t s = E->io_stream;
+    std::unique_lock<std::mutex> lk(E->mu);
+    while (!E->stop) {
+        if (!E->downloads.empty()) {
+            Download D = E->downloads.front();
+            E->downloads.pop_front();
+            lk.unlock();
+            peanut_status st = PEANUT_OK;
+            std::string msg;
+            HostHits* h = nullptr;
+            const double t0 = wall_ms();
+            try {
+                PN_CUDA(cudaStreamWaitEvent(s, D.ready, 0));
+                h = download_hits(D.fin->h, s);
+            } catch (const Fail& f) {
+                st = f.st;
+                msg = peanut_last_error();
+            } catch (...) {
+                st = PEANUT_CUDA_ERROR;
+                msg = "copy of the results failed";
+            }
+            D.fin->stream = s;  // copied (or failed) on this stream: release it here
+            free_device_hits(D.fin);
+            delete D.fin;
+            cudaEventDestroy(D.ready);
+            lk.lock();
+            E->sum.ms_download += wall_ms() - t0;
+            if (st != PEANUT_OK) set_failed(D.sub, st, msg.c_str());
+            else D.sub->result = h;
+            finish(E, D.sub);
+            continue;
+        }
+        if (!E->pending.empty() && !E->tuning_active) {
+            Submission* S = E->pending.front();
+            const uint64_t need = admission_bytes(S);
+            if (need > E->budget) {
+                E->pending.pop_front();
+                set_failed(S, PEANUT_NO_MEMORY, "submission does not fit the engine's device-memory budget");
+                finish(E, S);
+                continue;
+            }
+            if (E->reserved + need <= E->budget || E->running == 0) {
+                E->pending.pop_front();
+                E->reserved += need;
+                E->reserved_peak = std::max(E->reserved_peak, E->reserved);
+                S->reserved = need;
+                E->running++;
+                lk.unlock();
+                peanut_status st = PEANUT_OK;
+                std::string msg;
+                const double t0 = wall_ms();
+                try {
+                    admit(E, S, s);
+                } catch (const Fail& f) {
+                    st = f.st;
+                    msg = peanut_last_error();
+                } catch (...) {
+                    st = PEANUT_CUDA_ERROR;
+                    msg = "admission failed";
+                }
+                lk.lock();
+                E->sum.ms_admit += wall_ms() - t0;
+                E->running--;
+                if (st != PEANUT_OK) {
+                    set_failed(S, st, msg.c_str());
+                    finish(E, S);
+                } else {
+                    S->order = E->next_order++;
+                    for (int c = 1; c < kQSlots; ++c) {
+                        if (!S->cnt[c]) continue;
+                        ClassState& C = E->cls[c];
+                        C.queue.push_back(S);
+                        C.waiting += S->cnt[c];
+                        for (int w = 0; w < 8; ++w) C.lenmask[w] |= S->lenmask[c][w];
+                    }
+                }
+                E->cv_work.notify_all();
+                continue;
+            }
+        }
+        E->cv_work.wait(lk);
     }
 }
 
@@ -866,6 +927,11 @@ static void destroy_engine_impl(peanut_engine* E) {
     E->cv_work.notify_all();
     for (auto& t : E->threads)
         if (t.joinable()) t.join();
+    for (Download& D : E->downloads) {
+        free_device_hits(D.fin);
+        delete D.fin;
+        cudaEventDestroy(D.ready);
+    }
     for (auto& kv : E->subs) {
         Submission* S = kv.second;
         if (S->result) free_host_hits(S->result);
@@ -878,6 +944,10 @@ static void destroy_engine_impl(peanut_engine* E) {
     for (auto& s : E->streams) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
+    }
+    if (E->io_stream) {
+        cudaStreamSynchronize(E->io_stream);
+        cudaStreamDestroy(E->io_stream);
     }
     E->magic = 0;
     delete E;
@@ -961,7 +1031,9 @@ peanut_status peanut_engine_create(const peanut_ref* ref, const peanut_engine_pa
                 PN_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
                 E->streams.push_back(s);
             }
+            PN_CUDA(cudaStreamCreateWithFlags(&E->io_stream, cudaStreamNonBlocking));
             for (uint32_t i = 0; i < E->p.executors; ++i) E->threads.emplace_back(executor, E, (int)i);
+            E->threads.emplace_back(io_loop, E);
         } catch (...) {
             destroy_engine_impl(E);
             throw;
@@ -1113,6 +1185,7 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->ms_admit = E->sum.ms_admit;
         out->ms_launch = E->sum.ms_launch;
         out->ms_assemble = E->sum.ms_assemble;
+        out->ms_download = E->sum.ms_download;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

@@ -1194,6 +1194,23 @@ struct MyersShared {
         score += wide_step<W>(Pv, Mv, e, lastbit);
         return score;
     }
+    // The recurrence alone, without tracking E[m][j] (warm-up columns).
+    __device__ __forceinline__ void advance(uint32_t c) {
+        uint64_t e[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) e[w] = seq[(c * kMaxWords + w) * kVerifyThreads];
+        (void)wide_step<W>(Pv, Mv, e, lastbit);
+    }
+    // E[m][j] from the vertical deltas: E[0][j] = 0 and rows 1..m add +1 (Pv) or -1 (Mv).
+    __device__ __forceinline__ void rescore() {
+        int32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const uint64_t rows = (w < W - 1 || lastbit == 63) ? ~0ull : ((1ull << (lastbit + 1)) - 1);
+            v += __popcll(Pv[w] & rows) - __popcll(Mv[w] & rows);
+        }
+        score = v;
+    }
 };
 
 // Verifies one candidate range: columns a .. hi of the pattern's semiglobal matrix, runs of ends
@@ -1253,11 +1270,12 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
         }
     };
     int64_t j = a;
-    // warm-up: head of the first word, then whole words, then the tail
+    // warm-up: head of the first word, then whole words, then the tail; the score is recovered
+    // from the bit vectors at the end
     if (j < lo) {
         uint32_t word = __ldg(V.packed + (j >> 4)) << (2 * (uint32_t)(j & 15));
         while (j < lo && (j & 15)) {
-            M.step(word >> 30);
+            M.advance(word >> 30);
             word <<= 2;
             ++j;
         }
@@ -1266,7 +1284,7 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
             uint32_t wd = __ldg(V.packed + (j >> 4));
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                M.step(wd >> 30);
+                M.advance(wd >> 30);
                 wd <<= 2;
             }
             j += 16;
@@ -1274,11 +1292,12 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
         if (j < lo) {
             word = __ldg(V.packed + (j >> 4));
             while (j < lo) {
-                M.step(word >> 30);
+                M.advance(word >> 30);
                 word <<= 2;
                 ++j;
             }
         }
+        M.rescore();
     }
     // reported columns lo .. hi
     while (j <= hi && (j & 15)) {
