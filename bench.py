@@ -699,7 +699,8 @@ def main():
                "d2h_bytes_per_step": int(n_res_h) * HIT_BYTES, "ms_per_step": ems,
                "api": "peanut_engine_submit + peanut_engine_wait",
                "engine_ms_per_step": {f[3:]: hdelta[f] / args.steps
-                                      for f in ("ms_admit", "ms_launch", "ms_assemble", "ms_download")}}
+                                      for f in ("ms_admit", "ms_launch", "ms_assemble", "ms_download")},
+               "pageable_result_blocks": E.stats()["pageable_result_blocks"]}
     est = E.stats()
     E.free()
 

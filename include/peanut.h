@@ -292,6 +292,8 @@ typedef struct {
        results to the host; the executors (summed) running launches (gather, index, map) and
        assembling results (renumber, sort, strata) */
     double ms_admit, ms_launch, ms_assemble, ms_download;
+    uint64_t pageable_result_blocks; /* host result blocks (process-wide) that could not be
+                                        page-locked and fell back to pageable memory */
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with

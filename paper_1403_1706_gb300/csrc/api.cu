@@ -98,6 +98,7 @@ void free_device_hits(DeviceHits* H);
 static std::mutex g_pin_mu;
 static std::multimap<size_t, void*> g_pin_free;
 static size_t g_pin_kept = 0;
+static std::atomic<uint64_t> g_pageable_blocks{0};  // result blocks that could not be page-locked
 constexpr size_t kPinnedKeep = 8ull << 30;
 
 void* host_block_alloc(size_t bytes, size_t* got, bool* pinned) {
@@ -122,11 +123,14 @@ void* host_block_alloc(size_t bytes, size_t* got, bool* pinned) {
         return p;
     }
     cudaGetLastError();
+    g_pageable_blocks.fetch_add(1, std::memory_order_relaxed);
     p = malloc(bytes);
     *got = bytes;
     *pinned = false;
     return p;
 }
+
+uint64_t pageable_blocks() { return g_pageable_blocks.load(); }
 
 void host_block_free(void* p, size_t bytes, bool pinned) {
     if (!p) return;

@@ -1186,6 +1186,7 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->ms_launch = E->sum.ms_launch;
         out->ms_assemble = E->sum.ms_assemble;
         out->ms_download = E->sum.ms_download;
+        out->pageable_result_blocks = pageable_blocks();
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

@@ -217,6 +217,7 @@ namespace pn {
 void* host_block_alloc(size_t bytes, size_t* got, bool* pinned);
 void host_block_free(void* p, size_t bytes, bool pinned);
 HostHits* download_hits(const peanut_device_hits& dh, cudaStream_t s);  // synchronizes s
+uint64_t pageable_blocks();  // result blocks so far that fell back to pageable memory
 void free_host_hits(HostHits* H);
 // index.cu
 void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s);

@@ -553,11 +553,110 @@ __device__ void block_sweep(const uint64_t* keys, uint32_t h, uint32_t r, const 
     __syncthreads();
 }
 
+// Stable LSD radix sort of h <= kMedCap keys in shared memory (bufA) by bits [lo_bit, hi_bit),
+// 8-bit digits: every warp ranks a contiguous chunk of keys in 32-key rounds (eight ballots find
+// the lanes with equal digits, a per-warp counter per digit carries over rounds), the counters
+// become digit-major, warp-minor offsets, and the keys are scattered to the other buffer.  All
+// threads of the block call it; returns the buffer that holds the sorted keys.
+__device__ uint64_t* block_radix_sort(uint64_t* bufA, uint64_t* bufB, uint16_t* cnt, uint32_t* s_tot,
+                                      uint32_t* s_part, uint32_t h, int lo_bit, int hi_bit) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t chunk = ((h + kMedWarps * 32 - 1) / (kMedWarps * 32)) * 32;  // keys per warp
+    const uint32_t w0 = (uint32_t)w * chunk, w1 = min(h, w0 + chunk);
+    uint64_t* src = bufA;
+    uint64_t* dst = bufB;
+    for (int shift = lo_bit; shift < hi_bit; shift += 8) {
+        for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        uint32_t lr[kMedRounds];
+        const int nrounds = (int)((w1 > w0 ? w1 - w0 : 0) + 31) / 32;
+#pragma unroll
+        for (int i = 0; i < kMedRounds; ++i) {
+            if (i >= nrounds) break;  // warp-uniform
+            const uint32_t idx = w0 + 32 * i + lane;
+            const bool valid = idx < w1;
+            const uint32_t dig = valid ? (uint32_t)(src[idx] >> shift) & 255u : 0u;
+            // lanes with the same digit: intersect the eight bit-ballots
+            unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+            for (int bb = 0; bb < 8; ++bb) {
+                const unsigned bal = __ballot_sync(kFull, (dig >> bb) & 1u);
+                peers &= ((dig >> bb) & 1u) ? bal : ~bal;
+            }
+            const uint32_t base = valid ? cnt[w * 256 + dig] : 0u;
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) cnt[w * 256 + dig] = (uint16_t)(base + __popc(peers));
+            __syncwarp();
+            lr[i] = base + __popc(peers & lanemask_lt());
+        }
+        __syncthreads();
+        {  // per digit: exclusive prefix over the warps, four groups of eight warps in parallel
+            const int d = threadIdx.x & 255, g = threadIdx.x >> 8;
+            uint32_t run = 0;
+#pragma unroll
+            for (int ww = 8 * g; ww < 8 * g + 8; ++ww) {
+                const uint32_t c = cnt[ww * 256 + d];
+                cnt[ww * 256 + d] = (uint16_t)run;
+                run += c;
+            }
+            s_part[g * 256 + d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const uint32_t c = s_part[g * 256 + d];
+                s_part[g * 256 + d] = run;
+                run += c;
+            }
+            s_tot[d] = run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive prefix over the digits, 8 per lane
+            uint32_t v[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                v[j] = s_tot[lane * 8 + j];
+                sum += v[j];
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            uint32_t run = incl - sum;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                s_tot[lane * 8 + j] = run;
+                run += v[j];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x)
+            cnt[i] = (uint16_t)(cnt[i] + s_tot[i & 255] + s_part[(i >> 11) * 256 + (i & 255)]);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kMedRounds; ++i) {
+            if (i >= nrounds) break;
+            const uint32_t idx = w0 + 32 * i + lane;
+            if (idx < w1) {
+                const uint64_t key = src[idx];
+                dst[cnt[w * 256 + ((uint32_t)(key >> shift) & 255u)] + lr[i]] = key;
+            }
+        }
+        __syncthreads();
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
 // Reads with kWinCap < hits <= kMedCap: one block each sorts them in shared memory, then the
-// block sweeps them.  The sort is a stable LSD radix sort on 8-bit digits of (strand << sbit | biased
-// diagonal): every warp ranks a contiguous chunk of keys in 32-key rounds (__match_any_sync for
-// equal digits, a per-warp counter per digit), the counters become digit-major, warp-minor
-// offsets, and the keys are scattered to the other buffer.
+// block sweeps them; the sort key is strand << sbit | biased diagonal.
 __global__ void __launch_bounds__(kMedThreads, 1)
     windows_med_k(const uint64_t* __restrict__ binned, const uint32_t* __restrict__ list, uint32_t n_list,
                   WinParams P, uint32_t* cursor, int sbit) {
@@ -569,7 +668,6 @@ __global__ void __launch_bounds__(kMedThreads, 1)
     __shared__ uint32_t s_tot[256];
     __shared__ uint32_t s_part[4 * 256];
     __shared__ int32_t s_sci[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint64_t low = (1ull << sbit) - 1;
     for (;;) {
         if (threadIdx.x == 0) s_next = atomicAdd(cursor, 1u);  // reads of uneven size: dynamic order
@@ -583,97 +681,7 @@ __global__ void __launch_bounds__(kMedThreads, 1)
             const uint64_t k0 = binned[b + i];
             bufA[i] = (((k0 >> 40) & 1ull) << sbit) | (k0 & kPosMask40);
         }
-        const uint32_t chunk = ((h + kMedWarps * 32 - 1) / (kMedWarps * 32)) * 32;  // keys per warp
-        const uint32_t w0 = (uint32_t)w * chunk, w1 = min(h, w0 + chunk);
-        uint64_t* src = bufA;
-        uint64_t* dst = bufB;
-        for (int shift = 0; shift <= sbit; shift += 8) {
-            for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x) cnt[i] = 0;
-            __syncthreads();
-            uint32_t lr[kMedRounds];
-            const int nrounds = (int)((w1 > w0 ? w1 - w0 : 0) + 31) / 32;
-#pragma unroll
-            for (int i = 0; i < kMedRounds; ++i) {
-                if (i >= nrounds) break;  // warp-uniform
-                const uint32_t idx = w0 + 32 * i + lane;
-                const bool valid = idx < w1;
-                const uint32_t dig = valid ? (uint32_t)(src[idx] >> shift) & 255u : 0u;
-                // lanes with the same digit: intersect the eight bit-ballots
-                unsigned peers = __ballot_sync(kFull, valid);
-#pragma unroll
-                for (int bb = 0; bb < 8; ++bb) {
-                    const unsigned bal = __ballot_sync(kFull, (dig >> bb) & 1u);
-                    peers &= ((dig >> bb) & 1u) ? bal : ~bal;
-                }
-                const uint32_t base = valid ? cnt[w * 256 + dig] : 0u;
-                __syncwarp();
-                if (valid && lane == __ffs(peers) - 1) cnt[w * 256 + dig] = (uint16_t)(base + __popc(peers));
-                __syncwarp();
-                lr[i] = base + __popc(peers & lanemask_lt());
-            }
-            __syncthreads();
-            {  // per digit: exclusive prefix over the warps, four groups of eight warps in parallel
-                const int d = threadIdx.x & 255, g = threadIdx.x >> 8;
-                uint32_t run = 0;
-#pragma unroll
-                for (int ww = 8 * g; ww < 8 * g + 8; ++ww) {
-                    const uint32_t c = cnt[ww * 256 + d];
-                    cnt[ww * 256 + d] = (uint16_t)run;
-                    run += c;
-                }
-                s_part[g * 256 + d] = run;
-            }
-            __syncthreads();
-            if (threadIdx.x < 256) {
-                const int d = threadIdx.x;
-                uint32_t run = 0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    const uint32_t c = s_part[g * 256 + d];
-                    s_part[g * 256 + d] = run;
-                    run += c;
-                }
-                s_tot[d] = run;
-            }
-            __syncthreads();
-            if (threadIdx.x < 32) {  // exclusive prefix over the digits, 8 per lane
-                uint32_t v[8], sum = 0;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    v[j] = s_tot[lane * 8 + j];
-                    sum += v[j];
-                }
-                uint32_t incl = sum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                uint32_t run = incl - sum;
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    s_tot[lane * 8 + j] = run;
-                    run += v[j];
-                }
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < kMedWarps * 256; i += blockDim.x)
-                cnt[i] = (uint16_t)(cnt[i] + s_tot[i & 255] + s_part[(i >> 11) * 256 + (i & 255)]);
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < kMedRounds; ++i) {
-                if (i >= nrounds) break;
-                const uint32_t idx = w0 + 32 * i + lane;
-                if (idx < w1) {
-                    const uint64_t key = src[idx];
-                    dst[cnt[w * 256 + ((uint32_t)(key >> shift) & 255u)] + lr[i]] = key;
-                }
-            }
-            __syncthreads();
-            uint64_t* t = src;
-            src = dst;
-            dst = t;
-        }
+        uint64_t* src = block_radix_sort(bufA, bufB, cnt, s_tot, s_part, h, 0, sbit + 1);
         for (uint32_t i = threadIdx.x; i < h; i += blockDim.x) {  // back to strand << 40
             const uint64_t k1 = src[i];
             src[i] = ((k1 >> sbit) << 40) | (k1 & low);
@@ -777,18 +785,6 @@ __device__ void lc_lists(const LcParams& L, uint32_t r, uint32_t s, F&& visit) {
         for (uint32_t fr = 0; fr < 2; ++fr)
             if (mn[fr] != INT64_MAX) visit(L.grp_off[2 * phi + fr], L.grp_off[2 * phi + fr + 1], mn[fr], mx[fr]);
     }
-}
-
-__device__ __forceinline__ bool span_of(const LcParams& L, uint64_t c, int64_t imin, int64_t imax, int64_t m,
-                                        int64_t k, int64_t* lo, int64_t* hi) {
-    const int64_t n = (int64_t)L.n;
-    int64_t a = (int64_t)L.cl_lo[c] - imax + m - 1 - 2 * k;
-    int64_t b = (int64_t)L.cl_hi[c] - imin + m - 1 + k;
-    if (a < 0) a = 0;
-    if (b > n - 1) b = n - 1;
-    *lo = a;
-    *hi = b;
-    return a <= b;
 }
 
 // One list of clusters to verify for a (read, strand): clusters [cb, ce) of one (q-gram,
@@ -918,11 +914,12 @@ constexpr int kMergeBuf = 16;   // ranges buffered per source (8 KB per warp)
 // ranges are merged, so every maximal run of end positions lies in one output range.
 __global__ void __launch_bounds__(kMergeWarps * 32)
     lc_kmerge_k(LcParams L, const uint64_t* doff, LcDesc* desc, const uint64_t* off, uint64_t* olo, uint64_t* ohi,
-                uint32_t* ocnt) {
+                uint32_t* ocnt, const uint32_t* ylist, uint32_t ny) {
     __shared__ int64_t blo[kMergeWarps][32][kMergeBuf], bhi[kMergeWarps][32][kMergeBuf];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < 2 * L.n_list; y += nw) {
+    for (uint32_t yi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; yi < ny; yi += nw) {
+        const uint32_t y = ylist[yi];
         const uint32_t r = L.list[y >> 1], s = y & 1;
         const int64_t m = L.len[r], k = L.kk[r];
         const uint64_t d0 = doff[y], d1 = doff[y + 1];
@@ -1010,6 +1007,170 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
             ocnt[y] = M.cnt + (M.open ? 1 : 0);
         }
         __syncwarp();
+    }
+}
+
+// ---- low-complexity merge, block path -------------------------------------------------------
+//
+// Most segments hold at most kMedCap ranges.  Their ranges (counting-filter ranges and every
+// cluster range) are written as keys lo << 24 | (hi - lo), sorted by lo in shared memory by one
+// block, and merged with a block-wide max-scan of hi: range j opens a merged range exactly when
+// its lo lies beyond the largest hi before it by more than m + k, and that largest hi closes the
+// previous merged range.  Segments with more ranges, or with a range of 2^24 bases or more, keep
+// the k-way merge.
+
+constexpr uint64_t kLcWide = (1ull << 24) - 1;  // widths from here on do not fit the key
+constexpr uint64_t kLcDrop = ~0ull;             // a range clipped away (sorts last, skipped)
+
+__device__ __forceinline__ int64_t block_excl_max64(int64_t v, int64_t* sc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl = max(incl, t);
+    }
+    if (lane == 31) sc[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t y = sc[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(kFull, y, o);
+            if (lane >= o) y = max(y, t);
+        }
+        sc[lane] = y;
+    }
+    __syncthreads();
+    int64_t before = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0) before = INT64_MIN;
+    const int64_t r = max(before, w ? sc[w - 1] : INT64_MIN);
+    __syncthreads();
+    return r;
+}
+
+// One warp per segment: its ranges as sort keys at off[y]; wide[y] = 1 if a range does not fit.
+__global__ void lc_gather_k(LcParams L, const uint64_t* __restrict__ doff, const LcDesc* __restrict__ desc,
+                            const uint64_t* __restrict__ off, uint64_t* keys, uint32_t* wide) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < 2 * L.n_list; y += nw) {
+        const uint32_t r = L.list[y >> 1], s = y & 1;
+        const int64_t m = L.len[r], k = L.kk[r];
+        uint64_t at = off[y];
+        bool wd = false;
+        auto put = [&](int64_t lo, int64_t hi, uint64_t pos) {
+            uint64_t key = kLcDrop;
+            if (lo <= hi) {
+                const uint64_t width = (uint64_t)(hi - lo);
+                if (width >= kLcWide) wd = true;
+                key = ((uint64_t)lo << 24) | (width < kLcWide ? width : kLcWide);
+            }
+            keys[pos] = key;
+        };
+        const uint64_t w0 = L.roff[r] + (s == 0 ? 0 : L.wcnt[2 * r]), nwr = L.wcnt[2 * r + s];
+        for (uint64_t e = lane; e < nwr; e += 32)
+            put((int64_t)(L.wlo[w0 + e] & kPosMask40), (int64_t)L.whi[w0 + e], at + e);
+        at += nwr;
+        for (uint64_t d = doff[y]; d < doff[y + 1]; ++d) {
+            const LcDesc D = desc[d];
+            for (uint64_t c = D.cb + lane; c < D.ce; c += 32) {
+                int64_t lo, hi;
+                cluster_range(L, c, D.imin, D.imax, m, k, &lo, &hi);
+                put(lo, hi, at + (c - D.cb));
+            }
+            at += D.ce - D.cb;
+        }
+        if (__any_sync(kFull, wd) && lane == 0) wide[y] = 1;
+    }
+}
+
+// One block per segment (dynamic order): sort its keys by lo, merge, write the merged ranges to
+// olo / ohi at off[y] and their number to ocnt[y].  Segments left for the k-way merge go to
+// rest_list (count in rest[0]); cursor is rest[1].
+__global__ void __launch_bounds__(kMedThreads, 1)
+    lc_merge_med_k(LcParams L, const uint64_t* __restrict__ off, const uint64_t* __restrict__ keys,
+                   const uint32_t* __restrict__ wide, int hi_bit, uint64_t* olo, uint64_t* ohi, uint32_t* ocnt,
+                   uint32_t* rest_list, uint32_t* rest) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* bufA = sm;
+    uint64_t* bufB = sm + kMedCap;
+    uint16_t* cnt = reinterpret_cast<uint16_t*>(sm + 2 * kMedCap);
+    __shared__ uint32_t s_next, s_nv;
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_part[4 * 256];
+    __shared__ int64_t s_sc64[32];
+    __shared__ int64_t s_top;
+    const uint32_t nseg = 2 * L.n_list;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(rest + 1, 1u);
+        __syncthreads();
+        const uint32_t y = s_next;
+        if (y >= nseg) break;
+        const uint64_t base = off[y];
+        const uint64_t hall = off[y + 1] - base;
+        const uint32_t h = hall > kMedCap ? kMedCap + 1 : (uint32_t)hall;
+        if (h > kMedCap || wide[y]) {
+            if (threadIdx.x == 0) rest_list[atomicAdd(rest, 1u)] = y;
+            __syncthreads();
+            continue;
+        }
+        const uint32_t r = L.list[y >> 1];
+        const int64_t join = (int64_t)L.len[r] + L.kk[r];
+        if (threadIdx.x == 0) s_nv = 0;
+        __syncthreads();
+        uint32_t nv = 0;
+        for (uint32_t i = threadIdx.x; i < h; i += blockDim.x) {
+            const uint64_t key = keys[base + i];
+            bufA[i] = key;
+            nv += key != kLcDrop ? 1u : 0u;
+        }
+        atomicAdd(&s_nv, nv);
+        uint64_t* src = block_radix_sort(bufA, bufB, cnt, s_tot, s_part, h, 24, hi_bit);
+        const uint32_t hv = s_nv;  // valid ranges, sorted by lo ahead of the dropped ones
+        const uint32_t E = (hv + kMedThreads - 1) / kMedThreads;
+        const uint32_t j0 = threadIdx.x * E;
+        int64_t tmax = INT64_MIN;
+        for (uint32_t e = 0; e < E; ++e) {
+            const uint32_t j = j0 + e;
+            if (j < hv) {
+                const uint64_t key = src[j];
+                tmax = max(tmax, (int64_t)(key >> 24) + (int64_t)(key & kLcWide));
+            }
+        }
+        const int64_t pre = block_excl_max64(tmax, s_sc64);
+        uint32_t ns = 0;
+        int64_t run = pre;
+        for (uint32_t e = 0; e < E; ++e) {
+            const uint32_t j = j0 + e;
+            if (j >= hv) break;
+            const uint64_t key = src[j];
+            const int64_t lo = (int64_t)(key >> 24), hi = lo + (int64_t)(key & kLcWide);
+            if (j == 0 || lo > run + join) ++ns;
+            run = max(run, hi);
+        }
+        uint32_t total = 0;
+        uint32_t idx = block_excl_sum(ns, s_tot, &total);
+        run = pre;
+        for (uint32_t e = 0; e < E; ++e) {
+            const uint32_t j = j0 + e;
+            if (j >= hv) break;
+            const uint64_t key = src[j];
+            const int64_t lo = (int64_t)(key >> 24), hi = lo + (int64_t)(key & kLcWide);
+            if (j == 0 || lo > run + join) {
+                olo[base + idx] = (uint64_t)lo;
+                if (idx > 0) ohi[base + idx - 1] = (uint64_t)run;
+                ++idx;
+            }
+            run = max(run, hi);
+        }
+        if (threadIdx.x == kMedThreads - 1) s_top = max(pre, tmax);  // the largest hi of all
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (total) ohi[base + total - 1] = (uint64_t)s_top;
+            ocnt[y] = total;
+        }
+        __syncthreads();
     }
 }
 
@@ -1643,9 +1804,34 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         lc_keys.alloc(ncap ? ncap : 1, s);
         lc_vals.alloc(ncap ? ncap : 1, s);
         lcnt.alloc(nseg, s);
-        lc_kmerge_k<<<grid_for(nseg * 32, kMergeWarps * 32, (unsigned)sm_count() * 32), kMergeWarps * 32, 0, s>>>(
-            L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p);
-        PN_CHECK_LAUNCH();
+        // block path for segments of up to kMedCap ranges, the k-way merge for the rest
+        {
+            DBuf<uint64_t> gk(ncap ? ncap : 1, s);
+            DBuf<uint32_t> wide(nseg, s), rest_list(nseg, s), rest(2, s);
+            wide.zero();
+            rest.zero();
+            lc_gather_k<<<grid_for(nseg * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(L, doff.p, desc.p,
+                                                                                          lc_off.p, gk.p, wide.p);
+            PN_CHECK_LAUNCH();
+            static bool attr_set = false;
+            if (!attr_set) {
+                PN_CUDA(cudaFuncSetAttribute(lc_merge_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kMedSmem));
+                attr_set = true;
+            }
+            int top = 24;  // key bits: lo << 24 with lo < n < 2^(top - 24), so lo never reads all ones
+            while (top < 64 && (1ull << (top - 24)) <= n) ++top;
+            lc_merge_med_k<<<grid_for(nseg, 1, (unsigned)sm_count()), kMedThreads, kMedSmem, s>>>(
+                L, lc_off.p, gk.p, wide.p, top, lc_keys.p, lc_vals.p, lcnt.p, rest_list.p, rest.p);
+            PN_CHECK_LAUNCH();
+            const uint32_t n_rest = to_host(rest.p, s);
+            if (n_rest) {
+                lc_kmerge_k<<<grid_for((uint64_t)n_rest * 32, kMergeWarps * 32, (unsigned)sm_count() * 32),
+                              kMergeWarps * 32, 0, s>>>(L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p,
+                                                        rest_list.p, n_rest);
+                PN_CHECK_LAUNCH();
+            }
+        }
         lcpos.alloc(n_reads, s);
         lcpos_k<<<grid_for(nl, 256), 256, 0, s>>>(R->lowcx_list.p, nl, lcpos.p);
         PN_CHECK_LAUNCH();

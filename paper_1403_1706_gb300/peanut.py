@@ -80,7 +80,7 @@ class EngineStats(Structure):
                 ("bases_scanned", c_uint64), ("ms_verify_kernel", ctypes.c_double),
                 ("ms_scan_kernel", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double),
                 ("ms_admit", ctypes.c_double), ("ms_launch", ctypes.c_double), ("ms_assemble", ctypes.c_double),
-                ("ms_download", ctypes.c_double)]
+                ("ms_download", ctypes.c_double), ("pageable_result_blocks", c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
