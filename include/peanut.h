@@ -107,6 +107,8 @@ typedef struct {
     float ms_probe_kernel;     /* the probe half of the reference scan (present positions) */
     float ms_windows_med, ms_windows_big; /* window paths of reads with many hits (block / global) */
     uint64_t med_reads, big_reads;        /* reads taking those paths */
+    uint64_t lowcx_rest_segments; /* (read, strand) segments of low-complexity reads too large for
+                                     the block merge (merged by the warp k-way merge) */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first

@@ -1825,6 +1825,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
                 L, lc_off.p, gk.p, wide.p, top, lc_keys.p, lc_vals.p, lcnt.p, rest_list.p, rest.p);
             PN_CHECK_LAUNCH();
             const uint32_t n_rest = to_host(rest.p, s);
+            st.lowcx_rest_segments = n_rest;
             if (n_rest) {
                 lc_kmerge_k<<<grid_for((uint64_t)n_rest * 32, kMergeWarps * 32, (unsigned)sm_count() * 32),
                               kMergeWarps * 32, 0, s>>>(L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p,

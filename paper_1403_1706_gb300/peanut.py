@@ -54,7 +54,7 @@ class MapStats(Structure):
                 ("ms_output", c_float), ("ms_scan_kernel", c_float), ("ms_verify_kernel", c_float),
                 ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float),
                 ("ms_probe_kernel", c_float), ("ms_windows_med", c_float), ("ms_windows_big", c_float),
-                ("med_reads", c_uint64), ("big_reads", c_uint64)]
+                ("med_reads", c_uint64), ("big_reads", c_uint64), ("lowcx_rest_segments", c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
