@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kScanBlock, 4)
         for (int o0 = 0; o0 < 32; o0 += 8) {
             uint32_t cc[8];
             uint32_t meta[8];  // bit 0: valid, bit 1: orientation, bit 2: palindrome
-            uint64_t fw[8];
+            uint64_t fw[8], fb[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int o = o0 + u;
@@ -135,13 +135,14 @@ __global__ void __launch_bounds__(kScanBlock, 4)
                 const bool valid = active && p0 + o < npos;
                 cc[u] = c;
                 meta[u] = (valid ? 1u : 0u) | (g > h ? 2u : 0u) | (g == h ? 4u : 0u);
-                fw[u] = valid ? ld_u64_policy(bloom + ((bloom_hash(c) >> 24) & bloom_mask), keep) : 0;
+                const uint64_t hh = bloom_hash(c);
+                fb[u] = bloom_bits(hh);
+                fw[u] = valid ? ld_u64_policy(bloom + ((hh >> 24) & bloom_mask), keep) : 0;
             }
             uint2 vv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const uint64_t fb = bloom_bits(bloom_hash(cc[u]));
-                const bool pass = (meta[u] & 1u) && (fw[u] & fb) == fb;
+                const bool pass = (meta[u] & 1u) && (fw[u] & fb[u]) == fb[u];
                 vv[u] = pass ? ld_u32x2_policy(IS + (cc[u] >> 5), stream) : make_uint2(0, 0);
             }
 #pragma unroll
@@ -903,6 +904,16 @@ __device__ void lc_kmerge_serial(const LcParams& L, uint32_t r, uint32_t s, uint
     *ocnt_y = M.cnt;
 }
 
+// Sort keys of the large segments: (2^40 - 1 - ranges) ascending = ranges descending.
+__global__ void rest_order_k(const uint32_t* list, uint32_t n, const uint64_t* off, uint64_t* key, uint64_t* y) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t s = list[i];
+    const uint64_t sz = off[s + 1] - off[s];
+    key[i] = ((1ull << 40) - 1) - (sz < (1ull << 40) - 1 ? sz : (1ull << 40) - 1);
+    y[i] = s;
+}
+
 constexpr int kMergeWarps = 4;  // warps per block of the k-way merge
 constexpr int kMergeBuf = 16;   // ranges buffered per source (8 KB per warp)
 
@@ -914,12 +925,15 @@ constexpr int kMergeBuf = 16;   // ranges buffered per source (8 KB per warp)
 // ranges are merged, so every maximal run of end positions lies in one output range.
 __global__ void __launch_bounds__(kMergeWarps * 32)
     lc_kmerge_k(LcParams L, const uint64_t* doff, LcDesc* desc, const uint64_t* off, uint64_t* olo, uint64_t* ohi,
-                uint32_t* ocnt, const uint32_t* ylist, uint32_t ny) {
+                uint32_t* ocnt, const uint64_t* ylist, uint32_t ny, uint32_t* cursor) {
     __shared__ int64_t blo[kMergeWarps][32][kMergeBuf], bhi[kMergeWarps][32][kMergeBuf];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t yi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; yi < ny; yi += nw) {
-        const uint32_t y = ylist[yi];
+    for (;;) {
+        uint32_t yi = 0;
+        if (lane == 0) yi = atomicAdd(cursor, 1u);  // largest segments first, then whoever is free
+        yi = __shfl_sync(kFull, yi, 0);
+        if (yi >= ny) break;
+        const uint32_t y = (uint32_t)ylist[yi];
         const uint32_t r = L.list[y >> 1], s = y & 1;
         const int64_t m = L.len[r], k = L.kk[r];
         const uint64_t d0 = doff[y], d1 = doff[y + 1];
@@ -1827,9 +1841,15 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
             const uint32_t n_rest = to_host(rest.p, s);
             st.lowcx_rest_segments = n_rest;
             if (n_rest) {
+                // largest first, so that the biggest segments do not start last
+                DBuf<uint64_t> sk(n_rest, s), sy(n_rest, s), t1(n_rest, s), t2(n_rest, s);
+                rest_order_k<<<grid_for(n_rest, 256), 256, 0, s>>>(rest_list.p, n_rest, lc_off.p, sk.p, sy.p);
+                PN_CHECK_LAUNCH();
+                radix_sort_pairs(sk.p, sy.p, t1.p, t2.p, n_rest, 40, s);
+                PN_CUDA(cudaMemsetAsync(rest.p + 1, 0, sizeof(uint32_t), s));
                 lc_kmerge_k<<<grid_for((uint64_t)n_rest * 32, kMergeWarps * 32, (unsigned)sm_count() * 32),
                               kMergeWarps * 32, 0, s>>>(L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p,
-                                                        rest_list.p, n_rest);
+                                                        sy.p, n_rest, rest.p + 1);
                 PN_CHECK_LAUNCH();
             }
         }
