@@ -37,16 +37,16 @@ Allocator current_allocator() { return Allocator{g_alloc, g_release, g_ctx}; }
 // raised once per device), so per-batch temporaries are not returned to the driver and re-mapped
 // at every stream synchronization.
 static void retain_pool_memory() {
-    static bool done[256] = {};
+    static std::atomic<bool> done[256];
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256 || done[dev]) return;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256 || done[dev].load()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     cudaGetLastError();
-    done[dev] = true;
+    done[dev].store(true);
 }
 
 void* dalloc(size_t bytes, cudaStream_t s, Allocator* used) {
@@ -80,13 +80,17 @@ void dfree(void* p, cudaStream_t s, const Allocator& a) {
     if (cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();  // never leave a stale error behind
 }
 
-int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+int sm_count() {  // of the current device, looked up once per device (any thread)
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cudaGetLastError();
         if (n <= 0) n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }

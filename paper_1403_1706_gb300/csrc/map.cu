@@ -1758,11 +1758,8 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.big_reads = n_big;
     PN_CUDA(cudaEventRecord(kev[8], s));
     if (n_med) {
-        static bool attr_set = false;  // opt in to the block path's shared memory once per process
-        if (!attr_set) {
-            PN_CUDA(cudaFuncSetAttribute(windows_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmem));
-            attr_set = true;
-        }
+        // opt in to the block path's shared memory (a per-device function attribute; cheap to repeat)
+        PN_CUDA(cudaFuncSetAttribute(windows_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmem));
         // keys as strand << sbit | biased diagonal: 33 bits when the reference allows
         const int sbit = (n + (uint64_t)kDiagBias + 1) < (1ull << 32) ? 32 : 40;
         windows_med_k<<<grid_for(n_med, 1, (unsigned)sm_count()), kMedThreads, kMedSmem, s>>>(
@@ -1827,12 +1824,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
             lc_gather_k<<<grid_for(nseg * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(L, doff.p, desc.p,
                                                                                           lc_off.p, gk.p, wide.p);
             PN_CHECK_LAUNCH();
-            static bool attr_set = false;
-            if (!attr_set) {
-                PN_CUDA(cudaFuncSetAttribute(lc_merge_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kMedSmem));
-                attr_set = true;
-            }
+            PN_CUDA(cudaFuncSetAttribute(lc_merge_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmem));
             int top = 24;  // key bits: lo << 24 with lo < n < 2^(top - 24), so lo never reads all ones
             while (top < 64 && (1ull << (top - 24)) <= n) ++top;
             lc_merge_med_k<<<grid_for(nseg, 1, (unsigned)sm_count()), kMedThreads, kMedSmem, s>>>(
