@@ -251,8 +251,9 @@ peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t
  *     verification; a submission is admitted (its reads copied to the device) when its
  *     footprint fits next to the work in flight ("admission by free HBM");
  *   - with autotune, the first launch of each class is mapped once per candidate setting
- *     (q and q - 1, sampling strides 1..4 that every length of the class admits) and the setting
- *     with the lowest predicted time per read at full launch size is used from then on;
+ *     (its q with sampling strides 1, 2, 3, 4, 6, 8, 12, 16 up to q, and q - 1 with strides 1..4,
+ *     as far as every length of the class admits them) and the setting with the lowest predicted
+ *     time per read at full launch size is used from then on;
  *   - each submission's hits are renumbered to its own read ids and sorted on the device,
  *     reduced to the best stratum if asked, and returned in one host hit list.
  * A read's hits depend only on the read, its budget and the reference, so a submission's

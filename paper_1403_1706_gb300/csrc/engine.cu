@@ -539,8 +539,10 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
         for (uint32_t q = (uint32_t)c; q + 1 >= (uint32_t)c && q >= 1; --q) {
             const double rand_per_qgram = 2.0 * (double)E->ref->n / (double)(1ull << (2 * q));
             if (q != (uint32_t)c && (E->p.fixed_q || rand_per_qgram * 200.0 > 2.0e4)) break;
-            for (uint32_t st = 1; st <= 4; ++st)
-                if (setting_ok(E, mask, q, st)) cand.push_back({q, st});
+            // strides up to q (disjoint q-grams, the pigeonhole case) for the class's own q
+            static const uint32_t kStrides[] = {1, 2, 3, 4, 6, 8, 12, 16};
+            for (uint32_t st : kStrides)
+                if (st <= (q == (uint32_t)c ? q : 4u) && setting_ok(E, mask, q, st)) cand.push_back({q, st});
             if (q == 1) break;
         }
         float best = 1e30f;

@@ -233,7 +233,7 @@ def test_engine_autotune_records(gpu, world, expected):
     assert set(classes) == {12, 15, 16}
     for c in classes.values():
         assert c["tune_candidates"] >= 1 and c["q"] in (c["q_class"], c["q_class"] - 1)
-        assert 1 <= c["stride"] <= 4 and c["launches"] >= 1
+        assert 1 <= c["stride"] <= c["q"] and c["launches"] >= 1
 
 
 @pytest.mark.parametrize("stride", [2, 3, 4])
@@ -251,6 +251,27 @@ def test_sampling_stride_exact(gpu, stride):
         assert np.array_equal(got, want), (stride, mode)
         thr, lc = gpu.export_read_params(B)
         assert thr.min() >= 1
+
+
+@pytest.mark.parametrize("q,stride,lengths", [(16, 16, (100,)), (16, 8, (100, 150)), (12, 12, (50,)),
+                                               (16, 16, (150, 250)), (15, 15, (75,))])
+def test_disjoint_qgram_strides_exact(gpu, q, stride, lengths):
+    """Strides up to q (disjoint q-grams: each edit touches at most one, threshold = sampled - k)
+    on a repeat-rich reference with tandem runs (low-complexity reads included)."""
+    ref = synth.make_reference(2_000_000, 91, 0.05, 0.01)
+    reads = synth.make_reads(ref, 2500, 93, lengths=lengths, rate_range=(0.0, 0.04), random_frac=0.05)
+    R = gpu.pack_reference(ref)
+    ks = [k_of(int(m)) for m in reads.lengths]
+    for mode in ("all", "best"):
+        want = oracle.map_filter(ref, reads.seq, reads.offsets, ks, min(q, 12 if 50 in lengths else q), mode)
+        for cap in (0, 16):
+            B = gpu.index_reads(R, reads.seq, reads.offsets, q, k_permille=50, stride=stride, freq_cap=cap)
+            got = gpu.map(R, B, mode)
+            assert np.array_equal(got, want), (q, stride, lengths, mode, cap)
+            thr, lc = gpu.export_read_params(B)
+            assert thr.min() >= 1
+            if cap:
+                assert lc.sum() > 0  # a small cap makes low-complexity reads
 
 
 def test_sampling_stride_rejects_unfilterable(gpu):
