@@ -270,6 +270,7 @@ struct peanut_engine {
     uint64_t next_ticket = 1, next_order = 0;
     int running = 0;  // admissions and launches in progress
     int tuning_active = 0;  // tuning runs in progress (they run alone)
+    int launching = 0, admitting = 0;  // launches / admissions in progress
     bool stop = false;
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;
@@ -451,6 +452,8 @@ struct LaunchOut {
     std::vector<uint64_t> bounds;  // result row of each segment start, plus the total
     peanut_map_stats st = {};
     std::vector<peanut_map_stats> runs;  // every mapping run of the launch (several when tuning)
+    peanut_map_stats st_model = {};      // the run of the setting used from now on (memory model)
+    uint64_t nqg_model = 0;
     uint64_t n_qgrams = 0, total = 0;
 };
 
@@ -527,6 +530,8 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
         float ms = 0;
         out.launch = map_setting(E, buf.p, noff.p, n, total, q_use, stride_use, s, &out.st, &out.n_qgrams, &ms);
         out.runs.push_back(out.st);
+        out.st_model = out.st;
+        out.nqg_model = out.n_qgrams;
     } else {
         // candidate settings: q and q - 1 (if its random hits stay moderate), strides 1..4 that
         // every length of the class admits; the first (q, 1) is the plain setting and its
@@ -567,6 +572,8 @@ static LaunchOut run_launch(peanut_engine* E, int c, const std::vector<Segment>&
                 best = (float)pred;
                 *best_q = cand[i].first;
                 *best_stride = cand[i].second;
+                out.st_model = st;
+                out.nqg_model = nqg;
             }
             if (i == 0) {
                 out.launch = L;
@@ -670,6 +677,13 @@ static void executor(peanut_engine* E, int idx) {
             E->cv_work.wait(lk);
             continue;
         }
+        // while another launch keeps the GPU busy and submissions are still being admitted, let
+        // the class fill up to half a launch instead of starting a small one
+        if (!tune && E->launching > 0 && C.waiting < E->p.max_reads / 2 &&
+            (!E->pending.empty() || E->admitting > 0)) {
+            E->cv_work.wait(lk);
+            continue;
+        }
         uint64_t n = std::min<uint64_t>(C.waiting, tune ? std::min(kTuneReads, E->p.max_reads) : E->p.max_reads);
         // at most kMaxLaunchHits expected q-gram hits (the sorts of one launch index 32 bits)
         const double hpr = hits_per_read(E, C, C.q);
@@ -705,6 +719,7 @@ static void executor(peanut_engine* E, int idx) {
         E->reserved += need;
         E->reserved_peak = std::max(E->reserved_peak, E->reserved);
         E->running++;
+        E->launching++;
         lk.unlock();
 
         peanut_status st = PEANUT_OK;
@@ -727,6 +742,7 @@ static void executor(peanut_engine* E, int idx) {
         lk.lock();
         E->sum.ms_launch += wall_ms() - t_launch;
         E->running--;
+        E->launching--;
         E->reserved -= need;
         if (tune) {
             C.tuning = false;
@@ -747,9 +763,13 @@ static void executor(peanut_engine* E, int idx) {
             E->n_launches++;
             E->n_reads += taken;
             C.cap = default_freq_cap(E->ref->n, q_use);
-            const double per = launch_measured_bytes(L.st, taken, L.total, L.n_qgrams) / std::max<uint32_t>(taken, 1);
-            C.bytes_per_read = std::max(C.bytes_per_read, 1.25 * per);
-            C.hits_per_read = std::max(C.hits_per_read, 1.25 * (double)L.st.hits / std::max<uint32_t>(taken, 1));
+            // the class's memory model, from the setting it uses: set by the tuning launch, raised by
+            // any later launch that needed more
+            const double nr = (double)std::max<uint32_t>(taken, 1);
+            const double per = launch_measured_bytes(L.st_model, taken, L.total, L.nqg_model) / nr;
+            const double hpr = (double)L.st_model.hits / nr;
+            C.bytes_per_read = tune ? 1.25 * per : std::max(C.bytes_per_read, 1.25 * per);
+            C.hits_per_read = tune ? 1.25 * hpr : std::max(C.hits_per_read, 1.25 * hpr);
             for (const peanut_map_stats& m : L.runs) {
                 E->sum.hits += m.hits;
                 E->sum.candidates += m.candidates;
@@ -884,6 +904,7 @@ static void io_loop(peanut_engine* E) {
                 E->reserved_peak = std::max(E->reserved_peak, E->reserved);
                 S->reserved = need;
                 E->running++;
+                E->admitting++;
                 lk.unlock();
                 peanut_status st = PEANUT_OK;
                 std::string msg;
@@ -900,6 +921,7 @@ static void io_loop(peanut_engine* E) {
                 lk.lock();
                 E->sum.ms_admit += wall_ms() - t0;
                 E->running--;
+                E->admitting--;
                 if (st != PEANUT_OK) {
                     set_failed(S, st, msg.c_str());
                     finish(E, S);
