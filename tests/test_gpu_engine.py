@@ -274,6 +274,24 @@ def test_disjoint_qgram_strides_exact(gpu, q, stride, lengths):
                 assert lc.sum() > 0  # a small cap makes low-complexity reads
 
 
+def test_sampling_thresholds_follow_the_bound(gpu):
+    """On a uniform reference (no frequent q-grams) every read's threshold is the sampled-offset
+    bound ceil(nq/s) - k ceil(q/s) (the q-gram lemma for s = 1)."""
+    ref = synth.uniform_reference(1_000_000, 17)
+    R = gpu.pack_reference(ref)
+    for q, s, lengths in ((15, 1, (75, 100, 150, 250)), (15, 3, (75, 100, 150, 250)), (16, 4, (100, 150, 250)),
+                          (16, 16, (100, 150, 250)), (12, 12, (50,))):
+        reads = synth.make_reads(ref, 3000, 19, lengths=lengths, rate_range=(0.0, 0.04))
+        L = reads.lengths.astype(np.int64)
+        k = (L * 50 + 999) // 1000
+        B = gpu.index_reads(R, reads.seq, reads.offsets, q, k_permille=50, stride=s)
+        thr, lc = gpu.export_read_params(B)
+        nq = L - q + 1
+        want = -(-nq // s) - np.minimum(-(-nq // s), k * -(-q // s))
+        assert lc.sum() == 0
+        assert np.array_equal(thr.astype(np.int64), want), (q, s)
+
+
 def test_sampling_stride_rejects_unfilterable(gpu):
     ref = synth.make_reference(200_000, 5, 0.0, 0.0)
     reads = synth.make_reads(ref, 10, 7, lengths=(100,))
