@@ -677,17 +677,18 @@ static void executor(peanut_engine* E, int idx) {
             E->cv_work.wait(lk);
             continue;
         }
+        // the largest launch of this class: max_reads, and at most kMaxLaunchHits expected q-gram
+        // hits (the sorts of one launch index 32 bits)
+        const double hpr = hits_per_read(E, C, C.q);
+        uint64_t cap = tune ? std::min(kTuneReads, E->p.max_reads) : E->p.max_reads;
+        if ((double)cap * hpr > kMaxLaunchHits) cap = std::max<uint64_t>(1, (uint64_t)(kMaxLaunchHits / hpr));
         // while another launch keeps the GPU busy and submissions are still being admitted, let
         // the class fill up to half a launch instead of starting a small one
-        if (!tune && E->launching > 0 && C.waiting < E->p.max_reads / 2 &&
-            (!E->pending.empty() || E->admitting > 0)) {
+        if (!tune && E->launching > 0 && C.waiting < cap / 2 && (!E->pending.empty() || E->admitting > 0)) {
             E->cv_work.wait(lk);
             continue;
         }
-        uint64_t n = std::min<uint64_t>(C.waiting, tune ? std::min(kTuneReads, E->p.max_reads) : E->p.max_reads);
-        // at most kMaxLaunchHits expected q-gram hits (the sorts of one launch index 32 bits)
-        const double hpr = hits_per_read(E, C, C.q);
-        if ((double)n * hpr > kMaxLaunchHits) n = std::max<uint64_t>(1, (uint64_t)(kMaxLaunchHits / hpr));
+        uint64_t n = std::min<uint64_t>(C.waiting, cap);
         const double avail = (double)E->budget - (double)E->reserved;
         while (n > kMinLaunch && launch_bytes(E, C, C.q, n) > avail) n >>= 1;
         if (launch_bytes(E, C, C.q, n) > avail && E->running > 0) {
@@ -726,7 +727,7 @@ static void executor(peanut_engine* E, int idx) {
         std::string msg;
         LaunchOut L;
         std::vector<std::pair<uint32_t, uint32_t>> tried;
-        uint32_t bq = C.q, bs = C.stride;
+        uint32_t bq = q_use, bs = stride_use;  // (read under the lock above)
         float bpred = 0;
         const double t_launch = wall_ms();
         try {
