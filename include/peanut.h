@@ -174,7 +174,9 @@ uint64_t peanut_kernel_launches(void);
 /* Device memory provider for all later allocations (e.g. a caching allocator of the host
  * framework).  alloc(bytes, stream, ctx) returns device memory or NULL; release(ptr, stream,
  * ctx) frees it.  Passing NULL functions restores the default (cudaMallocAsync /
- * cudaFreeAsync on the stream).  Not thread-safe with concurrent calls. */
+ * cudaFreeAsync on the stream).  Not thread-safe with concurrent calls.  An engine allocates
+ * from its own threads on its own streams: a provider installed while engines exist must be
+ * thread-safe and accept any stream. */
 typedef void* (*peanut_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*peanut_release_fn)(void* ptr, void* stream, void* ctx);
 peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn release, void* ctx);

@@ -196,6 +196,12 @@ def test_engine_release_with_work_in_flight(gpu, world, expected):
     try:
         assert np.array_equal(E.wait(E.submit(subs[4].seq, subs[4].offsets, "best")), expected[4, "best"])
         assert E.wait(E.submit(subs[0].seq, subs[0].offsets, "all"), timeout_ms=60000) is not None
+        # a wait that times out keeps the ticket; the next wait returns the result
+        t = E.submit(subs[5].seq, subs[5].offsets, "all")
+        h = E.wait(t, timeout_ms=0)
+        if h is None:
+            h = E.wait(t)
+        assert np.array_equal(h, expected[5, "all"])
     finally:
         E.free()
 
