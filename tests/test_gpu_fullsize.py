@@ -94,3 +94,52 @@ def test_human_scale_batch_properties(human_batch):
         assert (int(r), s, lo + jstar, int(run.min())) in got, int(r)
         checked += 1
     assert checked > 450
+
+
+def test_reference_beyond_2_32_bases(gpu):
+    """A 4.4 Gbp reference (positions past 2^32: the block paths sort 41-bit keys).  The same reads
+    mapped at q = 14 (~3,000 hits per read: block window path) and at q = 16 (warp path), with
+    the default and a small frequency cap, must give one hit set; planted reads keep the
+    canonical tuple of the run holding their true end (local DP window of the oracle)."""
+    n = 4_400_000_000
+    ref = synth.make_reference(n, 2718, 0.45, 0.01)
+    reads = synth.make_reads(ref, 20000, 2719, lengths=(100,), rate_range=(0.01, 0.04), random_frac=0.05)
+    R = gpu.pack_reference(ref)
+    sets = []
+    for q, cap in ((16, 0), (14, 0), (14, 128)):  # a 14-gram occurs ~33 times by chance here
+        B = gpu.index_reads(R, reads.seq, reads.offsets, q, k=5, freq_cap=cap)
+        sets.append(gpu.map(R, B, "all"))
+        st = gpu.get_map_stats(B)
+        if q == 14:
+            assert st["med_reads"] > reads.n // 2
+        B.free()
+    assert np.array_equal(sets[0], sets[1]) and np.array_equal(sets[0], sets[2])
+    h = sets[0]
+    assert h["end"].max() >= 1 << 32 or (reads.truth_end >= 1 << 32).sum() == 0
+    got = set(zip(h["read"].tolist(), h["strand"].tolist(), h["end"].tolist(), h["dist"].tolist()))
+    k = 5
+    rng = np.random.default_rng(3)
+    planted = np.flatnonzero((reads.truth_edits >= 0) & (reads.truth_edits <= k) & (reads.truth_end >= 1 << 32))
+    checked = 0
+    for r in rng.choice(planted, min(100, planted.size), replace=False):
+        s = int(reads.truth_strand[r])
+        read = reads.read(int(r))
+        pat = read if s == 0 else synth.revcomp_ascii(read).tobytes()
+        m = len(pat)
+        e = int(reads.truth_end[r])
+        lo, hi = max(0, e - 600), min(ref.size, e + 600)
+        D = oracle.semiglobal_column(pat, ref[lo:hi])
+        j = e - lo
+        assert D[j] <= k
+        a = j
+        while a - 1 >= 0 and D[a - 1] <= k:
+            a -= 1
+        b = j
+        while b + 1 < D.size and D[b + 1] <= k:
+            b += 1
+        if a - 1 < m + k - 1 or b + 1 >= D.size:
+            continue
+        run = D[a:b + 1]
+        assert (int(r), s, lo + a + int(np.argmin(run)), int(run.min())) in got, int(r)
+        checked += 1
+    assert checked > 80
