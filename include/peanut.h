@@ -97,11 +97,12 @@ typedef struct {
     uint64_t results;          /* hits returned */
     uint64_t lowcx_reads;      /* reads verified around frequent q-gram clusters */
     uint64_t lowcx_ranges;     /* cluster and counting ranges of those reads, before merging */
-    uint64_t scan_retries;     /* hit-buffer regrowths */
+    uint64_t scan_retries;     /* present-position or hit buffer regrowths */
     uint64_t present_probes;   /* reference positions whose canonical q-gram is indexed */
     uint64_t candidate_word_columns; /* columns x 64-bit words of the verification */
     float ms_scan, ms_bin, ms_windows, ms_verify, ms_output; /* device time per stage */
-    float ms_scan_kernel;      /* the reference-scan kernel alone (CUDA events on its stream) */
+    float ms_scan_kernel;      /* the reference-scan kernels alone (probe and expand; CUDA events on
+                                  their stream) */
     float ms_verify_kernel;    /* the verification count pass alone (CUDA events on its stream) */
     float ms_windows_sweep, ms_lowcx, ms_compact; /* parts of ms_windows */
     float ms_probe_kernel;     /* the probe half of the reference scan (present positions) */
@@ -162,7 +163,8 @@ peanut_status peanut_download_hits(const peanut_device_hits* dh, void* stream, p
 peanut_status peanut_get_map_stats(const peanut_reads* reads, peanut_map_stats* out);
 
 /* Frees any object returned by this library (peanut_ref, peanut_reads, peanut_hits,
- * peanut_device_hits).  NULL is a no-op.  Device memory is released on the object's stream. */
+ * peanut_device_hits, peanut_engine).  NULL is a no-op.  Device memory is released on the
+ * object's stream. */
 void peanut_free(void* obj);
 
 /* Message describing the last failure on this thread ("" if none). */
