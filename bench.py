@@ -62,6 +62,7 @@ def parse_args():
                          "50-250 bp reads through the engine vs the plain path; serve: a Poisson request "
                          "stream through the engine vs one request at a time")
     ap.add_argument("--requests", type=int, default=None, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=None, help="serve: mean arrivals per second")
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
     ap.add_argument("--no-check", action="store_true", help="batched: skip the identical-output check")
     return ap.parse_args()
@@ -427,7 +428,8 @@ def run_serve(args, rank, world, local):
     n_req = args.requests or w["n_requests"]
     t0 = time.time()
     ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
-    arrivals, sizes, modes = synth.request_stream(91 + rank, n_req, w["rate_per_s"], w["req_min"], w["req_max"])
+    rate = args.rate or w["rate_per_s"]
+    arrivals, sizes, modes = synth.request_stream(91 + rank, n_req, rate, w["req_min"], w["req_max"])
     if args.reads:  # scale the request sizes down
         sizes = np.maximum(1, (sizes * (args.reads / max(1, int(sizes.sum()))))).astype(np.int64)
     reqs = []
@@ -512,7 +514,7 @@ def run_serve(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "mode": "serve",
             "config": {"workload": "serve_3g1", "reference_bp": int(n_ref), "requests": n_req,
-                       "rate_per_s": w["rate_per_s"], "request_reads": [int(sizes.min()), int(sizes.max())],
+                       "rate_per_s": rate, "request_reads": [int(sizes.min()), int(sizes.max())],
                        "reads": total_reads, "read_len": [75, 250], "k": "ceil(0.05 L)",
                        "modes": {m: int((modes == m).sum()) for m in ("all", "best")},
                        "executors": args.executors, "offered_reads_per_s": total_reads / float(arrivals[-1])},
