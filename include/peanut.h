@@ -272,7 +272,8 @@ typedef struct {
     uint32_t autotune;    /* 1 = pick (q, stride) per class by timing its first launch */
     uint32_t fixed_q;     /* 0 = per class; else every read is mapped with this q (1..16) */
     uint64_t hbm_budget;  /* device bytes the engine may hold (0 = 90 % of the free memory at
-                             creation, less 4 GiB) */
+                             creation, less 4 GiB; give explicit budgets when several engines
+                             share a device) */
 } peanut_engine_params;
 
 /* Per-class record of an engine (peanut_engine_get_stats). */
