@@ -1502,9 +1502,9 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
     return (uint64_t)(hi - a + 1);
 }
 
-// Work order of the verification: candidates grouped by words per column and by length (16-column
-// steps up to 4096), so that the 32 ranges of a warp take about the same number of steps.
-constexpr int kOrderBits = 10;
+// Work order of the verification: candidates grouped by words per column and by length (8-column
+// steps up to 4088), so that the 32 ranges of a warp take about the same number of steps.
+constexpr int kOrderBits = 11;
 __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_t* __restrict__ cand_hi, uint64_t n,
                             const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk, uint64_t* keys,
                             uint64_t* vals) {
@@ -1515,9 +1515,9 @@ __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_
         const uint32_t m = len[r];
         int64_t a = lo - ((int64_t)m + kk[r]) + 1;
         if (a < 0) a = 0;
-        const uint64_t cols = (uint64_t)(hi - a + 1) >> 4;
+        const uint64_t cols = (uint64_t)(hi - a + 1) >> 3;
         const uint64_t w = (m + 63) >> 6;
-        keys[x] = ((w - 1) << 8) | (cols < 255 ? cols : 255);
+        keys[x] = ((w - 1) << 9) | (cols < 511 ? cols : 511);
         vals[x] = x;
     }
 }
