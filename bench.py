@@ -40,7 +40,21 @@ sys.path.insert(0, ROOT)
 METRIC = "reads/sec mapped (all-hits, k=5%) on 1 GB300 vs oracle; p50/p99 request latency"
 UNIT = "reads/s"
 HIT_BYTES = 4 + 1 + 8 + 1  # read_id, strand, end_pos, dist of one result
-N_SM, INT32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0  # GB300
+# Myers' column step on one 64-bit word, counted as the fewest 32-bit ALU instructions it needs:
+# Xv = Eq | Mv (2), Eq & Pv (2), the carried add (2), Xh (2, one 3-input logic op per half),
+# Ph (2), Mh (2), the two carried one-bit shifts (4 funnel shifts), Pv (2), Mv (2)
+ALG_OPS_PER_WORD_COLUMN = 20
+
+
+def int_peaks(peanut, stream=None):
+    """The in-repo integer issue-rate microbenchmark (peanut_int_peak), every kind once."""
+    out = {}
+    for kind, iters in (("lop3", 20000), ("shf", 20000), ("iadd", 20000), ("imad", 20000), ("popc", 20000),
+                        ("myers_w1", 6000), ("myers_w2", 3000)):
+        r = peanut.int_peak(kind, iters, stream)
+        out[kind] = {"ops_per_s": r["ops_per_s"], "ms": r["ms"], "ops": r["ops"],
+                     "unit": "word-columns/s" if kind.startswith("myers") else "instructions/s"}
+    return out
 
 
 def parse_args():
@@ -65,6 +79,8 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=None, help="serve: mean arrivals per second")
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
     ap.add_argument("--no-check", action="store_true", help="batched: skip the identical-output check")
+    ap.add_argument("--no-serve", action="store_true", help="plain: skip the short serving leg")
+    ap.add_argument("--serve-requests", type=int, default=30, help="plain: requests of the serving leg")
     return ap.parse_args()
 
 
@@ -183,11 +199,17 @@ def make_inputs(args, rank):
     return ref, reads, w, time.time() - t0
 
 
-def cpu_baseline(ref, reads, w, slice_len, batch):
+def cpu_baseline(ref, reads, w, slice_len, batch, threads=None):
     """The oracle on a bounded sample: the reads whose planted origin lies in the first
-    `slice_len` bases (plus the unmappable ones at their natural rate), as many as one read
-    batch holds per base of reference, mapped against that prefix; single thread."""
+    `slice_len` bases (plus the unmappable ones at their natural rate), as many as one read batch
+    holds per base of reference, mapped against that prefix.  The sample's reads are split over
+    `threads` host threads (default: every core), each an independent oracle call that scans the
+    whole prefix (ctypes releases the GIL); value = sample reads / wall time.  The per-read rate
+    stands for the full workload because the sample is as dense on the prefix as a batch is on
+    the whole reference: it is an extrapolation from the sample, labelled as such."""
     import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    threads = threads or os.cpu_count() or 1
     n = ref.size
     slice_len = min(slice_len, n)
     want = max(1, int(round(batch * slice_len / n)))
@@ -196,12 +218,19 @@ def cpu_baseline(ref, reads, w, slice_len, batch):
     idx = np.flatnonzero(inside | (rnd & (np.arange(reads.n) % max(1, n // slice_len) == 0)))[:want]
     sub = reads.subset(idx)
     q, k = w["q"], w["k"]
+    prefix = ref[:slice_len]
+    shards = [sub.subset(np.arange(t, sub.n, threads)) for t in range(threads)]  # interleaved: balanced
     t0 = time.perf_counter()
-    h = oracle.map_filter(ref[:slice_len], sub.seq, sub.offsets, k, q, "all")
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda sh: oracle.map_filter(prefix, sh.seq, sh.offsets, k, q, "all"), shards))
     dt = time.perf_counter() - t0
-    return {"value": sub.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sub.n} reads (origin in the first {slice_len} bp, one batch's density) vs the "
-                      f"first {slice_len} bp of the {n} bp reference; {len(h)} hits; {dt:.1f} s single-thread"}
+    nh = sum(len(h) for h in parts)
+    return {"value": sub.n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "extrapolated": True,
+            "sample": f"{sub.n} reads (origin in the first {slice_len} bp, one {batch}-read batch's density on "
+                      f"the {n} bp reference) mapped against that prefix, split over {threads} threads; "
+                      f"{nh} hits; {dt:.1f} s wall; reads/s extrapolated per read to the full workload (optimistic: "
+                      f"the oracle's cost per low-complexity read grows with the reference length)"}
 
 
 def run_reference(args, rank, world):
@@ -212,7 +241,7 @@ def run_reference(args, rank, world):
     res = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        res = cpu_baseline(ref, reads, w, args.cpu_slice // 2, args.batch)
+        res = cpu_baseline(ref, reads, w, args.cpu_slice, args.batch)
         if i >= args.warmup:
             steps.append(res["value"])
             secs.append(time.perf_counter() - t0)
@@ -222,7 +251,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "sample": res["sample"]},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": res["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                             "extrapolated": True, "sample": res["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -412,29 +442,21 @@ def run_batched(args, rank, world, local):
     return 0
 
 
-def run_serve(args, rank, world, local):
-    """A Poisson request stream (50 requests/s, sizes log-uniform in 10^3..10^6 reads, lengths
-    75-250 bp, 1-4 % errors, k = ceil(0.05 L), half in best-stratum mode) on the resident 3.1 Gbp
-    reference.  Engine: requests submitted from host memory at their arrival times, results
-    waited for on their own threads.  Baseline: one request at a time through the plain path
-    (peanut_index_reads + peanut_map per q class of the request), queued in arrival order."""
+def serve_stream(peanut, R, ref, n_req, rate, seed, executors, warmup, clock_gpu=None, log=None):
+    """A Poisson request stream (sizes log-uniform in 10^3..10^6 reads, lengths 75-250 bp, 1-4 %
+    errors, k = ceil(0.05 L), half the requests in best-stratum mode) on a resident reference.
+    Engine: requests submitted from pinned host memory at their arrival times, each result
+    waited for on its own thread; latency = result in hand - arrival.  Baseline: one request at a
+    time through the plain path (peanut_index_reads + peanut_map per q class of the request), a
+    FIFO queue over the measured service times.  Returns the measurements as a dict."""
     import torch
     import synth
-    from paper_1403_1706_gb300 import peanut
-    torch.cuda.set_device(local)
-    peanut.load()
     w = synth.WORKLOADS["serve_3g1"]
-    n_ref = args.ref_len or w["ref_len"]
-    n_req = args.requests or w["n_requests"]
     t0 = time.time()
-    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
-    rate = args.rate or w["rate_per_s"]
-    arrivals, sizes, modes = synth.request_stream(91 + rank, n_req, rate, w["req_min"], w["req_max"])
-    if args.reads:  # scale the request sizes down
-        sizes = np.maximum(1, (sizes * (args.reads / max(1, int(sizes.sum()))))).astype(np.int64)
+    arrivals, sizes, modes = synth.request_stream(seed, n_req, rate, w["req_min"], w["req_max"])
     reqs = []
     for i in range(n_req):
-        rd = synth.make_reads(ref, int(sizes[i]), 9000 + i + 100000 * rank, lengths=w["lengths"],
+        rd = synth.make_reads(ref, int(sizes[i]), 9000 + i + 100 * seed, lengths=w["lengths"],
                               rate_range=w["rate_range"], random_frac=w["random_frac"])
         h_seq = torch.empty(rd.seq.size, dtype=torch.uint8, pin_memory=True)
         h_seq.numpy()[:] = rd.seq
@@ -448,19 +470,17 @@ def run_serve(args, rank, world, local):
             groups.append((int(q), idx.astype(np.int64), sub.seq, sub.offsets))
         reqs.append((h_seq, rd.offsets, groups, rd.n))
     t_gen = time.time() - t0
-    R = peanut.pack_reference(ref)
-    E = peanut.Engine(R, k_permille=50, executors=args.executors, autotune=True)
-    # warm-up: one request of every class through both paths (tunes the engine, builds the
+    E = peanut.Engine(R, k_permille=50, executors=executors, autotune=True)
+    # warm-up: the largest request through both paths (tunes the engine's classes, builds the
     # reference's per-q tables)
     warm = int(np.argmax(sizes))
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         E.wait(E.submit(reqs[warm][0].numpy(), reqs[warm][1], "all"))
     for q, idx, sq, of in reqs[warm][2]:
         B = peanut.index_reads(R, sq, of, q, k_permille=50)
         peanut.map(R, B, "all")
         B.free()
 
-    # engine: real-time arrivals
     done = [0.0] * n_req
     nres = [0] * n_req
     waiters = []
@@ -472,26 +492,29 @@ def run_serve(args, rank, world, local):
         h.free()
 
     l0 = peanut.kernel_launches()
-    with ClockSampler(local) as clk:
-        start = time.perf_counter()
-        for i in range(n_req):
-            delay = start + float(arrivals[i]) - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            t = E.submit(reqs[i][0].numpy(), reqs[i][1], str(modes[i]))
-            th = threading.Thread(target=waiter, args=(i, t))
-            th.start()
-            waiters.append(th)
-        for th in waiters:
-            th.join()
-    clocks = clk.summary()
+    clk = ClockSampler(clock_gpu) if clock_gpu is not None else None
+    if clk:
+        clk.__enter__()
+    start = time.perf_counter()
+    for i in range(n_req):
+        delay = start + float(arrivals[i]) - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        t = E.submit(reqs[i][0].numpy(), reqs[i][1], str(modes[i]))
+        th = threading.Thread(target=waiter, args=(i, t))
+        th.start()
+        waiters.append(th)
+    for th in waiters:
+        th.join()
+    if clk:
+        clk.__exit__()
     launches = peanut.kernel_launches() - l0
     lat = np.array([done[i] - (start + float(arrivals[i])) for i in range(n_req)])
     span = max(done) - (start + float(arrivals[0]))
     total_reads = int(sum(r[3] for r in reqs))
     st = E.stats()
+    E.free()
 
-    # baseline: the plain path, one request at a time, FIFO in arrival order
     service = []
     for i in range(n_req):
         t = time.perf_counter()
@@ -507,31 +530,56 @@ def run_serve(args, rank, world, local):
         plain_lat.append(fin - float(arrivals[i]))
     plain_lat = np.array(plain_lat)
     plain_span = fin - float(arrivals[0])
-    E.free()
+    pct = lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)),
+                     "max": float(a.max())}
+    return {
+        "value": total_reads / span, "unit": UNIT, "span_s": span, "requests": n_req, "rate_per_s": rate,
+        "request_reads": [int(sizes.min()), int(sizes.max())], "reads": total_reads,
+        "offered_reads_per_s": total_reads / max(float(arrivals[-1]), 1e-9),
+        "modes": {m: int((modes == m).sum()) for m in ("all", "best")},
+        "latency_s": pct(lat),
+        "one_at_a_time": {"value": total_reads / plain_span, "latency_s": pct(plain_lat),
+                          "service_s_total": float(sum(service)),
+                          "note": "plain path per q class of each request, FIFO queue from measured "
+                                  "service times"},
+        "h2d_bytes": int(sum(r[0].numel() + 8 * (r[3] + 1) for r in reqs)),
+        "d2h_bytes": int(sum(nres)) * HIT_BYTES, "results": int(sum(nres)), "gpu_launches": int(launches),
+        "clocks": clk.summary() if clk else None, "engine": st, "generate_s": t_gen,
+    }
+
+
+def run_serve(args, rank, world, local):
+    """The serving configuration (serve_3g1): a Poisson request stream of 100 requests at 50/s on
+    the resident 3.1 Gbp reference, through the engine and one request at a time (serve_stream)."""
+    import torch
+    import synth
+    from paper_1403_1706_gb300 import peanut
+    torch.cuda.set_device(local)
+    peanut.load()
+    w = synth.WORKLOADS["serve_3g1"]
+    n_ref = args.ref_len or w["ref_len"]
+    n_req = args.requests or w["n_requests"]
+    t0 = time.time()
+    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
+    t_ref = time.time() - t0
+    rate = args.rate or w["rate_per_s"]
+    R = peanut.pack_reference(ref)
+    sv = serve_stream(peanut, R, ref, n_req, rate, 91 + rank, args.executors, args.warmup, clock_gpu=local)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": total_reads / span, "unit": UNIT, "n_gpus": world, "steps": 1,
-            "warmup": args.warmup, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": sv["value"], "unit": UNIT, "n_gpus": world, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sv["span_s"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "mode": "serve",
             "config": {"workload": "serve_3g1", "reference_bp": int(n_ref), "requests": n_req,
-                       "rate_per_s": rate, "request_reads": [int(sizes.min()), int(sizes.max())],
-                       "reads": total_reads, "read_len": [75, 250], "k": "ceil(0.05 L)",
-                       "modes": {m: int((modes == m).sum()) for m in ("all", "best")},
-                       "executors": args.executors, "offered_reads_per_s": total_reads / float(arrivals[-1])},
-            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "max": float(lat.max())},
-            "one_at_a_time": {"value": total_reads / plain_span,
-                              "latency_s": {"p50": float(np.percentile(plain_lat, 50)),
-                                            "p99": float(np.percentile(plain_lat, 99)),
-                                            "max": float(plain_lat.max())},
-                              "service_s_total": float(sum(service)),
-                              "note": "plain path per q class of each request, FIFO queue from measured "
-                                      "service times"},
-            "e2e": {"value": total_reads / span, "unit": UNIT,
-                    "h2d_bytes_per_step": int(sum(r[0].numel() + 8 * (r[3] + 1) for r in reqs)),
-                    "d2h_bytes_per_step": int(sum(nres)) * HIT_BYTES},
-            "gpu_launches": int(launches), "clocks": clocks, "results": int(sum(nres)), "engine": st,
-            "setup_s": {"generate": t_gen},
+                       "rate_per_s": rate, "request_reads": sv["request_reads"],
+                       "reads": sv["reads"], "read_len": [75, 250], "k": "ceil(0.05 L)",
+                       "modes": sv["modes"], "executors": args.executors,
+                       "offered_reads_per_s": sv["offered_reads_per_s"]},
+            "latency_s": sv["latency_s"], "one_at_a_time": sv["one_at_a_time"],
+            "e2e": {"value": sv["value"], "unit": UNIT, "h2d_bytes_per_step": sv["h2d_bytes"],
+                    "d2h_bytes_per_step": sv["d2h_bytes"]},
+            "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"], "results": sv["results"],
+            "engine": sv["engine"], "setup_s": {"generate": t_ref + sv["generate_s"]},
         }
         print(json.dumps(line), flush=True)
     return 0
@@ -565,6 +613,7 @@ def main():
     ref, reads, w, t_gen = make_inputs(args, rank)
     q, k = w["q"], w["k"]
     stream = torch.cuda.current_stream()
+    ipk = int_peaks(peanut, stream)
     t0 = time.time()
     R = peanut.pack_reference(ref, stream=stream)
     t_pack = time.time() - t0
@@ -584,10 +633,10 @@ def main():
                             d_seq=d_seq[o0:o1], h_seq=h_seq.numpy()[o0:o1]))
     kw = dict(k=k) if isinstance(k, int) else dict(k_permille=50)
 
-    def step_device(stats=None):
+    def step_device(stats=None, qs=(q, 1)):
         n_res = 0
         for bt in batches:
-            RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], q, stream=stream, **kw)
+            RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], qs[0], stream=stream, stride=qs[1], **kw)
             H = peanut.map_device(R, RB)
             n_res += H.n
             if stats is not None:
@@ -679,6 +728,7 @@ def main():
             clk.__exit__()
         e1 = E.stats()
         delta = {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
+                                               "candidate_columns", "useful_columns",
                                                "bases_scanned", "ms_verify_kernel", "ms_scan_kernel",
                                                "ms_admit", "ms_launch", "ms_assemble", "ms_download")}
         ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
@@ -706,22 +756,47 @@ def main():
     est = E.stats()
     E.free()
 
+    # the plain path at the engine's tuned setting: isolates what batching and overlap add
+    tuned = next((c for c in est["classes"] if c["q_class"] == q), None)
+    plain_tuned = None
+    if tuned is not None:
+        qs_t = (tuned["q"], tuned["stride"])
+        step_device(qs=qs_t)  # warm-up at this setting
+        ms_t, _, launches_t, _, _ = timed(lambda: step_device(qs=qs_t))
+        plain_tuned = {"value": units / (ms_t / 1e3), "ms_per_step": ms_t, "q": qs_t[0], "stride": qs_t[1],
+                       "gpu_launches": int(launches_t)}
+
+    # a short serving leg: the serving configuration's request stream (sizes log-uniform in
+    # 10^3..10^6 reads, 50 requests/s), fewer requests, on the same resident reference
+    serving = None
+    if not args.no_serve:
+        sv = serve_stream(peanut, R, ref, args.serve_requests, 50.0, 91 + rank, args.executors, 1)
+        serving = {k2: sv[k2] for k2 in ("value", "unit", "requests", "rate_per_s", "request_reads", "reads",
+                                          "offered_reads_per_s", "modes", "latency_s", "one_at_a_time",
+                                          "span_s")}
+
     # rooflines: the verification count pass (largest launch-list share; integer-ALU bound) and the
     # reference scan (the memory-bound kernels), from the runs' CUDA-event kernel times
     peak, peak_kind = load_peaks()
     n_ref = ref.size
-    int_peak_tops = INT32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+    int_peak_tops = ipk["lop3"]["ops_per_s"] / 1e12
+    step_peak = ipk["myers_w2"]["ops_per_s"]
     per_wc = traffic_per_unit("verify_k", source_sha())
 
     def rooflines(runs, wc, ms_v, probes, hits, bases, ms_s, note):
-        v_ops = 34.0 * wc / runs
+        v_ops = ALG_OPS_PER_WORD_COLUMN * wc / runs
         v_ms = ms_v / runs
         v_ach = v_ops / (v_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": v_ach, "peak": int_peak_tops, "unit": "TOP/s",
                 "frac": v_ach / int_peak_tops,
                 "traffic": per_wc * wc / runs if per_wc is not None else None, "kernel": "verify_k (count pass)",
-                "algorithmic_int32_ops_per_launch": v_ops, "avg_launch_ms": v_ms, "launches": runs,
-                "peak_source": "derived: 152 SMs x 128 INT32 lanes x 2070 MHz", "timing": note}
+                "algorithmic_int32_ops_per_launch": v_ops, "ops_per_word_column": ALG_OPS_PER_WORD_COLUMN,
+                "avg_launch_ms": v_ms, "launches": runs,
+                "peak_source": "measured: in-repo microbenchmark, 3-input logic (lop3.b32) issue rate "
+                               "(peanut_int_peak kind 0), same process, before the timed region",
+                "word_columns_per_s": wc / runs / (v_ms / 1e3),
+                "step_frac": wc / runs / (v_ms / 1e3) / step_peak,
+                "step_peak_word_columns_per_s": step_peak, "timing": note}
         algo = (bases * (0.25 + 8.0) + probes * 8.0 + hits * (4.0 + 1.0 + 8.0)) / runs
         s_ms = ms_s / runs
         ach = algo / (s_ms / 1e3) / 1e9
@@ -746,8 +821,8 @@ def main():
                                      "ms_windows_sweep", "ms_lowcx", "ms_compact", "ms_verify",
                                      "ms_verify_kernel", "ms_output")},
              "per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
-                           ("hits", "present_probes", "candidates", "candidate_columns", "lowcx_reads",
-                            "lowcx_ranges", "results")}}
+                           ("hits", "present_probes", "candidates", "candidate_columns", "useful_columns",
+                            "lowcx_reads", "lowcx_ranges", "lowcx_rest_segments", "results")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -767,7 +842,15 @@ def main():
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
             "roofline_scan": roof_scan, "cpu_baseline": cpu,
             "path": "engine (peanut_engine_submit_device / peanut_engine_wait)",
-            "plain": plain, "vs_plain": ms_p / ms, "identical_output": identical,
+            "plain": plain, "plain_tuned": plain_tuned, "vs_plain": ms_p / ms,
+            "vs_plain_tuned": plain_tuned["ms_per_step"] / ms if plain_tuned else None,
+            "identical_output": identical, "serving": serving,
+            "int_peak": {kk: {"per_s": v["ops_per_s"], "unit": v["unit"],
+                              "per_sm_per_clock": (v["ops_per_s"] / (152 * clocks["sm_mhz"] * 1e6)
+                                                   if clocks and clocks.get("sm_mhz") else None)}
+                         for kk, v in ipk.items()},
+            "verify_useful_column_fraction": (edelta["useful_columns"] / edelta["candidate_columns"]
+                                              if edelta["candidate_columns"] else None),
             "engine": {"classes": est["classes"], "launches": est["launches"],
                        "hbm_reserved_peak": est["hbm_reserved_peak"],
                        "engine_ms_per_step": {f[3:]: edelta[f] / args.steps

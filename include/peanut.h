@@ -110,6 +110,16 @@ typedef struct {
     uint64_t med_reads, big_reads;        /* reads taking those paths */
     uint64_t lowcx_rest_segments; /* (read, strand) segments of low-complexity reads too large for
                                      the block merge (merged by the warp k-way merge) */
+    uint64_t lowcx_serial_segments; /* of those, segments with 32 or more cluster lists (merged by
+                                       one lane) */
+    uint64_t useful_columns;   /* verified columns whose distance is within the read's k (the
+                                  columns that lie in reported runs) */
+    uint64_t prefilter_columns;/* columns the verification would have run without the q'-gram
+                                  filter on candidate ranges */
+    uint64_t filter_positions; /* reference positions scanned by that filter */
+    uint64_t filter_live;      /* candidate ranges it kept (narrowed); the rest hold no end
+                                  within k edits */
+    float ms_filter_kernel;    /* the filter kernel (CUDA events on its stream) */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
@@ -203,8 +213,9 @@ peanut_status peanut_export_index(const peanut_reads* reads, uint32_t* I, uint32
  * lowcx[i] = 1 if read i is verified around frequent-q-gram clusters (host arrays of n_reads). */
 peanut_status peanut_export_read_params(const peanut_reads* reads, uint16_t* thr, uint8_t* lowcx);
 
-/* Candidate end ranges of the last map call (host arrays of *n entries, or NULL to query n):
- * read, strand, lo, hi (inclusive, clipped to the reference). */
+/* Candidate end ranges the last map call verified (host arrays of *n entries, or NULL to query
+ * n): read, strand, lo, hi (inclusive, clipped to the reference), in (read, strand, lo) order:
+ * the compacted windows after the q'-gram filter narrowed them (ranges it removed are left out). */
 peanut_status peanut_export_candidates(const peanut_reads* reads, uint64_t* n, uint32_t* read,
                                        uint8_t* strand, uint64_t* lo, uint64_t* hi);
 
@@ -238,6 +249,48 @@ peanut_status peanut_debug_bitvector_columns(const char* pat, const uint64_t* pa
 peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat,
                                                const char* d_txt, const uint64_t* d_txt_off, int32_t* d_out,
                                                void* stream);
+
+/* ---- postprocessing ------------------------------------------------------------------------
+ *
+ * Annotates a batch's hit list (from peanut_map_device on that batch, either mode, or any list of
+ * its hits grouped by ascending read) on the device:
+ *   start: the alignment start, from the edit distance recomputed backwards from the hit's end
+ *          (Section "Validation", last paragraph): the leftmost reference position i such that
+ *          the edit distance between the pattern (the read, or its reverse complement for
+ *          strand 1) and reference[i .. end] equals the hit's distance;
+ *   rank:  the hit-rank of Section "Postprocessing": the number of the read's hits in the list
+ *          (both strands) whose distance is at most this hit's (percent identity at least as
+ *          high);
+ *   mapq:  the mapping quality of Section "Postprocessing", min(-10 log10((rank - 1) / n), 255)
+ *          for a reference of n bases; 255 for rank 1; the integer part of the double-precision
+ *          value plus 1e-9, clamped to 0..255.
+ *   hits: device hit list (peanut_device_hits); d_start / d_rank / d_mapq: caller-owned device
+ *   arrays of hits->n entries.  Work runs on the batch's stream; the call synchronizes it.
+ * Errors: INVALID_ARG (bad objects, the batch indexed against another reference, a hit naming a
+ *         read / strand / end outside the batch or reference, a distance that is not the
+ *         pattern's distance at that end, hits not grouped by ascending read), NO_MEMORY,
+ *         CUDA_ERROR. */
+peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* reads, const peanut_device_hits* hits,
+                                   uint64_t* d_start, uint32_t* d_rank, uint8_t* d_mapq);
+
+/* ---- measurement ---------------------------------------------------------------------------
+ *
+ * Integer issue-rate microbenchmark: the measured ceiling against which the bit-vector
+ * verification kernel (Section "Validation") is reported.  Runs one kernel of the given kind on
+ * 8 x 256-thread blocks per SM of the current device, every thread twelve independent chains of
+ * one instruction form (no two foldable, operands in registers, no memory traffic), after one
+ * shorter warm-up launch, and times it with CUDA events on `stream` (synchronized).
+ *   kind: 0 = 3-input logic (lop3.b32), 1 = funnel shift (shf.l.wrap.b32), 2 = 32-bit add
+ *         (add.u32), 3 = integer multiply-add (mad.lo.u32), 4 = population count (popc.b32);
+ *         5 / 6 = Myers' column step on 1 / 2 64-bit words with the match masks in shared memory,
+ *         one column stream per thread (the verification kernel's recurrence without its
+ *         global-memory accesses, run bookkeeping or lane divergence).
+ *   iters: loop trips per thread (48 instructions, or 16 columns, per trip).
+ *   ms: kernel time; ops: instructions executed (kinds 0-4) or 64-bit word-columns (5, 6), over
+ *   all threads; grid / block: the launch shape.
+ * Errors: INVALID_ARG (NULL pointer, iters = 0, unknown kind), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_int_peak(uint32_t kind, uint32_t iters, void* stream, double* ms, uint64_t* ops,
+                              uint32_t* grid, uint32_t* block);
 
 /* ---- batched and served mapping ------------------------------------------------------------
  *
@@ -302,6 +355,8 @@ typedef struct {
     double ms_admit, ms_launch, ms_assemble, ms_download;
     uint64_t pageable_result_blocks; /* host result blocks (process-wide) that could not be
                                         page-locked and fell back to pageable memory */
+    uint64_t candidate_columns;       /* columns run through the bit-vector verification */
+    uint64_t useful_columns;          /* of those, columns whose distance is within k */
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with

@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
         os.close(fd)
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -46,13 +46,12 @@ def _load():
         c = ctypes
         vp = c.c_void_p
         lib.oracle_semiglobal_column.restype = c.c_int
-        lib.oracle_semiglobal_column.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, c.c_int64, vp]
+        lib.oracle_semiglobal_column.argtypes = [vp, c.c_int64, vp, c.c_int64, vp]
         for f in (lib.oracle_map_bruteforce,):
             f.restype = vp
-            f.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, vp, c.c_int64, vp, c.c_int]
+            f.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int]
         lib.oracle_map_filter.restype = vp
-        lib.oracle_map_filter.argtypes = [c.c_char_p, c.c_int64, c.c_char_p, vp, c.c_int64, vp,
-                                          c.c_int, c.c_int]
+        lib.oracle_map_filter.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int, c.c_int]
         lib.oracle_hits_count.restype = c.c_int64
         lib.oracle_hits_count.argtypes = [vp]
         lib.oracle_hits_copy.argtypes = [vp, vp, vp, vp, vp]
@@ -61,18 +60,28 @@ def _load():
         lib.oracle_qgroup_build.argtypes = [vp, vp, c.c_int64, c.c_int, c.c_int, vp, vp, vp, vp]
         lib.oracle_indexpair.argtypes = [vp, vp, vp, c.c_int, c.c_uint64, vp, vp]
         lib.oracle_canonical_text.restype = c.c_int64
-        lib.oracle_canonical_text.argtypes = [c.c_char_p, vp, c.c_int64, c.c_int, vp, vp]
+        lib.oracle_canonical_text.argtypes = [vp, vp, c.c_int64, c.c_int, vp, vp]
         lib.oracle_frequent_qgrams.restype = c.c_int64
-        lib.oracle_frequent_qgrams.argtypes = [c.c_char_p, c.c_int64, c.c_int, c.c_int64, vp, vp,
-                                               c.c_int64]
+        lib.oracle_frequent_qgrams.argtypes = [vp, c.c_int64, c.c_int, c.c_int64, vp, vp, c.c_int64]
+        lib.oracle_annotate.restype = c.c_int
+        lib.oracle_annotate.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, vp, vp, vp, c.c_int64, vp, vp, vp]
         _lib = lib
     return _lib
 
 
-def _bytes(x) -> bytes:
+def _bytes(x) -> np.ndarray:
+    """The sequence as a contiguous uint8 array (a view of numpy input; no 3 GB copies)."""
     if isinstance(x, (bytes, bytearray)):
-        return bytes(x)
-    return np.ascontiguousarray(x, dtype=np.uint8).tobytes()
+        return np.frombuffer(bytes(x), dtype=np.uint8)
+    return np.ascontiguousarray(x, dtype=np.uint8)
+
+
+_EMPTY = np.zeros(8, np.uint8)
+
+
+def _p(a: np.ndarray) -> int:
+    """Address of a contiguous array, for the ctypes calls (the caller keeps `a` alive)."""
+    return a.ctypes.data if a.size else _EMPTY.ctypes.data
 
 
 def _reads_args(seq, offsets):
@@ -103,7 +112,7 @@ def semiglobal_column(pattern, ref) -> np.ndarray:
     """D[j] = E[m][j] of Section "Validation" for every end position j of `ref`."""
     P, R = _bytes(pattern), _bytes(ref)
     D = np.empty(max(len(R), 1), np.int32)
-    if _load().oracle_semiglobal_column(P, len(P), R, len(R), D.ctypes.data) != 0:
+    if _load().oracle_semiglobal_column(_p(P), len(P), _p(R), len(R), D.ctypes.data) != 0:
         raise ValueError("non-ACGT character")
     return D[:len(R)]
 
@@ -121,7 +130,7 @@ def map_bruteforce(ref, seq, offsets, k, mode: str = "all") -> np.ndarray:
     S, offs = _reads_args(seq, offsets)
     n = offs.size - 1
     kv = _kvec(k, n)
-    return _collect(_load().oracle_map_bruteforce(R, len(R), S, offs.ctypes.data, n, kv.ctypes.data,
+    return _collect(_load().oracle_map_bruteforce(_p(R), len(R), _p(S), offs.ctypes.data, n, kv.ctypes.data,
                                                   MODES[mode]))
 
 
@@ -131,8 +140,29 @@ def map_filter(ref, seq, offsets, k, q: int, mode: str = "all") -> np.ndarray:
     S, offs = _reads_args(seq, offsets)
     n = offs.size - 1
     kv = _kvec(k, n)
-    return _collect(_load().oracle_map_filter(R, len(R), S, offs.ctypes.data, n, kv.ctypes.data,
+    return _collect(_load().oracle_map_filter(_p(R), len(R), _p(S), offs.ctypes.data, n, kv.ctypes.data,
                                               int(q), MODES[mode]))
+
+
+def annotate(ref, seq, offsets, hits: np.ndarray):
+    """Per hit (a hit set grouped by read): the leftmost alignment start (backward DP, Section
+    "Validation"), the hit-rank and the mapping quality (Section "Postprocessing").  Returns
+    (start int64, rank uint32, mapq int32)."""
+    R = _bytes(ref)
+    S, offs = _reads_args(seq, offsets)
+    n = offs.size - 1
+    hr = np.ascontiguousarray(hits["read"], np.uint32)
+    hs = np.ascontiguousarray(hits["strand"], np.uint8)
+    he = np.ascontiguousarray(hits["end"], np.int64)
+    hd = np.ascontiguousarray(hits["dist"], np.int32)
+    nh = hr.size
+    start = np.empty(max(nh, 1), np.int64)
+    rank = np.empty(max(nh, 1), np.uint32)
+    mapq = np.empty(max(nh, 1), np.int32)
+    if _load().oracle_annotate(_p(R), len(R), _p(S), offs.ctypes.data, n, _p(hr), _p(hs), _p(he), _p(hd), nh,
+                               start.ctypes.data, rank.ctypes.data, mapq.ctypes.data) != 0:
+        raise ValueError("bad input to annotate")
+    return start[:nh], rank[:nh], mapq[:nh]
 
 
 def qgroup_build(codes, payload, q: int, w: int = 32):
@@ -172,7 +202,7 @@ def canonical_text(seq, offsets, q: int):
     total = int(np.maximum(lens - q + 1, 0).sum())
     codes = np.empty(max(total, 1), np.uint64)
     payload = np.empty(max(total, 1), np.uint64)
-    got = _load().oracle_canonical_text(S, offs.ctypes.data, n, q, codes.ctypes.data, payload.ctypes.data)
+    got = _load().oracle_canonical_text(_p(S), offs.ctypes.data, n, q, codes.ctypes.data, payload.ctypes.data)
     if got < 0:
         raise ValueError("bad input")
     return codes[:got], payload[:got]
@@ -183,7 +213,7 @@ def frequent_qgrams(ref, q: int, cap: int, max_out: int = 1 << 20):
     R = _bytes(ref)
     codes = np.empty(max_out, np.uint64)
     counts = np.empty(max_out, np.int64)
-    n = _load().oracle_frequent_qgrams(R, len(R), q, cap, codes.ctypes.data, counts.ctypes.data, max_out)
+    n = _load().oracle_frequent_qgrams(_p(R), len(R), q, cap, codes.ctypes.data, counts.ctypes.data, max_out)
     if n < 0:
         raise ValueError("bad input")
     if n > max_out:

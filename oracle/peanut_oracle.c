@@ -31,11 +31,15 @@
  *   oracle_qgroup_build:   Algorithm 1 (q-group index I, S, S', O) over a text of q-gram codes,
  *                          with GROUPBIT / GROUPRANK / INDEXPAIR as defined in Section
  *                          "The q-group index" and Section "Filtration".
+ *   oracle_annotate:       per hit, the alignment start from the backward DP (Section
+ *                          "Validation"), the hit-rank and the mapping quality (Section
+ *                          "Postprocessing").
  *
  * Readings where the paper is silent: 0-based inclusive end positions in forward coordinates;
  * exclusive cumulative sums in Algorithm 1, S' with one sentinel entry holding |T|; only
  * q-grams lying fully inside one read are indexed.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -559,4 +563,84 @@ int64_t oracle_frequent_qgrams(const char* R, int64_t n, int q, int64_t cap, uin
     }
     free(cs);
     return nout;
+}
+
+/* ---- postprocessing: alignment start, hit-rank, mapping quality ---- */
+
+/* Start of a hit (Section "Validation", last paragraph: the distance of the semi-global
+ * alignment recomputed in backward direction gives the alignment's start).  For a hit of
+ * pattern P (the read, or its reverse complement for strand 1; length m) ending at j with
+ * distance d: G[c] = edit distance between P and R[j-c+1 .. j] for c = 0, 1, ..., the edit matrix
+ * of the reversed pattern against the reference read leftwards from j, with E[0][c] = c (the
+ * alignment must end exactly at j) and E[i][0] = i.  min_c G[c] = d by the definition of D[j].
+ * Reading (the paper does not say which start when several give d): the leftmost one,
+ * start = j - c + 1 for the largest c with G[c] = d; an alignment of cost d spans at most m + d
+ * reference bases, so c <= min(j + 1, m + d).  Returns -1 if no c reaches d (not a hit). */
+static int64_t hit_start(const char* P, int64_t m, const char* R, int64_t j, int32_t d) {
+    int64_t C = m + d;
+    if (C > j + 1) C = j + 1;
+    int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
+    for (int64_t i = 0; i <= m; i++) col[i] = (int32_t)i; /* c = 0: the whole pattern deleted */
+    int64_t best = (col[m] == d) ? 0 : -1;
+    for (int64_t c = 1; c <= C; c++) {
+        const char t = R[j - c + 1];  /* c-th reference base going left */
+        int32_t diag = col[0];
+        col[0] = (int32_t)c;
+        for (int64_t i = 1; i <= m; i++) {
+            int32_t up = col[i];
+            int32_t v = diag + (P[m - i] != t ? 1 : 0); /* i-th pattern base from the right */
+            if (up + 1 < v) v = up + 1;
+            if (col[i - 1] + 1 < v) v = col[i - 1] + 1;
+            col[i] = v;
+            diag = up;
+        }
+        if (col[m] == d) best = c;
+    }
+    free(col);
+    return best < 0 ? -1 : j - best + 1;
+}
+
+/* Section "Postprocessing": for the hits of a read (all of them, both strands), the hit-rank of a
+ * hit is the number of the read's hits whose percent identity (m - d) / m is at least its own,
+ * i.e. whose distance is at most its own; the mapping quality is
+ * min(-10 log10(Pr), 255) with Pr = (rank - 1) / |P|, |P| = n reference positions.  Readings:
+ * rank 1 gives Pr = 0 and quality 255; the quality is the integer part of -10 log10(Pr) computed
+ * in double precision plus 1e-9 (so that ratios at exact powers of ten land on their integer on
+ * any machine), clamped to 0..255.
+ * Hits must be grouped by read.  start[], rank[] and mapq[] receive one value per hit.
+ * Returns 0, or -1 on bad input (non-ACGT base, a hit whose start cannot be found). */
+int oracle_annotate(const char* R, int64_t n, const char* reads, const int64_t* offs, int64_t nreads,
+                    const uint32_t* hr, const uint8_t* hs, const int64_t* he, const int32_t* hd, int64_t nh,
+                    int64_t* start, uint32_t* rank, int32_t* mapq) {
+    if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return -1;
+    int64_t x = 0;
+    while (x < nh) {
+        int64_t y = x;
+        while (y < nh && hr[y] == hr[x]) y++;
+        const uint32_t r = hr[x];
+        if ((int64_t)r >= nreads) return -1;
+        const int64_t m = offs[r + 1] - offs[r];
+        char* fw = (char*)malloc((size_t)m + 1);
+        memcpy(fw, reads + offs[r], (size_t)m);
+        char* rc = revcomp_copy(reads + offs[r], m);
+        for (int64_t z = x; z < y; z++) {
+            if (he[z] < 0 || he[z] >= n) return -1;
+            start[z] = hit_start(hs[z] ? rc : fw, m, R, he[z], hd[z]);
+            if (start[z] < 0) return -1;
+            uint32_t c = 0;
+            for (int64_t u = x; u < y; u++) c += hd[u] <= hd[z] ? 1u : 0u;
+            rank[z] = c;
+            if (c <= 1) {
+                mapq[z] = 255;
+            } else {
+                double q = -10.0 * log10((double)(c - 1) / (double)n);
+                int64_t qi = (int64_t)floor(q + 1e-9);
+                mapq[z] = (int32_t)(qi < 0 ? 0 : qi > 255 ? 255 : qi);
+            }
+        }
+        free(fw);
+        free(rc);
+        x = y;
+    }
+    return 0;
 }

@@ -495,14 +495,14 @@ peanut_status peanut_export_candidates(const peanut_reads* R, uint64_t* n, uint3
                                        uint64_t* lo, uint64_t* hi) {
     return guarded([&] {
         PN_REQUIRE(R && R->magic == kMagicReads && n, PEANUT_INVALID_ARG, "bad batch or NULL n");
-        const uint64_t nc = R->n_cand;
+        const uint64_t nc = R->n_cand, nl = R->n_live;
         if (!read && !strand && !lo && !hi) {
-            *n = nc;
+            *n = nl;
             return;
         }
-        PN_REQUIRE(*n >= nc, PEANUT_INVALID_ARG, "buffers hold %llu entries, %llu needed", (unsigned long long)*n,
-                   (unsigned long long)nc);
-        *n = nc;
+        PN_REQUIRE(*n >= nl, PEANUT_INVALID_ARG, "buffers hold %llu entries, %llu needed", (unsigned long long)*n,
+                   (unsigned long long)nl);
+        *n = nl;
         if (!nc) return;
         uint64_t* k = (uint64_t*)malloc(nc * 8);
         uint64_t* h = (uint64_t*)malloc(nc * 8);
@@ -511,11 +511,16 @@ peanut_status peanut_export_candidates(const peanut_reads* R, uint64_t* n, uint3
         cudaMemcpyAsync(k, R->cand_key.p, nc * 8, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(h, R->cand_hi.p, nc * 8, cudaMemcpyDeviceToHost, s);
         const cudaError_t e = cudaStreamSynchronize(s);
+        uint64_t o = 0;
         for (uint64_t x = 0; x < nc && e == cudaSuccess; ++x) {
-            if (read) read[x] = (uint32_t)(k[x] >> 41);
-            if (strand) strand[x] = (uint8_t)((k[x] >> 40) & 1);
-            if (lo) lo[x] = k[x] & ((1ull << 40) - 1);
-            if (hi) hi[x] = h[x];
+            if (h[x] == ~0ull) continue;  // removed by the q'-gram filter
+            if (o < nl) {
+                if (read) read[o] = (uint32_t)(k[x] >> 41);
+                if (strand) strand[o] = (uint8_t)((k[x] >> 40) & 1);
+                if (lo) lo[o] = k[x] & ((1ull << 40) - 1);
+                if (hi) hi[o] = h[x];
+            }
+            ++o;
         }
         free(k);
         free(h);
@@ -537,6 +542,26 @@ peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t
     return guarded([&] {
         PN_REQUIRE(d_pat && d_pat_off && d_txt && d_txt_off && d_out, PEANUT_INVALID_ARG, "NULL argument");
         bitvector_columns_noalloc(d_pat, d_pat_off, n_pat, d_txt, d_txt_off, d_out, (cudaStream_t)stream);
+    });
+}
+
+peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* reads, const peanut_device_hits* hits,
+                                   uint64_t* d_start, uint32_t* d_rank, uint8_t* d_mapq) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && reads && reads->magic == kMagicReads && hits, PEANUT_INVALID_ARG,
+                   "bad reference, batch or hit list");
+        PN_REQUIRE(reads->ref == ref, PEANUT_INVALID_ARG, "the batch was indexed against another reference");
+        PN_REQUIRE(hits->n == 0 || (hits->read_id && hits->strand && hits->end_pos && hits->dist && d_start && d_rank &&
+                                    d_mapq), PEANUT_INVALID_ARG, "NULL array");
+        annotate_hits(ref, reads, *hits, d_start, d_rank, d_mapq);
+    });
+}
+
+peanut_status peanut_int_peak(uint32_t kind, uint32_t iters, void* stream, double* ms, uint64_t* ops,
+                              uint32_t* grid, uint32_t* block) {
+    return guarded([&] {
+        PN_REQUIRE(ms && ops && grid && block && iters >= 1, PEANUT_INVALID_ARG, "bad arguments");
+        int_peak(kind, iters, (cudaStream_t)stream, ms, ops, grid, block);
     });
 }
 

@@ -279,7 +279,7 @@ struct peanut_engine {
     uint64_t n_submitted = 0, n_completed = 0, n_reads = 0, n_launches = 0, n_tuning = 0;
     struct {
         uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
-        uint64_t bases_scanned = 0, runs = 0;
+        uint64_t bases_scanned = 0, runs = 0, columns = 0, useful_columns = 0;
         double ms_verify = 0, ms_scan = 0, ms_probe = 0;
         double ms_admit = 0, ms_launch = 0, ms_assemble = 0, ms_download = 0;  // wall time per phase
     } sum;
@@ -303,6 +303,11 @@ static double hits_per_read(const peanut_engine* E, const ClassState& C, uint32_
     const double nq = mmax >= q ? (double)(mmax - q + 1) : 1.0;
     return nq / C.stride * (2.0 * 2.0 * (double)E->ref->n / (double)(1ull << (2 * q))) + nq;
 }
+
+// Device bytes per result row held from its launch until its submission is assembled: the row
+// itself (read, strand, end, distance: 14 B) and the assembly's sort keys, values and final
+// arrays (about 48 B).
+constexpr uint64_t kResultHoldBytes = 14 + 48;
 
 static double launch_bytes(const peanut_engine* E, const ClassState& C, uint32_t q, uint64_t n) {
     const double fixed = (double)(((1ull << (2 * q)) + 31) / 32) * 8.0 + (80u << 20);
@@ -493,7 +498,8 @@ static std::shared_ptr<Launch> map_setting(peanut_engine* E, const char* d_seq, 
 }
 
 static double launch_measured_bytes(const peanut_map_stats& st, uint32_t n, uint64_t total, uint64_t nqg) {
-    return 48.0 * st.hits + 12.0 * st.present_probes + 48.0 * st.candidates + 32.0 * st.results +
+    return 48.0 * st.hits + 12.0 * st.present_probes + 48.0 * st.candidates +
+           (32.0 + (double)kResultHoldBytes) * st.results +
            40.0 * st.lowcx_ranges + 3.0 * total + 330.0 * n + 28.0 * nqg;
 }
 
@@ -775,6 +781,8 @@ static void executor(peanut_engine* E, int idx) {
                 E->sum.hits += m.hits;
                 E->sum.candidates += m.candidates;
                 E->sum.word_columns += m.candidate_word_columns;
+                E->sum.columns += m.candidate_columns;
+                E->sum.useful_columns += m.useful_columns;
                 E->sum.present_probes += m.present_probes;
                 E->sum.results += m.results;
                 E->sum.ms_verify += m.ms_verify_kernel;
@@ -792,6 +800,13 @@ static void executor(peanut_engine* E, int idx) {
                 P.launch = L.launch;
                 P.lo = L.bounds[i];
                 P.hi = L.bounds[i + 1];
+                // the part's rows stay in device memory until the submission is assembled, and the
+                // assembly needs its own arrays for them: both are held against the budget until
+                // the submission finishes
+                const uint64_t hold = (P.hi - P.lo) * kResultHoldBytes;
+                S->reserved += hold;
+                E->reserved += hold;
+                E->reserved_peak = std::max(E->reserved_peak, E->reserved);
                 P.base = segs[i].base;
                 P.cls = (uint32_t)c;
                 P.x0 = segs[i].x0;
@@ -1212,6 +1227,8 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->ms_assemble = E->sum.ms_assemble;
         out->ms_download = E->sum.ms_download;
         out->pageable_result_blocks = pageable_blocks();
+        out->candidate_columns = E->sum.columns;
+        out->useful_columns = E->sum.useful_columns;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

@@ -88,8 +88,10 @@ __device__ __forceinline__ uint32_t chunk_code(const uint32_t w[3], int o, uint3
     return q == 16 ? (uint32_t)g : (uint32_t)g & ((1u << (2 * q)) - 1u);
 }
 
-// tab[c] += 1 for the canonical code c of every reference position p <= n - q.
-__global__ void ref_count_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, uint32_t* tab) {
+// tab[c - c0] += 1 for the canonical code c of every reference position p <= n - q with
+// c in [c0, c0 + span) (the table is built one range of codes at a time).
+__global__ void ref_count_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, uint32_t* tab, uint64_t c0,
+                            uint64_t span) {
     const uint64_t nchunks = (n + 31) / 32;
     for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
          ch += (uint64_t)gridDim.x * blockDim.x) {
@@ -100,38 +102,55 @@ __global__ void ref_count_k(const uint32_t* __restrict__ packed, uint64_t n, uin
             if (p + q > n) break;
             const uint32_t g = chunk_code(w, o, q);
             const uint32_t h = revcomp_code(g, q);
-            atomicAdd(&tab[g < h ? g : h], 1u);
+            const uint64_t c = (uint64_t)(g < h ? g : h) - c0;  // wraps above span when below c0
+            if (c < span) atomicAdd(&tab[c], 1u);
         }
     }
 }
 
-__global__ void phi_collect_k(const uint32_t* tab, uint64_t size, uint32_t cap, uint64_t* out,
-                              unsigned long long* n_out) {
-    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < size;
+// Codes of the range (c0 + index) occurring more than cap times, as code << 32 | count; at most
+// max_out are written (the count keeps growing past it).
+__global__ void phi_collect_k(const uint32_t* tab, uint64_t span, uint64_t c0, uint32_t cap, uint64_t* out,
+                              uint64_t max_out, unsigned long long* n_out) {
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < span;
          c += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = tab[c];
         if (v > cap) {
             const unsigned long long i = atomicAdd(n_out, 1ull);
-            if (out) out[i] = (c << 32) | v;
+            if (i < max_out) out[i] = ((c0 + c) << 32) | v;
         }
     }
 }
 
-__global__ void phi_mark_k(const uint64_t* keys, uint32_t n_phi, uint32_t* tab, uint32_t* codes,
-                           uint64_t* counts, uint32_t* filter, uint32_t shift) {
+__global__ void phi_mark_k(const uint64_t* keys, uint32_t n_phi, uint32_t* codes, uint64_t* counts, uint32_t* filter,
+                           uint32_t shift) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_phi) return;
     const uint32_t c = (uint32_t)(keys[i] >> 32);
     codes[i] = c;
     counts[i] = keys[i] & 0xFFFFFFFFull;
-    tab[c] = 0x80000000u | i;
     const uint32_t b = c >> shift;
     atomicOr(&filter[b >> 5], 1u << (b & 31));
 }
 
+// Index of code c in the sorted frequent codes, or -1 (the prefilter bit is tested first).
+__device__ __forceinline__ int64_t phi_index(uint32_t c, const uint32_t* __restrict__ codes, uint32_t n_phi,
+                                             const uint32_t* __restrict__ filter, uint32_t shift) {
+    const uint32_t b = c >> shift;
+    if (!((__ldg(filter + (b >> 5)) >> (b & 31)) & 1u)) return -1;
+    uint32_t lo = 0, hi = n_phi;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(codes + mid) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n_phi && __ldg(codes + lo) == c ? (int64_t)lo : -1;
+}
+
 // For each position whose canonical q-gram is frequent: key = phi << 41 | orientation << 40 | p.
 __global__ void ref_occ_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q,
-                          const uint32_t* __restrict__ tab, uint64_t* occ, unsigned long long* n_occ) {
+                          const uint32_t* __restrict__ codes, uint32_t n_phi, const uint32_t* __restrict__ filter,
+                          uint32_t shift, uint64_t* occ, unsigned long long* n_occ) {
     const uint64_t nchunks = (n + 31) / 32;
     for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
          ch += (uint64_t)gridDim.x * blockDim.x) {
@@ -142,9 +161,9 @@ __global__ void ref_occ_k(const uint32_t* __restrict__ packed, uint64_t n, uint3
             if (p + q > n) break;
             const uint32_t g = chunk_code(w, o, q);
             const uint32_t h = revcomp_code(g, q);
-            const uint32_t v = tab[g < h ? g : h];
-            if (v & 0x80000000u) {
-                const uint64_t phi = v & 0x7FFFFFFFu;
+            const int64_t x = phi_index(g < h ? g : h, codes, n_phi, filter, shift);
+            if (x >= 0) {
+                const uint64_t phi = (uint64_t)x;
                 const unsigned long long i = atomicAdd(n_occ, 1ull);
                 occ[i] = (phi << 41) | ((uint64_t)(g > h) << 40) | p;
             }
@@ -190,6 +209,9 @@ uint32_t default_freq_cap(uint64_t ref_len, uint32_t q) {
     return cap > (double)kDefaultFreqCap ? (cap < 4e9 ? (uint32_t)cap : 4000000000u) : kDefaultFreqCap;
 }
 
+constexpr uint64_t kCountSpan = 1ull << 29;  // codes counted per pass over the reference
+constexpr uint64_t kMaxPhi = 1ull << 23;     // frequent q-grams at most (their index fits 23 bits)
+
 RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s) {
     RefPrep* P = new RefPrep();
     try {
@@ -205,36 +227,41 @@ RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cuda
             P->grp_off.zero();
             return P;
         }
-        DBuf<uint32_t> tab(size, s);
-        tab.zero();
+        // occurrence counts of every canonical code, one range of at most 2^29 codes (a 2 GiB
+        // table) at a time, so that the transient memory stays bounded at q = 16 (4^16 codes)
+        const uint64_t span = size < kCountSpan ? size : kCountSpan;
+        DBuf<uint32_t> tab(span, s);
         const uint64_t nchunks = (n + 31) / 32;
         const unsigned g = grid_for(nchunks, 256, (unsigned)sm_count() * 32);
-        ref_count_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, tab.p);
-        PN_CHECK_LAUNCH();
+        const unsigned gt = grid_for(span, 256, (unsigned)sm_count() * 64);
         DBuf<unsigned long long> cnt(1, s);
         cnt.zero();
-        const unsigned gt = grid_for(size, 256, (unsigned)sm_count() * 64);
-        phi_collect_k<<<gt, 256, 0, s>>>(tab.p, size, cap, nullptr, cnt.p);
-        PN_CHECK_LAUNCH();
+        DBuf<uint64_t> keys(kMaxPhi, s);
+        for (uint64_t c0 = 0; c0 < size; c0 += span) {
+            tab.zero();
+            ref_count_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, tab.p, c0, span);
+            PN_CHECK_LAUNCH();
+            phi_collect_k<<<gt, 256, 0, s>>>(tab.p, span, c0, cap, keys.p, kMaxPhi, cnt.p);
+            PN_CHECK_LAUNCH();
+        }
+        tab.reset();
         const uint64_t n_phi = to_host(cnt.p, s);
-        PN_REQUIRE(n_phi < (1ull << 23), PEANUT_UNSUPPORTED, "too many frequent q-grams (%llu)",
-                   (unsigned long long)n_phi);
+        PN_REQUIRE(n_phi < kMaxPhi, PEANUT_UNSUPPORTED, "too many frequent q-grams (%llu)", (unsigned long long)n_phi);
         P->n_phi = (uint32_t)n_phi;
         if (n_phi == 0) {
             P->grp_off.alloc(1, s);
             P->grp_off.zero();
             return P;
         }
-        DBuf<uint64_t> keys(n_phi, s), tmpk(n_phi, s);
-        cnt.zero();
-        phi_collect_k<<<gt, 256, 0, s>>>(tab.p, size, cap, keys.p, cnt.p);
-        PN_CHECK_LAUNCH();
+        DBuf<uint64_t> tmpk(n_phi, s);
         radix_sort_u64(keys.p, tmpk.p, n_phi, 64, s);
         P->phi_codes.alloc(n_phi, s);
         DBuf<uint64_t> counts(n_phi, s);
-        phi_mark_k<<<grid_for(n_phi, 256), 256, 0, s>>>(keys.p, (uint32_t)n_phi, tab.p, P->phi_codes.p,
-                                                        counts.p, P->filter.p, P->filter_shift);
+        phi_mark_k<<<grid_for(n_phi, 256), 256, 0, s>>>(keys.p, (uint32_t)n_phi, P->phi_codes.p, counts.p,
+                                                        P->filter.p, P->filter_shift);
         PN_CHECK_LAUNCH();
+        keys.reset();
+        tmpk.reset();
         // every occurrence of a frequent q-gram, sorted by (phi, orientation, position)
         DBuf<uint64_t> tot(1, s);
         DBuf<uint64_t> scratch(n_phi, s);
@@ -243,9 +270,9 @@ RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cuda
         P->n_occ = n_occ;
         DBuf<uint64_t> occ(n_occ, s), occ_tmp(n_occ, s);
         cnt.zero();
-        ref_occ_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, tab.p, occ.p, cnt.p);
+        ref_occ_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, P->phi_codes.p, (uint32_t)n_phi, P->filter.p,
+                                    P->filter_shift, occ.p, cnt.p);
         PN_CHECK_LAUNCH();
-        tab.reset();
         int phi_bits = 0;
         while ((1ull << phi_bits) < n_phi) ++phi_bits;
         radix_sort_u64(occ.p, occ_tmp.p, n_occ, 41 + phi_bits, s);

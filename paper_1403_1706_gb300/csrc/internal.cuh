@@ -194,6 +194,7 @@ struct peanut_reads {
     pn::DBuf<uint64_t> cand_key;  // lo (40 bits) | strand << 40 | read << 41
     pn::DBuf<uint64_t> cand_hi;
     uint64_t n_cand = 0;
+    uint64_t n_live = 0;          // of those, ranges the q'-gram filter kept (cand_hi != ~0)
     peanut_map_stats stats = {};
 };
 
@@ -239,6 +240,12 @@ void alloc_device_hits(DeviceHits* H, uint64_t n, cudaStream_t s);
 void free_device_hits(DeviceHits* H);
 void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
                        const uint64_t* txt_off, int32_t* out, cudaStream_t s);
+// post.cu: start, hit-rank and mapping quality of a batch's hits (device arrays of H.n entries)
+void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, uint64_t* d_start,
+                   uint32_t* d_rank, uint8_t* d_mapq);
+// peak.cu: integer issue-rate microbenchmark (timed with CUDA events on s)
+void int_peak(uint32_t kind, uint32_t iters, cudaStream_t s, double* ms, uint64_t* ops, uint32_t* grid,
+              uint32_t* block);
 void bitvector_columns_noalloc(const char* d_pat, const uint64_t* d_pat_off, uint32_t n_pat, const char* d_txt,
                                const uint64_t* d_txt_off, int32_t* d_out, cudaStream_t s);
 }  // namespace pn

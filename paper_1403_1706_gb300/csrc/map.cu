@@ -925,7 +925,7 @@ constexpr int kMergeBuf = 16;   // ranges buffered per source (8 KB per warp)
 // ranges are merged, so every maximal run of end positions lies in one output range.
 __global__ void __launch_bounds__(kMergeWarps * 32)
     lc_kmerge_k(LcParams L, const uint64_t* doff, LcDesc* desc, const uint64_t* off, uint64_t* olo, uint64_t* ohi,
-                uint32_t* ocnt, const uint64_t* ylist, uint32_t ny, uint32_t* cursor) {
+                uint32_t* ocnt, const uint64_t* ylist, uint32_t ny, uint32_t* cursor, uint32_t* n_serial) {
     __shared__ int64_t blo[kMergeWarps][32][kMergeBuf], bhi[kMergeWarps][32][kMergeBuf];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (;;) {
@@ -940,7 +940,10 @@ __global__ void __launch_bounds__(kMergeWarps * 32)
         const uint32_t nd = (uint32_t)(d1 - d0);
         const uint64_t o = off[y];
         if (nd >= 32) {
-            if (lane == 0) lc_kmerge_serial(L, r, s, d0, d1, desc, o, olo, ohi, ocnt + y);
+            if (lane == 0) {
+                atomicAdd(n_serial, 1u);
+                lc_kmerge_serial(L, r, s, d0, d1, desc, o, olo, ohi, ocnt + y);
+            }
             __syncwarp();
             continue;
         }
@@ -1342,7 +1345,7 @@ struct VerifyParams {
     const uint64_t* peq;
     uint32_t* cnt;          // tuples per candidate
     uint64_t* inl;          // 2 inline tuples per candidate: end << 8 | dist
-    unsigned long long* columns;  // [0] columns, [1] columns x words
+    unsigned long long* columns;  // [0] columns, [1] columns x words, [2] columns with D <= k
     // phase 2
     const uint64_t* toff;
     uint32_t* out_read;
@@ -1392,7 +1395,7 @@ struct MyersShared {
 // with distance <= k, leftmost minimum of each run.  Returns the number of columns.  Columns
 // before lo only warm the recurrence up; whole packed words (16 bases) are stepped unrolled.
 template <int W, bool kWrite>
-__device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq) {
+__device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq, unsigned long long& useful) {
     const uint64_t key = V.cand_key[x];
     const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
     const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)V.cand_hi[x];
@@ -1434,6 +1437,7 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
     auto column = [&](uint32_t c, int64_t jj) {
         const int32_t d = M.step(c);
         if (d <= k) {
+            if (!kWrite) ++useful;
             if (!in || d < best) {
                 best = d;
                 bestj = jj;
@@ -1502,13 +1506,144 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq)
     return (uint64_t)(hi - a + 1);
 }
 
+// ---- q'-gram counting filter on candidate ranges (the q-gram lemma per end position) ---------
+//
+// An alignment of a read of length m with e <= k edits ending at reference position j keeps at
+// least m - q' + 1 - q' e of the read's q'-grams intact (each edit touches at most q' of them;
+// Section "The q-group index", q-gram lemma), and every intact one occurs in the reference at a
+// distinct start position p in [j - m - k + 1, j - q' + 1] (the alignment spans at most m + k
+// bases).  So an end j can have distance <= k only if at least T' = m - q' + 1 - q' k reference
+// positions of that window start a q'-gram that occurs in the read.  The filter counts such
+// positions per 16-base block of the reference (one packed word) and, for every block of end
+// positions, sums the counts of the blocks its windows can reach: ends in blocks whose sum is
+// below T' cannot hold a hit.  A candidate range shrinks to its first .. last surviving block
+// (or is dropped), and the bit-vector verification runs only there, with its usual m + k warm-up
+// columns before the new start.  q' = 4: the read's 4-gram set is a 256-bit table per (read,
+// strand).  The result is unchanged: no end with distance <= k is ever removed.
+constexpr int kQf = 4;                  // q'
+constexpr int kFilterThreads = 128;
+constexpr uint64_t kDeadRange = ~0ull;  // cand_hi of a range the filter removed
+
+// 4-gram sets of every read: qset[(r * 2 + s) * 8 + w] bit b = 4-gram 32 w + b occurs in the
+// read (s = 0) or in its reverse complement (s = 1).  One warp per read.
+__global__ void qset_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ base_off, uint32_t n_reads,
+                       uint32_t* __restrict__ qset) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += nw) {
+        const uint64_t b = base_off[r], m = base_off[r + 1] - b;
+        uint32_t f[8] = {}, rc[8] = {};
+        for (uint64_t i = lane; i + kQf <= m; i += 32) {
+            const uint32_t g = (uint32_t)codes[b + i] << 6 | (uint32_t)codes[b + i + 1] << 4 |
+                               (uint32_t)codes[b + i + 2] << 2 | (uint32_t)codes[b + i + 3];
+            // reverse complement: complement every base (3 - c) and reverse their order
+            const uint32_t h = (3u - (g & 3u)) << 6 | (3u - ((g >> 2) & 3u)) << 4 | (3u - ((g >> 4) & 3u)) << 2 |
+                               (3u - (g >> 6));
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                f[w] |= (g >> 5) == (uint32_t)w ? 1u << (g & 31) : 0u;
+                rc[w] |= (h >> 5) == (uint32_t)w ? 1u << (h & 31) : 0u;
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t a = __reduce_or_sync(kFull, f[w]), c = __reduce_or_sync(kFull, rc[w]);
+            if (lane == 0) {
+                qset[(uint64_t)r * 16 + w] = a;
+                qset[(uint64_t)r * 16 + 8 + w] = c;
+            }
+        }
+    }
+}
+
+// One thread per candidate range, in verification order (similar lengths share a warp).  Writes
+// the narrowed range in place (cand_hi = kDeadRange if nothing survives); fstats[0] += reference
+// positions scanned, fstats[1] += surviving ranges, fstats[2] += columns the verification would
+// have run without the filter.
+__global__ void __launch_bounds__(kFilterThreads)
+    qfilter_k(uint64_t* __restrict__ cand_key, uint64_t* __restrict__ cand_hi, const uint64_t* __restrict__ order,
+              uint64_t n, const uint32_t* __restrict__ packed, const uint8_t* __restrict__ len,
+              const uint8_t* __restrict__ kk, const uint32_t* __restrict__ qset, unsigned long long* fstats) {
+    __shared__ uint32_t s_set[8 * kFilterThreads];
+    __shared__ uint8_t s_ring[32 * kFilterThreads];
+    uint32_t* set = s_set + threadIdx.x;
+    uint8_t* ring = s_ring + threadIdx.x;
+    unsigned long long scanned = 0, live = 0, before = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = order[i];
+        const uint64_t key = cand_key[x];
+        const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
+        const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)cand_hi[x];
+        const int64_t m = len[r], k = kk[r];
+        const int64_t a = lo - (m + k) + 1 < 0 ? 0 : lo - (m + k) + 1;
+        before += (unsigned long long)(hi - a + 1);
+        const int64_t T = m - kQf + 1 - (int64_t)kQf * k;  // T'
+        if (T <= 0) {  // nothing can be excluded
+            ++live;
+            continue;
+        }
+#pragma unroll
+        for (int w = 0; w < 8; ++w) set[w * kFilterThreads] = __ldg(qset + ((uint64_t)r * 2 + s) * 8 + w);
+        const int64_t D = (m + k - 1 + 15) >> 4;  // blocks a window reaches before its own
+        const int64_t B0 = a >> 4, J0 = lo >> 4, J1 = hi >> 4;
+        int32_t sum = 0;
+        int64_t first = -1, last = -1;
+        uint32_t wc = __ldg(packed + B0);
+#pragma unroll 1
+        for (int64_t w = B0; w <= J1; ++w) {
+            const uint32_t wn = __ldg(packed + w + 1);
+            int32_t cnt = 0;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {  // the 4-gram starting at base u of this word
+                const uint32_t g = __funnelshift_l(wn, wc, 2 * u) >> 24;
+                cnt += (int32_t)((set[(g >> 5) * kFilterThreads] >> (g & 31)) & 1u);
+            }
+            ring[(w & 31) * kFilterThreads] = (uint8_t)cnt;
+            sum += cnt;
+            if (w - D - 1 >= B0) sum -= ring[((w - D - 1) & 31) * kFilterThreads];
+            if (w >= J0 && sum >= T) {
+                if (first < 0) first = w;
+                last = w;
+            }
+            wc = wn;
+        }
+        scanned += (unsigned long long)(J1 - B0 + 1) * 16;
+        if (first < 0) {
+            cand_hi[x] = kDeadRange;
+        } else {
+            const int64_t nlo = first * 16 > lo ? first * 16 : lo;
+            const int64_t nhi = last * 16 + 15 < hi ? last * 16 + 15 : hi;
+            cand_key[x] = (key & ~kPosMask40) | (uint64_t)nlo;
+            cand_hi[x] = (uint64_t)nhi;
+            ++live;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        scanned += __shfl_xor_sync(kFull, scanned, o);
+        live += __shfl_xor_sync(kFull, live, o);
+        before += __shfl_xor_sync(kFull, before, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(fstats, scanned);
+        atomicAdd(fstats + 1, live);
+        atomicAdd(fstats + 2, before);
+    }
+}
+
 // Work order of the verification: candidates grouped by words per column and by length (8-column
 // steps up to 4088), so that the 32 ranges of a warp take about the same number of steps.
-constexpr int kOrderBits = 11;
+// Ranges the q'-gram filter removed sort last.
+constexpr int kOrderBits = 12;
 __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_t* __restrict__ cand_hi, uint64_t n,
                             const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk, uint64_t* keys,
                             uint64_t* vals) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        vals[x] = x;
+        if (cand_hi[x] == kDeadRange) {
+            keys[x] = 1ull << 11;
+            continue;
+        }
         const uint64_t key = cand_key[x];
         const uint32_t r = (uint32_t)(key >> 41);
         const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)cand_hi[x];
@@ -1518,16 +1653,17 @@ __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_
         const uint64_t cols = (uint64_t)(hi - a + 1) >> 3;
         const uint64_t w = (m + 63) >> 6;
         keys[x] = ((w - 1) << 9) | (cols < 511 ? cols : 511);
-        vals[x] = x;
     }
 }
 
 template <bool kWrite>
-__global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V, const uint64_t* __restrict__ order) {
+__global__ void __launch_bounds__(kVerifyThreads, 8)
+    verify_k(VerifyParams V, const uint64_t* __restrict__ order, const unsigned long long* __restrict__ n_live) {
     __shared__ uint64_t s_eq[4 * kMaxWords * kVerifyThreads];
     uint64_t* seq = s_eq + threadIdx.x;
-    unsigned long long cols = 0, wcols = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V.n_cand;
+    unsigned long long cols = 0, wcols = 0, useful = 0;
+    const uint64_t nl = *n_live;  // surviving ranges come first in `order`
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = order[i];
         if (kWrite && V.cnt[x] <= 2) continue;
@@ -1535,10 +1671,10 @@ __global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V, const
         const uint32_t W = (V.len[r] + 63) >> 6;
         uint64_t c = 0;
         switch (W) {
-            case 1: c = verify_one<1, kWrite>(V, x, seq); break;
-            case 2: c = verify_one<2, kWrite>(V, x, seq); break;
-            case 3: c = verify_one<3, kWrite>(V, x, seq); break;
-            default: c = verify_one<4, kWrite>(V, x, seq); break;
+            case 1: c = verify_one<1, kWrite>(V, x, seq, useful); break;
+            case 2: c = verify_one<2, kWrite>(V, x, seq, useful); break;
+            case 3: c = verify_one<3, kWrite>(V, x, seq, useful); break;
+            default: c = verify_one<4, kWrite>(V, x, seq, useful); break;
         }
         cols += c;
         wcols += c * W;
@@ -1548,10 +1684,12 @@ __global__ void __launch_bounds__(kVerifyThreads) verify_k(VerifyParams V, const
         for (int o = 16; o > 0; o >>= 1) {
             cols += __shfl_xor_sync(kFull, cols, o);
             wcols += __shfl_xor_sync(kFull, wcols, o);
+            useful += __shfl_xor_sync(kFull, useful, o);
         }
         if ((threadIdx.x & 31) == 0) {
             atomicAdd(V.columns, cols);
             atomicAdd(V.columns + 1, wcols);
+            atomicAdd(V.columns + 2, useful);
         }
     }
 }
@@ -1818,7 +1956,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         // block path for segments of up to kMedCap ranges, the k-way merge for the rest
         {
             DBuf<uint64_t> gk(ncap ? ncap : 1, s);
-            DBuf<uint32_t> wide(nseg, s), rest_list(nseg, s), rest(2, s);
+            DBuf<uint32_t> wide(nseg, s), rest_list(nseg, s), rest(3, s);  // count, cursor, serial merges
             wide.zero();
             rest.zero();
             lc_gather_k<<<grid_for(nseg * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(L, doff.p, desc.p,
@@ -1841,8 +1979,9 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
                 PN_CUDA(cudaMemsetAsync(rest.p + 1, 0, sizeof(uint32_t), s));
                 lc_kmerge_k<<<grid_for((uint64_t)n_rest * 32, kMergeWarps * 32, (unsigned)sm_count() * 32),
                               kMergeWarps * 32, 0, s>>>(L, doff.p, desc.p, lc_off.p, lc_keys.p, lc_vals.p, lcnt.p,
-                                                        sy.p, n_rest, rest.p + 1);
+                                                        sy.p, n_rest, rest.p + 1, rest.p + 2);
                 PN_CHECK_LAUNCH();
+                st.lowcx_serial_segments = to_host(rest.p + 2, s);
             }
         }
         lcpos.alloc(n_reads, s);
@@ -1869,17 +2008,35 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.candidates = NC;
     tm.mark();  // 3
 
-    // 4. verification: count + inline pass, offsets, write pass
+    // 4. verification: q'-gram filter, count + inline pass, offsets, write pass
     DBuf<uint32_t> vcnt(NC ? NC : 1, s);
+    vcnt.zero();  // ranges the filter removes report no tuples
     DBuf<uint64_t> inl(2 * (NC ? NC : 1), s), toff(NC ? NC : 1, s);
-    DBuf<unsigned long long> cols(2, s);
+    DBuf<unsigned long long> cols(3, s), fst(3, s);  // fst: filter positions, surviving ranges, columns before
     cols.zero();
+    fst.zero();
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
     const unsigned gv = grid_for(NC, kVerifyThreads, (unsigned)sm_count() * 32);
     DBuf<uint64_t> okey(NC ? NC : 1, s), order(NC ? NC : 1, s);
+    PN_CUDA(cudaEventRecord(kev[10], s));
+    PN_CUDA(cudaEventRecord(kev[11], s));
     if (NC) {
         DBuf<uint64_t> t1(NC, s), t2(NC, s);
+        order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+            R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
+        PN_CHECK_LAUNCH();
+        radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
+        DBuf<uint32_t> qset((uint64_t)n_reads * 16, s);
+        qset_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+            R->codes.p, R->base_off.p, n_reads, qset.p);
+        PN_CHECK_LAUNCH();
+        PN_CUDA(cudaEventRecord(kev[10], s));
+        qfilter_k<<<grid_for(NC, kFilterThreads, (unsigned)sm_count() * 32), kFilterThreads, 0, s>>>(
+            R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, fst.p);
+        PN_CHECK_LAUNCH();
+        PN_CUDA(cudaEventRecord(kev[11], s));
+        // verification order over the narrowed ranges; removed ones last
         order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
             R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
         PN_CHECK_LAUNCH();
@@ -1888,18 +2045,24 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     okey.reset();
     PN_CUDA(cudaEventRecord(kev[2], s));
     if (NC) {
-        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p);
+        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
         PN_CHECK_LAUNCH();
     }
     PN_CUDA(cudaEventRecord(kev[3], s));
     exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
     const uint64_t NT = to_host(tot.p, s);
     {
-        unsigned long long cv[2];
+        unsigned long long cv[3], fv[3];
         PN_CUDA(cudaMemcpyAsync(cv, cols.p, sizeof(cv), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaMemcpyAsync(fv, fst.p, sizeof(fv), cudaMemcpyDeviceToHost, s));
         PN_CUDA(cudaStreamSynchronize(s));
         st.candidate_columns = cv[0];
         st.candidate_word_columns = cv[1];
+        st.useful_columns = cv[2];
+        st.filter_positions = fv[0];
+        st.filter_live = fv[1];
+        st.prefilter_columns = fv[2];
+        R->n_live = fv[1];
     }
     DeviceHits* out = new DeviceHits();
     try {
@@ -1912,7 +2075,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         if (NC) {
             inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
             PN_CHECK_LAUNCH();
-            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p);
+            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
             PN_CHECK_LAUNCH();
         }
         tm.mark();  // 4
@@ -1947,6 +2110,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
     cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
     cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);
+    cudaEventElapsedTime(&st.ms_filter_kernel, kev[10], kev[11]);
     R->stats = st;
     return out;
 }

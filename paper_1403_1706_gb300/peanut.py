@@ -54,7 +54,10 @@ class MapStats(Structure):
                 ("ms_output", c_float), ("ms_scan_kernel", c_float), ("ms_verify_kernel", c_float),
                 ("ms_windows_sweep", c_float), ("ms_lowcx", c_float), ("ms_compact", c_float),
                 ("ms_probe_kernel", c_float), ("ms_windows_med", c_float), ("ms_windows_big", c_float),
-                ("med_reads", c_uint64), ("big_reads", c_uint64), ("lowcx_rest_segments", c_uint64)]
+                ("med_reads", c_uint64), ("big_reads", c_uint64), ("lowcx_rest_segments", c_uint64),
+                ("lowcx_serial_segments", c_uint64), ("useful_columns", c_uint64),
+                ("prefilter_columns", c_uint64), ("filter_positions", c_uint64), ("filter_live", c_uint64),
+                ("ms_filter_kernel", c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,7 +83,8 @@ class EngineStats(Structure):
                 ("bases_scanned", c_uint64), ("ms_verify_kernel", ctypes.c_double),
                 ("ms_scan_kernel", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double),
                 ("ms_admit", ctypes.c_double), ("ms_launch", ctypes.c_double), ("ms_assemble", ctypes.c_double),
-                ("ms_download", ctypes.c_double), ("pageable_result_blocks", c_uint64)]
+                ("ms_download", ctypes.c_double), ("pageable_result_blocks", c_uint64),
+                ("candidate_columns", c_uint64), ("useful_columns", c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
@@ -119,6 +123,9 @@ def load():
                                                 c_void_p]),
         "peanut_bitvector_columns_noalloc": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
                                                   c_void_p]),
+        "peanut_annotate_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_void_p, c_void_p]),
+        "peanut_int_peak": (st, [c_uint32, c_uint32, c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64),
+                                 POINTER(c_uint32), POINTER(c_uint32)]),
         "peanut_engine_create": (st, [c_void_p, POINTER(EngineParams), POINTER(c_void_p)]),
         "peanut_engine_submit": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_int, POINTER(c_uint64)]),
         "peanut_engine_submit_device": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint64, c_int,
@@ -332,9 +339,35 @@ def map_device(ref: Reference, batch: ReadBatch, mode: str = "all") -> DeviceHit
     return DeviceHits(hp)
 
 
+def annotate_hits(ref: Reference, batch: ReadBatch, hits: DeviceHits):
+    """peanut_annotate_hits on a device hit list of the batch: (start, rank, mapq) as torch device
+    tensors (int64, int32 holding the uint32 ranks, uint8), one entry per hit."""
+    import torch
+    n = hits.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    start = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    rank = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    mapq = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    _check(load().peanut_annotate_hits(ref.ptr, batch.ptr, hits._hp, start.data_ptr(), rank.data_ptr(),
+                                       mapq.data_ptr()))
+    return start[:n], rank[:n], mapq[:n]
+
+
 def kernel_launches() -> int:
     """peanut_kernel_launches: kernels launched by the library so far in this process."""
     return int(load().peanut_kernel_launches())
+
+
+INT_PEAK_KINDS = {"lop3": 0, "shf": 1, "iadd": 2, "imad": 3, "popc": 4, "myers_w1": 5, "myers_w2": 6}
+
+
+def int_peak(kind: str, iters: int, stream=None) -> dict:
+    """peanut_int_peak: one timed microbenchmark launch; ops per second of the given kind."""
+    ms, ops, g, b = ctypes.c_double(), c_uint64(), c_uint32(), c_uint32()
+    _check(load().peanut_int_peak(INT_PEAK_KINDS[kind], int(iters), _stream_ptr(stream), ctypes.byref(ms),
+                                  ctypes.byref(ops), ctypes.byref(g), ctypes.byref(b)))
+    return {"kind": kind, "ms": ms.value, "ops": ops.value, "ops_per_s": ops.value / (ms.value / 1e3),
+            "grid": g.value, "block": b.value}
 
 
 def get_map_stats(batch: ReadBatch) -> dict:

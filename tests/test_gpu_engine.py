@@ -305,3 +305,24 @@ def test_sampling_stride_rejects_unfilterable(gpu):
     # 100 bp, k = 5, q = 16: stride 3 leaves 29 sampled q-grams, 5 edits can touch 30
     with pytest.raises(gpu.PeanutError, match="stride"):
         gpu.index_reads(R, reads.seq, reads.offsets, 16, k=5, stride=3)
+
+
+def test_result_heavy_submission_stays_within_budget(gpu):
+    """Reads from a 300-copy family hit ~300 places each: the result rows held from the launches to
+    the submission's assembly are reserved with the launches, so the engine's reserved device
+    memory never exceeds its budget; the hits equal the oracle's."""
+    ref = synth.make_reference(1_500_000, 97)
+    fam = ref[-1000:-700].copy()
+    rng = np.random.default_rng(3)
+    for c in range(300):
+        st = 4000 * c + int(rng.integers(0, 3000))
+        ref[st:st + 300] = fam
+    R = gpu.pack_reference(ref)
+    reads = synth.make_reads(ref[:1_200_000], 3000, 98, lengths=(100,), rate_range=(0.0, 0.02))
+    budget = 2 << 30
+    res, st = run_engine(gpu, R, [reads, reads.slice(0, 1000)], ["all", "best"], executors=2, autotune=False,
+                         max_reads=1500, hbm_budget=budget)
+    assert st["hbm_reserved_peak"] <= budget, st["hbm_reserved_peak"]
+    assert st["results"] > 20_000
+    want = oracle.map_filter(ref, reads.seq, reads.offsets, [k_of(100)] * reads.n, 16, "all")
+    assert np.array_equal(res[0], want)

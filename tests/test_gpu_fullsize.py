@@ -6,6 +6,8 @@ reference (exact hit sets; a read's hits do not depend on the other reads of its
 end lies in a run of ends within k edits whose canonical tuple (found here by a local DP window
 of the oracle) must be in the GPU output.
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -36,30 +38,130 @@ def test_repeat_rich_full_size_sampled(gpu):
         assert np.array_equal(got, want), mode
 
 
+def has_short_period_stretch(read: np.ndarray, length: int = 16, pmax: int = 3) -> bool:
+    """True if some `length`-base stretch of the read repeats with a period of at most `pmax`
+    bases (a poly-A, dinucleotide or trinucleotide run)."""
+    r = np.asarray(read, dtype=np.uint8)
+    for P in range(1, pmax + 1):
+        w = length - P
+        if r.size < length:
+            break
+        bad = np.concatenate([[0], np.cumsum(r[P:] != r[:-P])])
+        if np.any(bad[w:] - bad[:-w] == 0):
+            return True
+    return False
+
+
+def oracle_jobs(ref, jobs, parts, workers=14):
+    """oracle.map_filter for every job (reads, k, q, mode), each split into `parts` slices of its
+    reads, all side by side in threads (ctypes releases the GIL; a read's hits do not depend on the
+    other reads); returns each job's hit set in read order."""
+    tasks = []
+    for j, (sub, k, q, mode) in enumerate(jobs):
+        bounds = np.linspace(0, sub.n, parts + 1).astype(int)
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            if b > a:
+                tasks.append((j, a, b))
+
+    def run(t):
+        j, a, b = t
+        sub, k, q, mode = jobs[j]
+        kk = np.ascontiguousarray(np.asarray(k)[a:b]) if np.ndim(k) else k
+        sl = sub.slice(a, b)
+        h = oracle.map_filter(ref, sl.seq, sl.offsets, kk, q, mode)
+        h["read"] += np.uint32(a)
+        return j, h
+    with ThreadPoolExecutor(min(workers, len(tasks))) as ex:
+        res = list(ex.map(run, tasks))
+    return [oracle.sort_hits(np.concatenate([h for jj, h in res if jj == j])) for j in range(len(jobs))]
+
+
 @pytest.fixture(scope="module")
-def human_batch(gpu):
-    """The first 2^20-read batch of the 3.1 Gbp workload (bench seed), mapped on the GPU."""
+def human_ref(gpu):
     w = synth.WORKLOADS["human_3g1_10m"]
     ref = synth.make_reference(w["ref_len"], 1403, w["repeat_frac"], w["tandem_frac"])
+    return ref, gpu.pack_reference(ref)
+
+
+@pytest.fixture(scope="module")
+def human_batch(gpu, human_ref):
+    """The first 2^20-read batch of the 3.1 Gbp workload (bench seed), mapped on the GPU in both
+    modes with the bench's q = 16, k = 5."""
+    ref, R = human_ref
+    w = synth.WORKLOADS["human_3g1_10m"]
     seed = 1706 + list(synth.WORKLOADS).index("human_3g1_10m")
     reads = synth.make_reads(ref, 1 << 20, seed, lengths=w["lengths"], rate_range=w["rate_range"],
                              random_frac=w["random_frac"])
-    R = gpu.pack_reference(ref)
     B = gpu.index_reads(R, reads.seq, reads.offsets, 16, k=5)
     h = gpu.map(R, B, "all")
-    return ref, reads, h
+    st = gpu.get_map_stats(B)
+    hb = gpu.map(R, B, "best")
+    thr, lowcx = gpu.export_read_params(B)
+    B.free()
+    return ref, reads, h, hb, lowcx, st
 
 
 def test_human_scale_batch_sampled_exact(human_batch):
-    ref, reads, h = human_batch
-    idx = np.arange(0, reads.n, reads.n // 8)[:8]
+    """2,000 evenly spaced reads of the batch plus 150 of the reads the GPU verified around
+    frequent-q-gram clusters, exact against the oracle in both modes.  The low-complexity sample
+    leaves out reads holding a 16-base stretch of period 1-3: against 3.1 Gbp a poly-A read has
+    ~2e8 q-gram hits per strand, more than the oracle's per-diagonal lists hold; those reads are
+    checked exactly at 7 Mbp (test_gpu_lowcx_paths) and 2 Mbp (test_repeat_rich_scaled)."""
+    ref, reads, h, hb, lowcx, st = human_batch
+    assert st["lowcx_rest_segments"] > 0 and st["lowcx_reads"] > 5000
+    even = np.unique(np.linspace(0, reads.n - 1, 2000).astype(np.int64))
+    rng = np.random.default_rng(11)
+    lc = [int(r) for r in rng.permutation(np.flatnonzero(lowcx)) if not has_short_period_stretch(
+        np.frombuffer(reads.read(int(r)), np.uint8))][:150]
+    assert len(lc) == 150
+    idx = np.unique(np.concatenate([even, np.asarray(lc, np.int64)]))
     sub = reads.subset(idx)
-    want = oracle.map_filter(ref, sub.seq, sub.offsets, 5, 16, "all")
-    assert np.array_equal(_hits_of(h, idx), want)
+    wants = oracle_jobs(ref, [(sub, 5, 16, "all"), (sub, 5, 16, "best")], 7)
+    for mode, got, want in (("all", h, wants[0]), ("best", hb, wants[1])):
+        assert np.array_equal(_hits_of(got, idx), want), mode
+
+
+def test_uneven_human_scale_engine_sampled_exact(gpu, human_ref):
+    """The uneven configuration on the 3.1 Gbp reference: 2^17 reads of 50, 75, 100, 150 and
+    250 bp (2 % errors, k = ceil(0.05 L)) in one engine submission, autotuned as in the bench;
+    2,000 evenly spaced reads (without 16-base stretches of period 1-3, as above) exact against
+    the oracle, each length class at the largest q its reads admit."""
+    ref, R = human_ref
+    w = synth.WORKLOADS["uneven_3g1_10m"]
+    reads = synth.make_reads(ref, 1 << 17, 4242, lengths=w["lengths"], rate_range=w["rate_range"],
+                             random_frac=0.0)
+    E = gpu.Engine(R, k_permille=50, executors=2, autotune=True)
+    try:
+        got = {m: E.wait(E.submit(reads.seq, reads.offsets, m)) for m in ("all", "best")}
+    finally:
+        E.free()
+    even = np.unique(np.linspace(0, reads.n - 1, 2000).astype(np.int64))
+    idx = np.asarray([int(r) for r in even if not has_short_period_stretch(
+        np.frombuffer(reads.read(int(r)), np.uint8))], np.int64)
+    assert idx.size > 1900
+    lens = reads.lengths[idx]
+    jobs, sels = [], []
+    for mode in ("all", "best"):
+        for q, sel in ((12, lens == 50), (15, lens == 75), (16, lens >= 100)):
+            sub = reads.subset(idx[sel])
+            jobs.append((sub, synth.k_of_length(sub.lengths, "5pct"), q, mode))
+            sels.append(idx[sel])
+    res = oracle_jobs(ref, jobs, 2)
+    for x, mode in enumerate(("all", "best")):
+        parts = []
+        for y in range(3):
+            want = res[3 * x + y]
+            want["read"] = sels[3 * x + y][want["read"]]
+            parts.append(want)
+        want = oracle.sort_hits(np.concatenate(parts))
+        g = got[mode]
+        keep = np.isin(g["read"], idx.astype(np.uint32))
+        gg = oracle.sort_hits(g[keep].astype(oracle.HIT_DTYPE))
+        assert np.array_equal(gg, want), mode
 
 
 def test_human_scale_batch_properties(human_batch):
-    ref, reads, h = human_batch
+    ref, reads, h, hb, lowcx, st = human_batch
     k = 5
     # sorted by (read, strand, end), unique, within budget
     key = h["read"].astype(np.int64) * 2 + h["strand"]

@@ -207,6 +207,11 @@ def test_hit_heavy_reads_take_every_window_path(gpu, q, stride):
         assert_same_hits(got, want)
     st = gpu.get_map_stats(B)
     assert st["hits"] > reads.n * (2000 if q == 8 else 20000) / stride
+    # the block path (1,025-12,288 hits per read) and the global radix-sorted path (more) ran
+    if q == 8:
+        assert st["med_reads"] > 0, st
+    else:
+        assert st["big_reads"] > 0, st
 
 
 def test_candidates_cover_every_true_end(gpu):

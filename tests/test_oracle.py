@@ -423,3 +423,79 @@ def test_generator_deterministic_and_acgt():
     ra = synth.make_reads(a, 1000, 5, lengths=(50, 75, 100, 150, 250), rate_range=(0.02, 0.02))
     rb = synth.make_reads(a, 1000, 5, lengths=(50, 75, 100, 150, 250), rate_range=(0.02, 0.02))
     assert np.array_equal(ra.seq, rb.seq) and set(np.unique(ra.lengths).tolist()) == {50, 75, 100, 150, 250}
+
+
+# ---------------------------------------------------------------- postprocessing
+
+
+def test_postprocess_hand_example():
+    """Start, hit-rank and mapping quality of the hand example's hits, worked by hand."""
+    g = read_fixture("semiglobal_hand.txt")
+    ref, read, k = g["ref"][0][0], g["read"][0][0], int(g["k"][0][0])
+    h = oracle.map_bruteforce(ref.encode(), read.encode(), [0, len(read)], k)
+    want = [tuple(int(x) for x in row) for row in read_fixture("postprocess_hand.txt")["hit"]]
+    start, rank, mapq = oracle.annotate(ref.encode(), read.encode(), [0, len(read)], h)
+    got = [(int(s), int(e), int(d), int(a), int(b), int(c))
+           for (_, s, e, d), a, b, c in zip(as_tuples(h), start, rank, mapq)]
+    assert got == want
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_start_is_leftmost_substring_at_the_hit_distance(seed):
+    """The start equals the smallest i with Levenshtein(pattern, R[i..end]) = dist, found by trying
+    every substring with the textbook distance (independent of the oracle's backward DP)."""
+    rng = random.Random(40 + seed)
+    ref = rand_seq(rng, 300, "ACGT" if seed else "AC")
+    reads = []
+    for _ in range(12):
+        m = rng.randint(5, 14)
+        p = rng.randrange(0, 300 - m)
+        s = list(ref[p:p + m])
+        for _ in range(rng.randint(0, 2)):
+            x = rng.randrange(len(s))
+            op = rng.random()
+            if op < 0.5:
+                s[x] = rng.choice("ACGT")
+            elif op < 0.75:
+                s.insert(x, rng.choice("ACGT"))
+            elif len(s) > 3:
+                del s[x]
+        reads.append("".join(s))
+    seq = "".join(reads).encode()
+    offs = np.concatenate([[0], np.cumsum([len(r) for r in reads])])
+    h = oracle.map_bruteforce(ref.encode(), seq, offs, 2)
+    assert len(h) > 10
+    start, rank, mapq = oracle.annotate(ref.encode(), seq, offs, h)
+    for (r, s, e, d), st in zip(as_tuples(h), start.tolist()):
+        P = reads[r] if s == 0 else rc(reads[r])
+        dists = [levenshtein(P, ref[i:e + 1]) for i in range(0, e + 2)]
+        assert min(dists) == d
+        assert st == dists.index(d)
+
+
+def test_rank_counts_hits_at_least_as_good_and_mapq_special_cases():
+    """Hit-rank = the read's hits with distance <= the hit's (counted here directly); quality 255
+    at rank 1 (the hand example) and exactly 10 x when (rank - 1) / |P| = 10^-x."""
+    rng = random.Random(5)
+    unit = "ACGTTGCA"
+    ref = (unit * 125)  # 1,000 bases: a 100-base read maps at every period
+    read = (unit * 13)[:100]
+    h = oracle.map_bruteforce(ref.encode(), read.encode(), [0, 100], 3)
+    start, rank, mapq = oracle.annotate(ref.encode(), read.encode(), [0, 100], h)
+    d = h["dist"]
+    for x in range(len(h)):
+        assert rank[x] == int((d <= d[x]).sum())
+    n = len(ref)
+    for x in range(len(h)):
+        if rank[x] == 1:
+            assert mapq[x] == 255
+        elif rank[x] - 1 == n // 10:  # (rank - 1) / |P| = 10^-1
+            assert mapq[x] == 10
+    # 11 separate exact copies of a read on a 100-base reference (no G, so its reverse complement
+    # GGTT never occurs): rank 11, -10 log10(10 / 100) = 10 exactly
+    ref2 = "AACCTT" * 11 + "T" * 34
+    h2 = oracle.map_bruteforce(ref2.encode(), b"AACC", [0, 4], 0)
+    assert len(h2) == 11
+    s2, r2, q2 = oracle.annotate(ref2.encode(), b"AACC", [0, 4], h2)
+    assert r2.tolist() == [11] * 11 and q2.tolist() == [10] * 11
+    assert s2.tolist() == [6 * x for x in range(11)]

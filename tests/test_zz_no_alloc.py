@@ -5,8 +5,9 @@ another allocator's pool (a cudaMalloc there fails or takes memory the pool coun
 latency-critical path that must not pay an allocation's implicit synchronization.  For them
 peanut_bitvector_columns_noalloc takes only caller-owned device buffers and keeps its scratch in
 a fixed array inside the library.  This file checks, through the C ABI, that it returns exactly
-what the allocating entry point (peanut_debug_bitvector_columns) returns, on two calls in a row,
-and that a request larger than the fixed scratch is refused.  It is collected last on purpose.
+what the allocating entry point (peanut_debug_bitvector_columns) returns, and that both equal the
+oracle's DP column, on two calls in a row, and that a request larger than the fixed scratch is
+refused.  It is collected last on purpose.
 """
 import ctypes
 import random
@@ -46,11 +47,15 @@ def _device_buffers(pats, txts):
 
 
 def test_noalloc_equals_allocating_entry_point_twice(gpu):
+    import oracle
     import torch
     lib = gpu.load()
     for seed in (11, 12):  # two calls in a row, different inputs
         pats, txts = _cases(seed)
         want = gpu.bitvector_columns(pats, txts)
+        # the allocating entry point itself equals the oracle's DP column (Section "Validation")
+        for p, t, w in zip(pats, txts, want):
+            assert w.tolist() == oracle.semiglobal_column(p, t).tolist()
         dp, dpo, dt, dto, dout, to = _device_buffers(pats, txts)
         st = lib.peanut_bitvector_columns_noalloc(dp.data_ptr(), dpo.data_ptr(), len(pats), dt.data_ptr(),
                                                   dto.data_ptr(), dout.data_ptr(),
