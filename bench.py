@@ -50,10 +50,11 @@ def int_peaks(peanut, stream=None):
     """The in-repo integer issue-rate microbenchmark (peanut_int_peak), every kind once."""
     out = {}
     for kind, iters in (("lop3", 20000), ("shf", 20000), ("iadd", 20000), ("imad", 20000), ("popc", 20000),
-                        ("myers_w1", 6000), ("myers_w2", 3000)):
+                        ("myers_w1", 6000), ("myers_w2", 3000), ("probe_l2", 400), ("probe_hbm", 100)):
         r = peanut.int_peak(kind, iters, stream)
         out[kind] = {"ops_per_s": r["ops_per_s"], "ms": r["ms"], "ops": r["ops"],
-                     "unit": "word-columns/s" if kind.startswith("myers") else "instructions/s"}
+                     "unit": ("word-columns/s" if kind.startswith("myers") else
+                              "8-byte loads/s" if kind.startswith("probe") else "instructions/s")}
     return out
 
 
@@ -710,10 +711,10 @@ def main():
             identical = bool(identical)
     t_warm = time.time() - t0
 
-    def timed(fn, clocks=False):
+    def timed(fn, clocks=False, engine=True):
         barrier()
         l0 = peanut.kernel_launches()
-        e0 = E.stats()
+        e0 = E.stats() if engine else None
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         clk = ClockSampler(local) if clocks else None
         if clk:
@@ -726,8 +727,8 @@ def main():
         torch.cuda.synchronize()
         if clk:
             clk.__exit__()
-        e1 = E.stats()
-        delta = {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
+        e1 = E.stats() if engine else None
+        delta = None if not engine else {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
                                                "candidate_columns", "useful_columns",
                                                "bases_scanned", "ms_verify_kernel", "ms_scan_kernel",
                                                "ms_admit", "ms_launch", "ms_assemble", "ms_download")}
@@ -762,7 +763,7 @@ def main():
     if tuned is not None:
         qs_t = (tuned["q"], tuned["stride"])
         step_device(qs=qs_t)  # warm-up at this setting
-        ms_t, _, launches_t, _, _ = timed(lambda: step_device(qs=qs_t))
+        ms_t, _, launches_t, _, _ = timed(lambda: step_device(qs=qs_t), engine=False)
         plain_tuned = {"value": units / (ms_t / 1e3), "ms_per_step": ms_t, "q": qs_t[0], "stride": qs_t[1],
                        "gpu_launches": int(launches_t)}
 
@@ -819,10 +820,11 @@ def main():
              "stage_ms_per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
                                     ("ms_scan", "ms_scan_kernel", "ms_probe_kernel", "ms_bin", "ms_windows",
                                      "ms_windows_sweep", "ms_lowcx", "ms_compact", "ms_verify",
-                                     "ms_verify_kernel", "ms_output")},
+                                     "ms_filter_kernel", "ms_verify_kernel", "ms_output")},
              "per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
-                           ("hits", "present_probes", "candidates", "candidate_columns", "useful_columns",
-                            "lowcx_reads", "lowcx_ranges", "lowcx_rest_segments", "results")}}
+                           ("hits", "present_probes", "candidates", "prefilter_columns", "filter_positions",
+                            "filter_live", "candidate_columns", "useful_columns", "lowcx_reads", "lowcx_ranges",
+                            "lowcx_rest_segments", "results")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

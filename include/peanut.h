@@ -284,10 +284,13 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
  *         (add.u32), 3 = integer multiply-add (mad.lo.u32), 4 = population count (popc.b32);
  *         5 / 6 = Myers' column step on 1 / 2 64-bit words with the match masks in shared memory,
  *         one column stream per thread (the verification kernel's recurrence without its
- *         global-memory accesses, run bookkeeping or lane divergence).
- *   iters: loop trips per thread (48 instructions, or 16 columns, per trip).
- *   ms: kernel time; ops: instructions executed (kinds 0-4) or 64-bit word-columns (5, 6), over
- *   all threads; grid / block: the launch shape.
+ *         global-memory accesses, run bookkeeping or lane divergence);
+ *         7 / 8 = random 8-byte loads (eight in flight per thread) from an 8 MiB table (held in
+ *         L2) / a 2 GiB table (HBM): the access pattern of the reference scan's filter and index
+ *         probes (Section "Filtration").
+ *   iters: loop trips per thread (48 instructions, 16 columns, or 8 loads per trip).
+ *   ms: kernel time; ops: instructions executed (kinds 0-4), 64-bit word-columns (5, 6) or loads
+ *   (7, 8), over all threads; grid / block: the launch shape.
  * Errors: INVALID_ARG (NULL pointer, iters = 0, unknown kind), NO_MEMORY, CUDA_ERROR. */
 peanut_status peanut_int_peak(uint32_t kind, uint32_t iters, void* stream, double* ms, uint64_t* ops,
                               uint32_t* grid, uint32_t* block);

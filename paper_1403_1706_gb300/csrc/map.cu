@@ -1516,34 +1516,50 @@ __device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq,
 // positions of that window start a q'-gram that occurs in the read.  The filter counts such
 // positions per 16-base block of the reference (one packed word) and, for every block of end
 // positions, sums the counts of the blocks its windows can reach: ends in blocks whose sum is
-// below T' cannot hold a hit.  A candidate range shrinks to its first .. last surviving block
-// (or is dropped), and the bit-vector verification runs only there, with its usual m + k warm-up
-// columns before the new start.  q' = 4: the read's 4-gram set is a 256-bit table per (read,
-// strand).  The result is unchanged: no end with distance <= k is ever removed.
+// below T' cannot hold a hit.  The intact q'-grams are moreover a sub-multiset of the read's, so
+// a q'-gram that the window repeats more often than the read holds it counts only as often as
+// the read holds it: the count less that excess for the read's most frequent q'-grams is a
+// tighter bound, and on tandem-run text (where the low-complexity reads' candidates lie) it
+// removes most of what the plain count keeps.  A candidate range shrinks to its first .. last
+// surviving block (or is dropped), and the bit-vector verification runs only there, with its
+// usual m + k warm-up columns before the new start.  q' = 4: the read's 4-gram set is a 256-bit
+// table per (read, strand).  The result is unchanged: no end with distance <= k is removed.
 constexpr int kQf = 4;                  // q'
 constexpr int kFilterThreads = 128;
 constexpr uint64_t kDeadRange = ~0ull;  // cand_hi of a range the filter removed
 
+__device__ __forceinline__ uint32_t rc4(uint32_t g) {
+    return (3u - (g & 3u)) << 6 | (3u - ((g >> 2) & 3u)) << 4 | (3u - ((g >> 4) & 3u)) << 2 | (3u - (g >> 6));
+}
+
 // 4-gram sets of every read: qset[(r * 2 + s) * 8 + w] bit b = 4-gram 32 w + b occurs in the
-// read (s = 0) or in its reverse complement (s = 1).  One warp per read.
-__global__ void qset_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ base_off, uint32_t n_reads,
-                       uint32_t* __restrict__ qset) {
+// read (s = 0) or in its reverse complement (s = 1); qtop[r * 2 + s] = the four 4-grams occurring
+// most often there (x: one code per byte, y: their counts per byte, 0xFF for an unused slot;
+// ties go to the smaller code).  One warp per read.
+__global__ void __launch_bounds__(256)
+    qset_k(const uint8_t* __restrict__ codes, const uint64_t* __restrict__ base_off, uint32_t n_reads,
+           uint32_t* __restrict__ qset, uint2* __restrict__ qtop) {
+    __shared__ uint32_t s_hist[8][256];
     const uint32_t lane = threadIdx.x & 31;
+    uint32_t* hist = s_hist[threadIdx.x >> 5];
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += nw) {
         const uint64_t b = base_off[r], m = base_off[r + 1] - b;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) hist[lane * 8 + e] = 0;
+        __syncwarp();
         uint32_t f[8] = {}, rc[8] = {};
         for (uint64_t i = lane; i + kQf <= m; i += 32) {
             const uint32_t g = (uint32_t)codes[b + i] << 6 | (uint32_t)codes[b + i + 1] << 4 |
                                (uint32_t)codes[b + i + 2] << 2 | (uint32_t)codes[b + i + 3];
             // reverse complement: complement every base (3 - c) and reverse their order
-            const uint32_t h = (3u - (g & 3u)) << 6 | (3u - ((g >> 2) & 3u)) << 4 | (3u - ((g >> 4) & 3u)) << 2 |
-                               (3u - (g >> 6));
+            const uint32_t h = rc4(g);
 #pragma unroll
             for (int w = 0; w < 8; ++w) {
                 f[w] |= (g >> 5) == (uint32_t)w ? 1u << (g & 31) : 0u;
                 rc[w] |= (h >> 5) == (uint32_t)w ? 1u << (h & 31) : 0u;
             }
+            atomicAdd(&hist[g], 1u);
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
@@ -1553,6 +1569,31 @@ __global__ void qset_k(const uint8_t* __restrict__ codes, const uint64_t* __rest
                 qset[(uint64_t)r * 16 + 8 + w] = c;
             }
         }
+        __syncwarp();
+        // the four most frequent codes: four rounds of a warp-wide maximum over (count, -code)
+        uint32_t tc = 0, tn = 0, rtc = 0;
+#pragma unroll 1
+        for (int t = 0; t < 4; ++t) {
+            uint32_t best = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t g = lane * 8 + e, v = (hist[g] << 8) | (255u - g);
+                best = v > best ? v : best;
+            }
+            best = __reduce_max_sync(kFull, best);
+            const uint32_t cnt = best >> 8, g = 255u - (best & 255u);
+            __syncwarp();
+            if (lane == 0) hist[g] = 0;
+            __syncwarp();
+            tc |= g << (8 * t);
+            rtc |= rc4(g) << (8 * t);
+            tn |= (cnt ? cnt : 0xFFu) << (8 * t);  // an unused slot never limits the count
+        }
+        if (lane == 0) {
+            qtop[(uint64_t)r * 2] = make_uint2(tc, tn);
+            qtop[(uint64_t)r * 2 + 1] = make_uint2(rtc, tn);
+        }
+        __syncwarp();
     }
 }
 
@@ -1560,14 +1601,25 @@ __global__ void qset_k(const uint8_t* __restrict__ codes, const uint64_t* __rest
 // the narrowed range in place (cand_hi = kDeadRange if nothing survives); fstats[0] += reference
 // positions scanned, fstats[1] += surviving ranges, fstats[2] += columns the verification would
 // have run without the filter.
+//
+// The bound per block J of end positions, over the union U of the blocks J - D .. J that its
+// windows reach: the intact q'-grams of an alignment are a sub-multiset of both the read's and
+// the window's q'-grams, so their number is at most sum over g of min(cnt_read(g), cnt_U(g)) <=
+// (positions of U holding a q'-gram of the read) - sum over the tracked g of
+// max(0, cnt_U(g) - cnt_read(g)), for any set of tracked q'-grams; the read's four most frequent
+// ones are tracked (on tandem-run text the window repeats a few q'-grams far more often than the
+// read holds them).  Their per-block counts are kept four to a word (one byte each, at most 16).
 __global__ void __launch_bounds__(kFilterThreads)
     qfilter_k(uint64_t* __restrict__ cand_key, uint64_t* __restrict__ cand_hi, const uint64_t* __restrict__ order,
               uint64_t n, const uint32_t* __restrict__ packed, const uint8_t* __restrict__ len,
-              const uint8_t* __restrict__ kk, const uint32_t* __restrict__ qset, unsigned long long* fstats) {
+              const uint8_t* __restrict__ kk, const uint32_t* __restrict__ qset, const uint2* __restrict__ qtop,
+              unsigned long long* fstats) {
     __shared__ uint32_t s_set[8 * kFilterThreads];
     __shared__ uint8_t s_ring[32 * kFilterThreads];
+    __shared__ uint32_t s_ring4[32 * kFilterThreads];
     uint32_t* set = s_set + threadIdx.x;
     uint8_t* ring = s_ring + threadIdx.x;
+    uint32_t* ring4 = s_ring4 + threadIdx.x;
     unsigned long long scanned = 0, live = 0, before = 0;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = order[i];
@@ -1584,26 +1636,52 @@ __global__ void __launch_bounds__(kFilterThreads)
         }
 #pragma unroll
         for (int w = 0; w < 8; ++w) set[w * kFilterThreads] = __ldg(qset + ((uint64_t)r * 2 + s) * 8 + w);
+        const uint2 top = __ldg(qtop + (uint64_t)r * 2 + s);
+        const uint32_t G4 = top.x;  // tracked codes, one per byte
+        int32_t cr[4];              // their counts in the read (an unused slot never limits)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t c = (top.y >> (8 * h)) & 0xFFu;
+            cr[h] = c == 0xFFu ? 0x7FFFFFFF : (int32_t)c;
+        }
         const int64_t D = (m + k - 1 + 15) >> 4;  // blocks a window reaches before its own
         const int64_t B0 = a >> 4, J0 = lo >> 4, J1 = hi >> 4;
         int32_t sum = 0;
+        uint32_t u02 = 0, u13 = 0;  // union counts of tracked codes 0 / 2 and 1 / 3 (16 bits each)
         int64_t first = -1, last = -1;
         uint32_t wc = __ldg(packed + B0);
 #pragma unroll 1
         for (int64_t w = B0; w <= J1; ++w) {
             const uint32_t wn = __ldg(packed + w + 1);
             int32_t cnt = 0;
+            uint32_t pc = 0;  // per-byte counts of the tracked codes in this block
 #pragma unroll
             for (int u = 0; u < 16; ++u) {  // the 4-gram starting at base u of this word
                 const uint32_t g = __funnelshift_l(wn, wc, 2 * u) >> 24;
                 cnt += (int32_t)((set[(g >> 5) * kFilterThreads] >> (g & 31)) & 1u);
+                const uint32_t xq = G4 ^ (g * 0x01010101u);  // zero bytes: tracked codes equal to g
+                const uint32_t zb = ~(((xq & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | xq) & 0x80808080u;
+                pc += zb >> 7;
             }
             ring[(w & 31) * kFilterThreads] = (uint8_t)cnt;
+            ring4[(w & 31) * kFilterThreads] = pc;
             sum += cnt;
-            if (w - D - 1 >= B0) sum -= ring[((w - D - 1) & 31) * kFilterThreads];
-            if (w >= J0 && sum >= T) {
-                if (first < 0) first = w;
-                last = w;
+            u02 += pc & 0x00FF00FFu;
+            u13 += (pc >> 8) & 0x00FF00FFu;
+            if (w - D - 1 >= B0) {
+                const uint32_t slot = (uint32_t)((w - D - 1) & 31) * kFilterThreads;
+                sum -= ring[slot];
+                const uint32_t old = ring4[slot];
+                u02 -= old & 0x00FF00FFu;
+                u13 -= (old >> 8) & 0x00FF00FFu;
+            }
+            if (w >= J0) {
+                const int32_t ex = max(0, (int32_t)(u02 & 0xFFFFu) - cr[0]) + max(0, (int32_t)(u13 & 0xFFFFu) - cr[1]) +
+                                   max(0, (int32_t)(u02 >> 16) - cr[2]) + max(0, (int32_t)(u13 >> 16) - cr[3]);
+                if (sum - ex >= T) {
+                    if (first < 0) first = w;
+                    last = w;
+                }
             }
             wc = wn;
         }
@@ -2028,12 +2106,13 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         PN_CHECK_LAUNCH();
         radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
         DBuf<uint32_t> qset((uint64_t)n_reads * 16, s);
+        DBuf<uint2> qtop((uint64_t)n_reads * 2, s);
         qset_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
-            R->codes.p, R->base_off.p, n_reads, qset.p);
+            R->codes.p, R->base_off.p, n_reads, qset.p, qtop.p);
         PN_CHECK_LAUNCH();
         PN_CUDA(cudaEventRecord(kev[10], s));
         qfilter_k<<<grid_for(NC, kFilterThreads, (unsigned)sm_count() * 32), kFilterThreads, 0, s>>>(
-            R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, fst.p);
+            R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, qtop.p, fst.p);
         PN_CHECK_LAUNCH();
         PN_CUDA(cudaEventRecord(kev[11], s));
         // verification order over the narrowed ranges; removed ones last

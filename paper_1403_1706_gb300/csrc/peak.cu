@@ -1,4 +1,5 @@
-// Integer issue-rate microbenchmark: the ceiling for the bit-vector verification kernel.
+// Microbenchmarks for the rooflines: the integer issue rate (the ceiling of the bit-vector
+// verification kernel) and the random-probe rate of L2 and HBM (the ceiling of the reference scan).
 //
 // The verification kernel (Section "Validation", Myers' bit-parallel recurrence) is bound by the
 // integer ALU: 32-bit logic (LOP3), funnel shifts (SHF) and carried adds.  These kernels measure,
@@ -129,12 +130,39 @@ __global__ void __launch_bounds__(256) myers_peak_k(uint32_t seed, uint32_t iter
     if ((uint32_t)x == seed) sink[tid & 1023] = (uint32_t)x;
 }
 
+// Random 8-byte loads from a table of mask + 1 words (eight independent loads in flight per
+// thread, addresses from a counter-based hash): the access pattern of the reference scan's filter
+// and index probes.  The table's size decides whether they hit in L2 or go to HBM.
+__global__ void __launch_bounds__(256) probe_peak_k(const uint64_t* __restrict__ tab, uint64_t mask, uint32_t iters,
+                                                    uint32_t* sink) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t acc = 0;
+    uint64_t h = 0x9E3779B97F4A7C15ull * (tid + 1);
+#pragma unroll 1
+    for (uint32_t it = 0; it < iters; ++it) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            h ^= h >> 31;
+            h *= 0xBF58476D1CE4E5B9ull;
+            v[u] = __ldcg(tab + ((h >> 11) & mask));
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    if ((uint32_t)acc == 0x12345u) sink[tid & 1023] = (uint32_t)acc;
+}
+
 void int_peak(uint32_t kind, uint32_t iters, cudaStream_t s, double* ms, uint64_t* ops, uint32_t* grid,
               uint32_t* block) {
     const unsigned threads = 256;
     unsigned per_sm = 8;  // 2,048 threads per SM
     const unsigned g = (unsigned)sm_count() * per_sm;
     DBuf<uint32_t> sink(1024, s);
+    // probe tables: 8 MiB (resident in the 129 MB L2) or 2 GiB (HBM)
+    const uint64_t words = kind == 7 ? (1ull << 20) : kind == 8 ? (1ull << 28) : 0;
+    DBuf<uint64_t> tab(words, s);
+    if (words) PN_CUDA(cudaMemsetAsync(tab.p, 1, words * 8, s));
     auto launch = [&](uint32_t n_it) {
         switch (kind) {
             case 0: int_peak_k<0><<<g, threads, 0, s>>>(0x1234567u, n_it, sink.p); break;
@@ -144,6 +172,8 @@ void int_peak(uint32_t kind, uint32_t iters, cudaStream_t s, double* ms, uint64_
             case 4: int_peak_k<4><<<g, threads, 0, s>>>(0x1234567u, n_it, sink.p); break;
             case 5: myers_peak_k<1><<<g, threads, 0, s>>>(0x1234567u, n_it, sink.p); break;
             case 6: myers_peak_k<2><<<g, threads, 0, s>>>(0x1234567u, n_it, sink.p); break;
+            case 7:
+            case 8: probe_peak_k<<<g, threads, 0, s>>>(tab.p, words - 1, n_it, sink.p); break;
             default: PN_REQUIRE(false, PEANUT_INVALID_ARG, "unknown microbenchmark kind %u", kind);
         }
         PN_CHECK_LAUNCH();
@@ -161,8 +191,8 @@ void int_peak(uint32_t kind, uint32_t iters, cudaStream_t s, double* ms, uint64_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const uint64_t nthreads = (uint64_t)g * threads;
-    // instructions (kinds 0-4) or word-columns (Myers kinds: 16 columns x W words)
-    const uint64_t per_it = kind <= 4 ? 4ull * kPeakChains : 16ull * (kind == 5 ? 1 : 2);
+    // instructions (kinds 0-4), word-columns (Myers kinds: 16 columns x W words) or loads (probes)
+    const uint64_t per_it = kind <= 4 ? 4ull * kPeakChains : kind <= 6 ? 16ull * (kind == 5 ? 1 : 2) : 8ull;
     *ms = t;
     *ops = nthreads * (uint64_t)iters * per_it;
     *grid = g;

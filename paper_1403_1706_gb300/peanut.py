@@ -358,7 +358,8 @@ def kernel_launches() -> int:
     return int(load().peanut_kernel_launches())
 
 
-INT_PEAK_KINDS = {"lop3": 0, "shf": 1, "iadd": 2, "imad": 3, "popc": 4, "myers_w1": 5, "myers_w2": 6}
+INT_PEAK_KINDS = {"lop3": 0, "shf": 1, "iadd": 2, "imad": 3, "popc": 4, "myers_w1": 5, "myers_w2": 6,
+                  "probe_l2": 7, "probe_hbm": 8}
 
 
 def int_peak(kind: str, iters: int, stream=None) -> dict:
