@@ -763,9 +763,17 @@ def main():
     if tuned is not None:
         qs_t = (tuned["q"], tuned["stride"])
         step_device(qs=qs_t)  # warm-up at this setting
-        ms_t, _, launches_t, _, _ = timed(lambda: step_device(qs=qs_t), engine=False)
+        stats_t = []
+        ms_t, _, launches_t, _, _ = timed(lambda: step_device(stats_t, qs=qs_t), engine=False)
         plain_tuned = {"value": units / (ms_t / 1e3), "ms_per_step": ms_t, "q": qs_t[0], "stride": qs_t[1],
-                       "gpu_launches": int(launches_t)}
+                       "gpu_launches": int(launches_t),
+                       "stage_ms_per_batch": {k2: statistics.mean(x[k2] for x in stats_t) for k2 in
+                                              ("ms_scan_kernel", "ms_probe_kernel", "ms_bin", "ms_windows",
+                                               "ms_lowcx", "ms_compact", "ms_verify", "ms_filter_kernel",
+                                               "ms_verify_kernel")},
+                       "per_batch": {k2: statistics.mean(x[k2] for x in stats_t) for k2 in
+                                     ("hits", "present_probes", "candidates", "filter_live", "candidate_columns",
+                                      "useful_columns", "results")}}
 
     # a short serving leg: the serving configuration's request stream (sizes log-uniform in
     # 10^3..10^6 reads, 50 requests/s), fewer requests, on the same resident reference
