@@ -6,14 +6,19 @@ runs) and 10,000,000 reads of 100 bp (95 % sampled with 1-4 % errors, 5 % random
 device-resident batches of 2^20 reads, q = 16, k = 5, all-hits mode.  One step maps all
 10,000,000 reads (10 batches: peanut_index_reads + peanut_map each).
 
-  value : reads/s with the reads already in device memory (peanut_index_reads_device +
-          peanut_map_device), timed with CUDA events on the mapping stream.
-  e2e   : reads/s through the host API (peanut_index_reads from pinned host memory +
-          peanut_map returning host arrays), host<->device copies inside the timed region.
-  roofline : the verification kernel (the largest launch-list share), algorithmic INT32
-          operations per launch over its CUDA-event duration, against the INT32 issue peak derived
-          from the SM count and clock; roofline_scan: the two reference-scan kernels, algorithmic
-          bytes per launch against the measured HBM copy bandwidth.
+  value : reads/s of the engine with the reads already in device memory and the results left
+          there (peanut_engine_submit_device / peanut_engine_wait_device), timed with CUDA events
+          on the bench's stream; `plain` is the per-batch path (peanut_index_reads_device +
+          peanut_map_device), `plain_tuned` the same at the engine's tuned setting.
+  e2e   : reads/s through the host API (peanut_engine_submit from pinned host memory +
+          peanut_engine_wait returning host arrays), host<->device copies inside the timed region.
+  serving : a short Poisson request stream through the engine: p50 / p99 request latency.
+  roofline : the q'-gram filter on candidate ranges (the largest launch-list share), algorithmic
+          INT32 instructions per launch over its CUDA-event duration, against the measured integer
+          issue rate of the in-repo microbenchmark; roofline_verify: the bit-vector verification
+          kernel, the same way; roofline_scan: the two reference-scan kernels, algorithmic bytes per
+          launch against the measured HBM copy bandwidth, and their L2 probe rate against the
+          measured random-probe rate.
   cpu_baseline : the CPU oracle on a bounded sample of the same workload (see --help).
 
 Launch: `python bench.py [--gpus N --steps K --warmup W]`; for N > 1 under torchrun, each rank
@@ -44,6 +49,10 @@ HIT_BYTES = 4 + 1 + 8 + 1  # read_id, strand, end_pos, dist of one result
 # Xv = Eq | Mv (2), Eq & Pv (2), the carried add (2), Xh (2, one 3-input logic op per half),
 # Ph (2), Mh (2), the two carried one-bit shifts (4 funnel shifts), Pv (2), Mv (2)
 ALG_OPS_PER_WORD_COLUMN = 20
+# The q'-gram filter per reference position scanned, in 32-bit ALU instructions: the 4-gram code
+# (a funnel shift and a shift), the set lookup's word index and bit test and the count (4), the
+# byte compares of the tracked 4-grams (xor, mask, add, zero-byte mask, shift, accumulate: 6)
+FILTER_OPS_PER_POSITION = 12
 
 
 def int_peaks(peanut, stream=None):
@@ -157,7 +166,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_per_unit(name: str, kernel_src_sha: str):
+def traffic_per_unit(name: str, unit: str, kernel_src_sha: str):
     """DRAM bytes per unit of work of a kernel, from the committed ncu summary
     profiles/<name>_traffic.json, if it was taken on the current kernel source; else None."""
     p = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
@@ -166,21 +175,15 @@ def traffic_per_unit(name: str, kernel_src_sha: str):
             d = json.load(f)
         if d.get("source_sha256") != kernel_src_sha:
             return None
-        return float(d["dram_bytes_per_word_column"])
+        return float(d[f"dram_bytes_per_{unit}"])
     except Exception:
         return None
 
 
 def source_sha() -> str:
-    """Hash of the verification kernel's source: the bit-vector verification section of map.cu
-    (up to the best-stratum section) and the shared primitives."""
+    """Hash of the mapping kernels' source (map.cu and the shared headers)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1403_1706_gb300", "csrc", "map.cu"), "rb") as fh:
-        src = fh.read()
-    a = src.index(b"// ---- bit-vector verification")
-    b = src.index(b"// ---- best stratum", a)
-    h.update(src[a:b])
-    for f in ("prims.cuh", "internal.cuh"):
+    for f in ("map.cu", "prims.cuh", "internal.cuh"):
         with open(os.path.join(ROOT, "paper_1403_1706_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -729,7 +732,8 @@ def main():
             clk.__exit__()
         e1 = E.stats() if engine else None
         delta = None if not engine else {f: e1[f] - e0[f] for f in ("map_runs", "hits", "candidate_word_columns", "present_probes",
-                                               "candidate_columns", "useful_columns",
+                                               "candidate_columns", "useful_columns", "filter_positions",
+                                               "ms_filter_kernel",
                                                "bases_scanned", "ms_verify_kernel", "ms_scan_kernel",
                                                "ms_admit", "ms_launch", "ms_assemble", "ms_download")}
         ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda") / args.steps
@@ -790,9 +794,23 @@ def main():
     n_ref = ref.size
     int_peak_tops = ipk["lop3"]["ops_per_s"] / 1e12
     step_peak = ipk["myers_w2"]["ops_per_s"]
-    per_wc = traffic_per_unit("verify_k", source_sha())
+    l2_probe_peak = ipk["probe_l2"]["ops_per_s"]
+    sha = source_sha()
+    per_wc = traffic_per_unit("verify_k", "word_column", sha)
+    per_pos = traffic_per_unit("qfilter_k", "position", sha)
+    peak_note = ("measured: in-repo microbenchmark, 3-input logic (lop3.b32) issue rate "
+                 "(peanut_int_peak kind 0), same process, before the timed region")
 
-    def rooflines(runs, wc, ms_v, probes, hits, bases, ms_s, note):
+    def rooflines(runs, wc, ms_v, probes, hits, bases, ms_s, fpos, ms_f, note):
+        # the q'-gram filter: the dominant kernel by launch-list share (profiles/launches_*.md)
+        f_ops = FILTER_OPS_PER_POSITION * fpos / runs
+        f_ms = ms_f / runs
+        f_ach = f_ops / (f_ms / 1e3) / 1e12
+        filt = {"bound": "alu", "achieved": f_ach, "peak": int_peak_tops, "unit": "TOP/s",
+                "frac": f_ach / int_peak_tops, "traffic": per_pos * fpos / runs if per_pos is not None else None,
+                "kernel": "qfilter_k", "algorithmic_int32_ops_per_launch": f_ops,
+                "ops_per_position": FILTER_OPS_PER_POSITION, "positions_per_launch": fpos / runs,
+                "avg_launch_ms": f_ms, "launches": runs, "peak_source": peak_note, "timing": note}
         v_ops = ALG_OPS_PER_WORD_COLUMN * wc / runs
         v_ms = ms_v / runs
         v_ach = v_ops / (v_ms / 1e3) / 1e12
@@ -800,9 +818,7 @@ def main():
                 "frac": v_ach / int_peak_tops,
                 "traffic": per_wc * wc / runs if per_wc is not None else None, "kernel": "verify_k (count pass)",
                 "algorithmic_int32_ops_per_launch": v_ops, "ops_per_word_column": ALG_OPS_PER_WORD_COLUMN,
-                "avg_launch_ms": v_ms, "launches": runs,
-                "peak_source": "measured: in-repo microbenchmark, 3-input logic (lop3.b32) issue rate "
-                               "(peanut_int_peak kind 0), same process, before the timed region",
+                "avg_launch_ms": v_ms, "launches": runs, "peak_source": peak_note,
                 "word_columns_per_s": wc / runs / (v_ms / 1e3),
                 "step_frac": wc / runs / (v_ms / 1e3) / step_peak,
                 "step_peak_word_columns_per_s": step_peak, "timing": note}
@@ -811,19 +827,24 @@ def main():
         ach = algo / (s_ms / 1e3) / 1e9
         scan = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "kernel": "probe_ref_k + expand_k", "algorithmic_bytes_per_launch": algo,
-                "avg_launch_ms": s_ms, "launches": runs, "peak_source": peak_kind, "timing": note}
-        return roof, scan
+                "avg_launch_ms": s_ms, "launches": runs, "peak_source": peak_kind, "timing": note,
+                "l2_probes_per_s": bases / runs / (s_ms / 1e3),
+                "l2_probe_frac": bases / runs / (s_ms / 1e3) / l2_probe_peak,
+                "l2_probe_peak_per_s": l2_probe_peak}
+        return filt, roof, scan
 
-    roof, roof_scan = rooflines(
+    filt, roof, roof_scan = rooflines(
         edelta["map_runs"], edelta["candidate_word_columns"], edelta["ms_verify_kernel"], edelta["present_probes"],
-        edelta["hits"], edelta["bases_scanned"], edelta["ms_scan_kernel"],
+        edelta["hits"], edelta["bases_scanned"], edelta["ms_scan_kernel"], edelta["filter_positions"],
+        edelta["ms_filter_kernel"],
         f"engine runs, {args.executors} launches in flight: kernels share the GPU with the other stream's work")
-    roof_p, roof_scan_p = rooflines(
+    filt_p, roof_p, roof_scan_p = rooflines(
         len(stats), sum(s["candidate_word_columns"] for s in stats), sum(s["ms_verify_kernel"] for s in stats),
         sum(s["present_probes"] for s in stats), sum(s["hits"] for s in stats), n_ref * len(stats),
-        sum(s["ms_scan_kernel"] for s in stats), "plain path, one launch sequence at a time")
+        sum(s["ms_scan_kernel"] for s in stats), sum(s["filter_positions"] for s in stats),
+        sum(s["ms_filter_kernel"] for s in stats), "plain path, one launch sequence at a time")
     plain = {"value": units / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": int(launches_p),
-             "q": q, "stride": 1, "roofline": roof_p, "roofline_scan": roof_scan_p,
+             "q": q, "stride": 1, "roofline": filt_p, "roofline_verify": roof_p, "roofline_scan": roof_scan_p,
              "results_per_step": int(n_res),
              "stage_ms_per_batch": {k2: statistics.mean(s[k2] for s in stats) for k2 in
                                     ("ms_scan", "ms_scan_kernel", "ms_probe_kernel", "ms_bin", "ms_windows",
@@ -849,8 +870,8 @@ def main():
                        "parallelism": f"read-sharded x{world}",
                        "l2": "no flush: every batch streams a 0.78 GB packed reference and probes a 1 GiB "
                              "index (> 129 MB L2)"},
-            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-            "roofline_scan": roof_scan, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": filt,
+            "roofline_verify": roof, "roofline_scan": roof_scan, "cpu_baseline": cpu,
             "path": "engine (peanut_engine_submit_device / peanut_engine_wait)",
             "plain": plain, "plain_tuned": plain_tuned, "vs_plain": ms_p / ms,
             "vs_plain_tuned": plain_tuned["ms_per_step"] / ms if plain_tuned else None,

@@ -360,6 +360,8 @@ typedef struct {
                                         page-locked and fell back to pageable memory */
     uint64_t candidate_columns;       /* columns run through the bit-vector verification */
     uint64_t useful_columns;          /* of those, columns whose distance is within k */
+    uint64_t filter_positions;        /* reference positions scanned by the q'-gram filter */
+    double ms_filter_kernel;          /* CUDA-event sum of the q'-gram filter kernel */
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with

@@ -279,7 +279,8 @@ struct peanut_engine {
     uint64_t n_submitted = 0, n_completed = 0, n_reads = 0, n_launches = 0, n_tuning = 0;
     struct {
         uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
-        uint64_t bases_scanned = 0, runs = 0, columns = 0, useful_columns = 0;
+        uint64_t bases_scanned = 0, runs = 0, columns = 0, useful_columns = 0, filter_positions = 0;
+        double ms_filter = 0;
         double ms_verify = 0, ms_scan = 0, ms_probe = 0;
         double ms_admit = 0, ms_launch = 0, ms_assemble = 0, ms_download = 0;  // wall time per phase
     } sum;
@@ -783,6 +784,8 @@ static void executor(peanut_engine* E, int idx) {
                 E->sum.word_columns += m.candidate_word_columns;
                 E->sum.columns += m.candidate_columns;
                 E->sum.useful_columns += m.useful_columns;
+                E->sum.filter_positions += m.filter_positions;
+                E->sum.ms_filter += m.ms_filter_kernel;
                 E->sum.present_probes += m.present_probes;
                 E->sum.results += m.results;
                 E->sum.ms_verify += m.ms_verify_kernel;
@@ -1229,6 +1232,8 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->pageable_result_blocks = pageable_blocks();
         out->candidate_columns = E->sum.columns;
         out->useful_columns = E->sum.useful_columns;
+        out->filter_positions = E->sum.filter_positions;
+        out->ms_filter_kernel = E->sum.ms_filter;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

@@ -84,7 +84,8 @@ class EngineStats(Structure):
                 ("ms_scan_kernel", ctypes.c_double), ("ms_probe_kernel", ctypes.c_double),
                 ("ms_admit", ctypes.c_double), ("ms_launch", ctypes.c_double), ("ms_assemble", ctypes.c_double),
                 ("ms_download", ctypes.c_double), ("pageable_result_blocks", c_uint64),
-                ("candidate_columns", c_uint64), ("useful_columns", c_uint64)]
+                ("candidate_columns", c_uint64), ("useful_columns", c_uint64),
+                ("filter_positions", c_uint64), ("ms_filter_kernel", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
