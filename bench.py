@@ -90,6 +90,8 @@ def parse_args():
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
     ap.add_argument("--no-check", action="store_true", help="batched: skip the identical-output check")
     ap.add_argument("--no-serve", action="store_true", help="plain: skip the short serving leg")
+    ap.add_argument("--no-refindex", action="store_true",
+                    help="plain: skip the reference-side q-group index comparison arm")
     ap.add_argument("--serve-requests", type=int, default=30, help="plain: requests of the serving leg")
     return ap.parse_args()
 
@@ -637,10 +639,11 @@ def main():
                             d_seq=d_seq[o0:o1], h_seq=h_seq.numpy()[o0:o1]))
     kw = dict(k=k) if isinstance(k, int) else dict(k_permille=50)
 
-    def step_device(stats=None, qs=(q, 1)):
+    def step_device(stats=None, qs=(q, 1), ri=False):
         n_res = 0
         for bt in batches:
-            RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], qs[0], stream=stream, stride=qs[1], **kw)
+            RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], qs[0], stream=stream, stride=qs[1],
+                                           ref_index=ri, **kw)
             H = peanut.map_device(R, RB)
             n_res += H.n
             if stats is not None:
@@ -779,6 +782,41 @@ def main():
                                      ("hits", "present_probes", "candidates", "filter_live", "candidate_columns",
                                       "useful_columns", "results")}}
 
+    # the reference-side q-group index as a comparison: the same batches at the tuned setting with
+    # their q-grams looked up in the reference's own index instead of streaming the reference
+    refidx = None
+    if tuned is not None and not args.no_refindex:
+        qs_t = (tuned["q"], tuned["stride"])
+        torch.cuda.synchronize()
+        t0 = time.time()
+        peanut.index_reference(R, qs_t[0], stream)
+        torch.cuda.synchronize()
+        t_build = time.time() - t0
+        same = True
+        for bt in batches[:1]:  # identical hits, batch 0, both scans
+            hs = []
+            for ri in (False, True):
+                RB = peanut.index_reads_device(R, bt["d_seq"], bt["d_off"], qs_t[0], stream=stream, stride=qs_t[1],
+                                               ref_index=ri, **kw)
+                H = peanut.map_device(R, RB)
+                hs.append(H.to_numpy())
+                H.free()
+                RB.free()
+            same = bool(np.array_equal(hs[0], hs[1]))
+        step_device(qs=qs_t, ri=True)
+        stats_r = []
+        ms_r, _, launches_r, _, _ = timed(lambda: step_device(stats_r, qs=qs_t, ri=True), engine=False)
+        refidx = {"value": units / (ms_r / 1e3), "ms_per_step": ms_r, "q": qs_t[0], "stride": qs_t[1],
+                  "gpu_launches": int(launches_r), "build_s": t_build, "identical_output_batch0": same,
+                  "scan_kernel_ms_per_batch": statistics.mean(x["ms_scan_kernel"] for x in stats_r),
+                  "streaming_scan_kernel_ms_per_batch": (plain_tuned["stage_ms_per_batch"]["ms_scan_kernel"]
+                                                         if plain_tuned else None),
+                  "stage_ms_per_batch": {k2: statistics.mean(x[k2] for x in stats_r) for k2 in
+                                         ("ms_scan_kernel", "ms_bin", "ms_windows", "ms_lowcx", "ms_compact",
+                                          "ms_verify", "ms_filter_kernel", "ms_verify_kernel")},
+                  "note": "plain path at the engine's tuned setting, hits from the reference's own q-group "
+                          "index (peanut_index_reference, ref_index = 1) instead of the streaming scan"}
+
     # a short serving leg: the serving configuration's request stream (sizes log-uniform in
     # 10^3..10^6 reads, 50 requests/s), fewer requests, on the same resident reference
     serving = None
@@ -875,7 +913,7 @@ def main():
             "path": "engine (peanut_engine_submit_device / peanut_engine_wait)",
             "plain": plain, "plain_tuned": plain_tuned, "vs_plain": ms_p / ms,
             "vs_plain_tuned": plain_tuned["ms_per_step"] / ms if plain_tuned else None,
-            "identical_output": identical, "serving": serving,
+            "identical_output": identical, "serving": serving, "plain_refindex": refidx,
             "int_peak": {kk: {"per_s": v["ops_per_s"], "unit": v["unit"],
                               "per_sm_per_clock": (v["ops_per_s"] / (152 * clocks["sm_mhz"] * 1e6)
                                                    if clocks and clocks.get("sm_mhz") else None)}

@@ -87,6 +87,10 @@ typedef struct {
                             at most ceil(q / stride) sampled q-grams touched per edit).  Exact
                             for any stride the reads admit; 0 or 1 = every offset, 1..64 */
     void* stream;        /* cudaStream_t for all device work of the batch */
+    uint32_t ref_index;  /* 0 = stream the packed reference past the batch's index (Algorithm 2);
+                            1 = look the batch's indexed q-grams up in the reference's own q-group
+                            index instead (built beforehand with peanut_index_reference at this q).
+                            Same hits, same output; a comparison of the two scans */
 } peanut_params;
 
 /* Counters of the last peanut_map() on a batch (diagnostics; all device-computed). */
@@ -131,6 +135,19 @@ peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream,
 
 /* Reference length in bases. */
 uint64_t peanut_ref_length(const peanut_ref* ref);
+
+/* Builds the reference's own q-group index (Algorithm 1 run over the reference's canonical
+ * q-grams: the reference-side index of Section "Filtration", without repeat masking) and keeps
+ * it with the reference; batches indexed with peanut_params.ref_index = 1 at this q then find
+ * their hits by looking their q-grams up in it instead of streaming the reference.  Device
+ * memory: 4^q / 4 bytes for I and S, at most 8.2 bytes per reference position for S' and the
+ * occurrences (26 GB at q = 16 for 3.1 Gbp), and 4 bytes per distinct q-gram more while it is
+ * built; building again at the same q is a no-op.
+ *   ref: a packed reference of fewer than 2^32 bases; q: 1..16; stream: see conventions
+ *   (synchronized).
+ * Errors: INVALID_ARG (bad reference), UNSUPPORTED (q outside 1..16, reference of 2^32 bases or
+ *         more), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_index_reference(peanut_ref* ref, uint32_t q, void* stream);
 
 /* Builds the q-group index (I, S, S', O of Algorithm 1, with the canonical q-gram of every read
  * position, Section "The q-group index") over a batch of reads, on the device.

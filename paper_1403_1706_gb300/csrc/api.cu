@@ -261,6 +261,7 @@ static void check_params(const peanut_params* p) {
     PN_REQUIRE(p->q >= 1 && p->q <= 16, PEANUT_UNSUPPORTED, "q = %u outside 1..16", p->q);
     PN_REQUIRE(p->k_fixed != 0xFFFFFFFFu || p->k_permille <= 1000, PEANUT_INVALID_ARG, "k_permille > 1000");
     PN_REQUIRE(p->stride <= 64, PEANUT_INVALID_ARG, "stride = %u outside 0..64", p->stride);
+    PN_REQUIRE(p->ref_index <= 1, PEANUT_INVALID_ARG, "ref_index = %u outside 0..1", p->ref_index);
 }
 
 peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets, uint32_t n_reads,
@@ -282,8 +283,16 @@ peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint6
         }
         prep = mref->prep[p->q];
     }
+    std::shared_ptr<const RefIndex> rindex;
+    if (p->ref_index) {
+        std::lock_guard<std::mutex> lock(mref->prep_mu);
+        PN_REQUIRE(mref->rindex[p->q], PEANUT_INVALID_ARG,
+                   "ref_index = 1 needs the reference's q-group index at q = %u (peanut_index_reference)", p->q);
+        rindex = mref->rindex[p->q];
+    }
     peanut_reads* R = new peanut_reads();
     try {
+        R->rindex = rindex;
         R->prep = prep;
         R->ref = ref;
         R->stream = s;
@@ -542,6 +551,21 @@ peanut_status peanut_bitvector_columns_noalloc(const char* d_pat, const uint64_t
     return guarded([&] {
         PN_REQUIRE(d_pat && d_pat_off && d_txt && d_txt_off && d_out, PEANUT_INVALID_ARG, "NULL argument");
         bitvector_columns_noalloc(d_pat, d_pat_off, n_pat, d_txt, d_txt_off, d_out, (cudaStream_t)stream);
+    });
+}
+
+peanut_status peanut_index_reference(peanut_ref* ref, uint32_t q, void* stream) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef, PEANUT_INVALID_ARG, "bad reference");
+        PN_REQUIRE(q >= 1 && q <= 16, PEANUT_UNSUPPORTED, "q = %u outside 1..16", q);
+        {
+            std::lock_guard<std::mutex> lock(ref->prep_mu);
+            if (ref->rindex[q]) return;
+        }
+        std::shared_ptr<RefIndex> X(build_ref_index(ref, q, (cudaStream_t)stream));
+        X->rehome();
+        std::lock_guard<std::mutex> lock(ref->prep_mu);
+        if (!ref->rindex[q]) ref->rindex[q] = X;
     });
 }
 

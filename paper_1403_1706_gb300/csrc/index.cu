@@ -533,6 +533,92 @@ __global__ void peq_k(const uint8_t* __restrict__ codes, const uint64_t* __restr
     }
 }
 
+// ---- the reference's own q-group index ---------------------------------------------------
+//
+// Algorithm 1 run over the reference instead of the reads (the reference-side index of Section
+// "Filtration", without repeat masking): every position p <= n - q contributes its canonical
+// code; I / S as for the reads (interleaved per group of 32 codes), S' by an exclusive scan of the
+// per-code counts, O the positions grouped by code, one orientation bit per O entry.
+
+__global__ void ref_set_bits_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, uint2* IS) {
+    const uint64_t nchunks = (n + 31) / 32;
+    for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
+         ch += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p0 = ch * 32;
+        const uint32_t w[3] = {packed[p0 / 16], packed[p0 / 16 + 1], packed[p0 / 16 + 2]};
+        for (int o = 0; o < 32; ++o) {
+            if (p0 + o + q > n) break;
+            const uint32_t g = chunk_code(w, o, q), h = revcomp_code(g, q);
+            const uint32_t c = g < h ? g : h;
+            atomicOr(&IS[c >> 5].x, 1u << (c & 31));
+        }
+    }
+}
+
+template <bool kScatter>
+__global__ void ref_slots_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q,
+                            const uint2* __restrict__ IS, uint32_t* cnt, const uint32_t* __restrict__ Sp,
+                            uint32_t* O, uint32_t* orient) {
+    const uint64_t nchunks = (n + 31) / 32;
+    for (uint64_t ch = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunks;
+         ch += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p0 = ch * 32;
+        const uint32_t w[3] = {packed[p0 / 16], packed[p0 / 16 + 1], packed[p0 / 16 + 2]};
+        for (int o = 0; o < 32; ++o) {
+            if (p0 + o + q > n) break;
+            const uint32_t g = chunk_code(w, o, q), h = revcomp_code(g, q);
+            const uint32_t c = g < h ? g : h;
+            const uint32_t slot = qgram_slot(IS, c);
+            if (!kScatter) {
+                atomicAdd(&cnt[slot], 1u);
+            } else {
+                const uint32_t x = Sp[slot] + atomicAdd(&cnt[slot], 1u);
+                O[x] = (uint32_t)(p0 + o);
+                if (g > h) atomicOr(&orient[x >> 5], 1u << (x & 31));
+            }
+        }
+    }
+}
+
+RefIndex* build_ref_index(const peanut_ref* ref, uint32_t q, cudaStream_t s) {
+    PN_REQUIRE(q >= 1 && q <= 16, PEANUT_UNSUPPORTED, "q = %u outside 1..16", q);
+    PN_REQUIRE(ref->n < (1ull << 32), PEANUT_UNSUPPORTED,
+               "the reference index stores 32-bit positions (the reference has %llu bases)",
+               (unsigned long long)ref->n);
+    RefIndex* X = new RefIndex();
+    try {
+        X->q = q;
+        const uint64_t n = ref->n;
+        X->n_pos = n >= q ? n - q + 1 : 0;
+        X->n_groups = ((1ull << (2 * q)) + 31) / 32;
+        X->IS.alloc(X->n_groups, s);
+        X->IS.zero();
+        const unsigned g = grid_for((n + 31) / 32, 256, (unsigned)sm_count() * 32);
+        ref_set_bits_k<<<g, 256, 0, s>>>(ref->packed.p, n, q, X->IS.p);
+        PN_CHECK_LAUNCH();
+        DBuf<uint64_t> tot(1, s);
+        exclusive_scan(PopcIn{X->IS.p}, SOut{X->IS.p}, X->n_groups, tot.p, s);
+        X->n_distinct = to_host(tot.p, s);
+        DBuf<uint32_t> cnt(X->n_distinct + 1, s);
+        cnt.zero();
+        ref_slots_k<false><<<g, 256, 0, s>>>(ref->packed.p, n, q, X->IS.p, cnt.p, nullptr, nullptr, nullptr);
+        PN_CHECK_LAUNCH();
+        X->Sp.alloc(X->n_distinct + 1, s);
+        exclusive_scan(ArrayIn<uint32_t>{cnt.p}, ArrayOut<uint32_t>{X->Sp.p}, X->n_distinct + 1, nullptr, s);
+        cnt.zero();
+        X->O.alloc(X->n_pos ? X->n_pos : 1, s);
+        X->orient.alloc((X->n_pos + 31) / 32 + 1, s);
+        X->orient.zero();
+        ref_slots_k<true><<<g, 256, 0, s>>>(ref->packed.p, n, q, X->IS.p, cnt.p, X->Sp.p, X->O.p, X->orient.p);
+        PN_CHECK_LAUNCH();
+        PN_CUDA(cudaStreamSynchronize(s));
+    } catch (...) {
+        delete X;
+        throw;
+    }
+    return X;
+}
+
 void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
                  uint32_t k_permille, uint32_t stride) {
     init_lut();

@@ -150,6 +150,17 @@ struct RefPrep {
     }
 };
 
+// ---- the reference's own q-group index (Algorithm 1 over the reference's q-grams) -----------
+struct RefIndex {
+    uint32_t q = 0;
+    uint64_t n_groups = 0, n_distinct = 0, n_pos = 0;
+    DBuf<uint2> IS;         // (I word, S) per group of 32 canonical codes
+    DBuf<uint32_t> Sp;      // n_distinct + 1 starts into O (positions < 2^32)
+    DBuf<uint32_t> O;       // reference positions grouped by canonical code
+    DBuf<uint32_t> orient;  // bit x: occurrence O[x] holds the reverse complement of its code
+    void rehome() { IS.s = Sp.s = O.s = orient.s = nullptr; }
+};
+
 }  // namespace pn
 
 struct peanut_ref {
@@ -159,6 +170,7 @@ struct peanut_ref {
     pn::DBuf<uint32_t> packed;  // base p at bits 30 - 2 (p % 16) of word p / 16
     cudaStream_t stream = nullptr;
     std::shared_ptr<pn::RefPrep> prep[17];  // per q; batches share the table they were indexed with
+    std::shared_ptr<pn::RefIndex> rindex[17];  // per q, built on request (peanut_index_reference)
     std::mutex prep_mu;
 };
 
@@ -167,6 +179,7 @@ struct peanut_reads {
     const peanut_ref* ref = nullptr;
     cudaStream_t stream = nullptr;
     uint32_t q = 0, n_reads = 0, max_len = 0, max_k = 0, freq_cap = 0, stride = 1;
+    std::shared_ptr<const pn::RefIndex> rindex;  // set: hits come from the reference's index
     uint64_t total_bases = 0;
     std::shared_ptr<const pn::RefPrep> prep;  // frequent q-grams of the reference at this q and cap
     // per read
@@ -227,6 +240,7 @@ void free_prep(RefPrep* p);
 void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,
                  uint32_t k_permille, uint32_t stride);
 uint32_t default_freq_cap(uint64_t ref_len, uint32_t q);
+RefIndex* build_ref_index(const peanut_ref* ref, uint32_t q, cudaStream_t s);
 // engine.cu: joins the executor threads and releases everything the engine holds
 void destroy_engine(peanut_engine* E);
 // api.cu: a new batch indexed from reads in device memory (throws Fail on error)

@@ -234,6 +234,88 @@ __global__ void __launch_bounds__(kScanBlock)
     stage_flush(st, scnt, hits, cap, n_hits);
 }
 
+// Algorithm 2 against the reference's own q-group index instead of a pass over the reference
+// (the reference-side index of Section "Filtration", kept whole: no repeat masking).  One entry of
+// the batch's O per lane (an indexed read q-gram: read, orientation, offset): its canonical code
+// from the read's bases, the code's occurrences in the reference index, and for each occurrence the
+// hit key(s) expand_k makes for the same (read q-gram, reference position) pair.  The hits are the
+// same multiset as the streaming scan's, so everything downstream and the output are unchanged.
+__global__ void __launch_bounds__(kScanBlock)
+    refprobe_k(const uint32_t* __restrict__ O, uint64_t n_entries, uint32_t q, const uint8_t* __restrict__ codes,
+               const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len, const uint2* __restrict__ RIS,
+               const uint32_t* __restrict__ RSp, const uint32_t* __restrict__ RO,
+               const uint32_t* __restrict__ Rorient, uint64_t* __restrict__ hits, uint64_t cap,
+               unsigned long long* n_hits, uint32_t* __restrict__ rcount) {
+    __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t* st = stage[wid];
+    uint32_t scnt = 0;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b0 = gwarp * 32; b0 < n_entries; b0 += nwarps * 32) {
+        const uint64_t x = b0 + lane;
+        uint32_t kb = 0, ke = 0, r = 0, fr = 0, i = 0;
+        bool pal = false;
+        if (x < n_entries) {
+            const uint32_t e = __ldg(O + x);
+            r = e >> 9;
+            fr = (e >> 8) & 1u;
+            i = e & 255u;
+            const uint8_t* rd = codes + base_off[r] + i;
+            uint32_t g = 0;
+            for (uint32_t t = 0; t < q; ++t) g = (g << 2) | rd[t];
+            const uint32_t h = revcomp_code(g, q);
+            const uint32_t c = g < h ? g : h;
+            pal = g == h;
+            const uint2 v = __ldg(RIS + (c >> 5));
+            if ((v.x >> (c & 31)) & 1u) {
+                const uint32_t slot = v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
+                kb = __ldg(RSp + slot);
+                ke = __ldg(RSp + slot + 1);
+            }
+        }
+        const int64_t m = x < n_entries ? (int64_t)len[r] : 0;
+        while (true) {
+            const bool has = kb < ke;
+            if (!__any_sync(kFull, has)) break;
+            uint64_t key0 = 0, key1 = 0;
+            int nk = 0;
+            if (has) {
+                const int64_t p = (int64_t)__ldg(RO + kb);
+                const uint32_t fref = (__ldg(Rorient + (kb >> 5)) >> (kb & 31)) & 1u;
+                ++kb;
+                const int64_t dp = p - (int64_t)i + kDiagBias;
+                const int64_t dm = p - (m - (int64_t)q - (int64_t)i) + kDiagBias;
+                const uint64_t rk = (uint64_t)r << 41;
+                if (pal) {
+                    key0 = rk | (uint64_t)dp;
+                    key1 = rk | (1ull << 40) | (uint64_t)dm;
+                    nk = 2;
+                } else if (fr == fref) {
+                    key0 = rk | (uint64_t)dp;
+                    nk = 1;
+                } else {
+                    key0 = rk | (1ull << 40) | (uint64_t)dm;
+                    nk = 1;
+                }
+                atomicAdd(rcount + r, (uint32_t)nk);
+            }
+            const unsigned b1 = __ballot_sync(kFull, nk >= 1), b2 = __ballot_sync(kFull, nk == 2);
+            const uint32_t tot = __popc(b1) + __popc(b2);
+            if (scnt + tot > kStageCap) {
+                stage_flush(st, scnt, hits, cap, n_hits);
+                scnt = 0;
+            }
+            const uint32_t pos = scnt + __popc(b1 & lanemask_lt()) + __popc(b2 & lanemask_lt());
+            if (nk >= 1) st[pos] = key0;
+            if (nk == 2) st[pos + 1] = key1;
+            scnt += tot;
+            __syncwarp();
+        }
+    }
+    stage_flush(st, scnt, hits, cap, n_hits);
+}
+
 // ---- binning hits by read ---------------------------------------------------------------
 
 __global__ void bin_hits_k(const uint64_t* __restrict__ hits, uint64_t nh, const uint64_t* __restrict__ roff,
@@ -1909,7 +1991,8 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     DBuf<uint32_t> pslot;
     uint64_t NP = 0;
     PN_CUDA(cudaEventRecord(kev[0], s));
-    for (int attempt = 0;; ++attempt) {
+    const RefIndex* RX = R->rindex.get();
+    for (int attempt = 0; !RX; ++attempt) {
         pkey.alloc(pcap, s);
         pslot.alloc(pcap, s);
         nh.zero();
@@ -1922,7 +2005,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         pcap = NP + (NP >> 4) + 1024;
         PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "present-position buffer kept overflowing");
     }
-    st.present_probes = NP;
+    st.present_probes = RX ? R->n_indexed : NP;
     PN_CUDA(cudaEventRecord(kev[7], s));
     DBuf<uint64_t> hits;
     uint64_t H = 0;
@@ -1931,8 +2014,14 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         hits.alloc(cap, s);
         rcount.zero();
         PN_CUDA(cudaMemsetAsync(nh.p + 1, 0, sizeof(unsigned long long), s));
-        expand_k<<<gexp, kScanBlock, 0, s>>>(pkey.p, pslot.p, NP, q, R->Sp.p, R->O.p, R->len.p, hits.p, cap, nh.p + 1,
-                                              rcount.p);
+        if (RX) {
+            refprobe_k<<<grid_for(R->n_indexed, kScanBlock, (unsigned)sm_count() * 8), kScanBlock, 0, s>>>(
+                R->O.p, R->n_indexed, q, R->codes.p, R->base_off.p, R->len.p, RX->IS.p, RX->Sp.p, RX->O.p,
+                RX->orient.p, hits.p, cap, nh.p + 1, rcount.p);
+        } else {
+            expand_k<<<gexp, kScanBlock, 0, s>>>(pkey.p, pslot.p, NP, q, R->Sp.p, R->O.p, R->len.p, hits.p, cap,
+                                                  nh.p + 1, rcount.p);
+        }
         PN_CHECK_LAUNCH();
         H = to_host(nh.p + 1, s);
         if (H <= cap) break;

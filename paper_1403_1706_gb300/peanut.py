@@ -32,7 +32,7 @@ class PeanutError(RuntimeError):
 
 class Params(Structure):
     _fields_ = [("q", c_uint32), ("k_fixed", c_uint32), ("k_permille", c_uint32), ("freq_cap", c_uint32),
-                ("stride", c_uint32), ("stream", c_void_p)]
+                ("stride", c_uint32), ("stream", c_void_p), ("ref_index", c_uint32)]
 
 
 class Hits(Structure):
@@ -125,6 +125,7 @@ def load():
         "peanut_bitvector_columns_noalloc": (st, [c_void_p, c_void_p, c_uint32, c_void_p, c_void_p, c_void_p,
                                                   c_void_p]),
         "peanut_annotate_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_void_p, c_void_p]),
+        "peanut_index_reference": (st, [c_void_p, c_uint32, c_void_p]),
         "peanut_int_peak": (st, [c_uint32, c_uint32, c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64),
                                  POINTER(c_uint32), POINTER(c_uint32)]),
         "peanut_engine_create": (st, [c_void_p, POINTER(EngineParams), POINTER(c_void_p)]),
@@ -229,19 +230,25 @@ def pack_reference(seq, stream=None) -> Reference:
     return Reference(out.value)
 
 
-def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None, stride: int = 1) -> Params:
+def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None, stride: int = 1,
+                ref_index: bool = False) -> Params:
     if k is None and k_permille is None:
         raise ValueError("give k or k_permille")
     return Params(q, K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(freq_cap),
-                  int(stride), _stream_ptr(stream))
+                  int(stride), _stream_ptr(stream), 1 if ref_index else 0)
+
+
+def index_reference(ref: "Reference", q: int, stream=None) -> None:
+    """peanut_index_reference: build (once) the reference's own q-group index at this q."""
+    _check(load().peanut_index_reference(ref.ptr, int(q), _stream_ptr(stream)))
 
 
 def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                stream=None, stride: int = 1) -> ReadBatch:
+                stream=None, stride: int = 1, ref_index: bool = False) -> ReadBatch:
     """peanut_index_reads: host reads (concatenated ASCII + n+1 offsets) -> indexed batch."""
     s = _host_u8(seq)
     o = np.ascontiguousarray(offsets, dtype=np.uint64)
-    p = make_params(q, k, k_permille, freq_cap, stream, stride)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index)
     out = c_void_p()
     _check(load().peanut_index_reads(ref.ptr, s.ctypes.data, o.ctypes.data, o.size - 1, ctypes.byref(p),
                                      ctypes.byref(out)))
@@ -249,9 +256,9 @@ def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, f
 
 
 def index_reads_device(ref: Reference, d_seq, d_offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                       stream=None, stride: int = 1) -> ReadBatch:
+                       stream=None, stride: int = 1, ref_index: bool = False) -> ReadBatch:
     """peanut_index_reads_device: reads already in device memory (torch uint8 / int64 tensors)."""
-    p = make_params(q, k, k_permille, freq_cap, stream, stride)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index)
     out = c_void_p()
     n = int(d_offsets.numel()) - 1
     _check(load().peanut_index_reads_device(ref.ptr, d_seq.data_ptr(), d_offsets.data_ptr(), n,
