@@ -200,12 +200,14 @@ const char* peanut_last_error(void);
 /* Number of CUDA kernels this library has launched in this process (diagnostics). */
 uint64_t peanut_kernel_launches(void);
 
-/* Device memory provider for all later allocations (e.g. a caching allocator of the host
- * framework).  alloc(bytes, stream, ctx) returns device memory or NULL; release(ptr, stream,
- * ctx) frees it.  Passing NULL functions restores the default (cudaMallocAsync /
- * cudaFreeAsync on the stream).  Not thread-safe with concurrent calls.  An engine allocates
- * from its own threads on its own streams: a provider installed while engines exist must be
- * thread-safe and accept any stream. */
+/* Device memory provider for all later allocations made on the caller's threads (e.g. the
+ * caching allocator of the host framework; the Python binding installs PyTorch's when a GPU is
+ * present).  alloc(bytes, stream, ctx) returns device memory or NULL; release(ptr, stream, ctx)
+ * frees it.  Passing NULL functions restores the default (cudaMallocAsync / cudaFreeAsync on the
+ * stream, CUDA's stream-ordered pool).  Not thread-safe with concurrent calls.  An engine's own
+ * threads (executors, I/O) always allocate from the stream-ordered pool, so a provider that calls
+ * back into an interpreter never serializes them.  An object is released by the provider that
+ * allocated it, even after another was installed. */
 typedef void* (*peanut_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*peanut_release_fn)(void* ptr, void* stream, void* ctx);
 peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn release, void* ctx);

@@ -31,7 +31,15 @@ static peanut_alloc_fn g_alloc = nullptr;
 static peanut_release_fn g_release = nullptr;
 static void* g_ctx = nullptr;
 
-Allocator current_allocator() { return Allocator{g_alloc, g_release, g_ctx}; }
+// Threads that allocate from CUDA's stream-ordered pool whatever provider is installed (an
+// engine's executors and I/O thread: a provider may call back into an interpreter, which would
+// serialize them).
+static thread_local bool t_pool_only = false;
+void use_pool_on_this_thread() { t_pool_only = true; }
+
+Allocator current_allocator() {
+    return t_pool_only ? Allocator{} : Allocator{g_alloc, g_release, g_ctx};
+}
 
 // Keep memory freed to the process's default CUDA memory pool cached for reuse (release threshold
 // raised once per device), so per-batch temporaries are not returned to the driver and re-mapped
@@ -53,7 +61,7 @@ void* dalloc(size_t bytes, cudaStream_t s, Allocator* used) {
     void* p = nullptr;
     if (bytes == 0) bytes = 1;
     if (used) *used = current_allocator();
-    if (g_alloc) {
+    if (g_alloc && !t_pool_only) {
         p = g_alloc(bytes, (void*)s, g_ctx);
         if (!p) {
             set_error("device allocation of %zu bytes failed (external allocator)", bytes);

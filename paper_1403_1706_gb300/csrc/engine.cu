@@ -660,6 +660,7 @@ static int pick_class(peanut_engine* E) {
 
 static void executor(peanut_engine* E, int idx) {
     cudaSetDevice(E->device);
+    use_pool_on_this_thread();
     cudaStream_t s = E->streams[idx];
     std::unique_lock<std::mutex> lk(E->mu);
     while (!E->stop) {
@@ -876,6 +877,7 @@ static void executor(peanut_engine* E, int idx) {
 // submission order while their footprint fits (none while a tuning run has the GPU).
 static void io_loop(peanut_engine* E) {
     cudaSetDevice(E->device);
+    use_pool_on_this_thread();
     cudaStream_t s = E->io_stream;
     std::unique_lock<std::mutex> lk(E->mu);
     while (!E->stop) {

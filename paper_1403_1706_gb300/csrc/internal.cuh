@@ -77,6 +77,7 @@ struct Allocator {
     void* ctx = nullptr;
 };
 Allocator current_allocator();
+void use_pool_on_this_thread();  // this thread allocates from the stream-ordered pool
 void* dalloc(size_t bytes, cudaStream_t s, Allocator* used = nullptr);  // throws Fail{NO_MEMORY}
 void dfree(void* p, cudaStream_t s, const Allocator& a);
 

@@ -142,6 +142,15 @@ def load():
         f.restype = res
         f.argtypes = args
     _lib = lib
+    # device memory of the calls made from Python comes from PyTorch's caching allocator (the
+    # engines' own threads keep CUDA's stream-ordered pool); PEANUT_DEVICE_ALLOCATOR=cuda opts out
+    if os.environ.get("PEANUT_DEVICE_ALLOCATOR", "torch") != "cuda":
+        try:
+            import torch
+            if torch.cuda.is_available():
+                use_torch_allocator()
+        except ImportError:
+            pass
     return lib
 
 
