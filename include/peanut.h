@@ -124,6 +124,9 @@ typedef struct {
     uint64_t filter_live;      /* candidate ranges it kept (narrowed); the rest hold no end
                                   within k edits */
     float ms_filter_kernel;    /* the filter kernel (CUDA events on its stream) */
+    uint64_t graph_segments;   /* stretches of the call's work launched as CUDA graphs (an engine's
+                                  launches: the scan, the binning and short-read windows, the
+                                  filter and verification count pass, the write pass) */
 } peanut_map_stats;
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
@@ -381,6 +384,7 @@ typedef struct {
     uint64_t useful_columns;          /* of those, columns whose distance is within k */
     uint64_t filter_positions;        /* reference positions scanned by the q'-gram filter */
     double ms_filter_kernel;          /* CUDA-event sum of the q'-gram filter kernel */
+    uint64_t graph_segments;          /* stretches of the launches' work run as CUDA graphs */
 } peanut_engine_stats;
 
 /* Mode flag of engine submissions: keep the result in device memory (take it with

@@ -36,6 +36,7 @@ static void* g_ctx = nullptr;
 // serialize them).
 static thread_local bool t_pool_only = false;
 void use_pool_on_this_thread() { t_pool_only = true; }
+bool pool_on_this_thread() { return t_pool_only; }
 
 Allocator current_allocator() {
     return t_pool_only ? Allocator{} : Allocator{g_alloc, g_release, g_ctx};

@@ -280,6 +280,7 @@ struct peanut_engine {
     struct {
         uint64_t hits = 0, candidates = 0, word_columns = 0, present_probes = 0, results = 0;
         uint64_t bases_scanned = 0, runs = 0, columns = 0, useful_columns = 0, filter_positions = 0;
+        uint64_t graph_segments = 0;
         double ms_filter = 0;
         double ms_verify = 0, ms_scan = 0, ms_probe = 0;
         double ms_admit = 0, ms_launch = 0, ms_assemble = 0, ms_download = 0;  // wall time per phase
@@ -786,6 +787,7 @@ static void executor(peanut_engine* E, int idx) {
                 E->sum.columns += m.candidate_columns;
                 E->sum.useful_columns += m.useful_columns;
                 E->sum.filter_positions += m.filter_positions;
+                E->sum.graph_segments += m.graph_segments;
                 E->sum.ms_filter += m.ms_filter_kernel;
                 E->sum.present_probes += m.present_probes;
                 E->sum.results += m.results;
@@ -1236,6 +1238,7 @@ peanut_status peanut_engine_get_stats(peanut_engine* e, peanut_engine_stats* out
         out->useful_columns = E->sum.useful_columns;
         out->filter_positions = E->sum.filter_positions;
         out->ms_filter_kernel = E->sum.ms_filter;
+        out->graph_segments = E->sum.graph_segments;
         for (int c = 1; c < kQSlots && out->n_classes < 16; ++c) {
             const ClassState& C = E->cls[c];
             if (!C.launches && !C.waiting && C.queue.empty()) continue;

@@ -78,6 +78,45 @@ struct Allocator {
 };
 Allocator current_allocator();
 void use_pool_on_this_thread();  // this thread allocates from the stream-ordered pool
+bool pool_on_this_thread();
+
+// A sync-free stretch of work on stream s captured as a CUDA graph and launched once (when
+// enabled: the thread allocates from the stream-ordered pool, whose allocations and frees become
+// graph memory nodes).  run() ends the capture and launches the graph; the graph is released when
+// the segment is destroyed (after the caller's next synchronization).  An exception inside the
+// captured stretch ends the capture and discards it.
+struct GraphSegment {
+    cudaStream_t s = nullptr;
+    bool on = false, capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    GraphSegment(cudaStream_t st, bool enable) : s(st), on(enable) {
+        if (on) {
+            PN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            capturing = true;
+        }
+    }
+    GraphSegment(const GraphSegment&) = delete;
+    GraphSegment& operator=(const GraphSegment&) = delete;
+    bool run() {
+        if (!on) return false;
+        capturing = false;
+        PN_CUDA(cudaStreamEndCapture(s, &g));
+        PN_CUDA(cudaGraphInstantiate(&x, g, 0));
+        PN_CUDA(cudaGraphLaunch(x, s));
+        return true;
+    }
+    ~GraphSegment() {
+        if (capturing) {
+            cudaGraph_t t = nullptr;
+            cudaStreamEndCapture(s, &t);
+            if (t) cudaGraphDestroy(t);
+            cudaGetLastError();
+        }
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+    }
+};
 void* dalloc(size_t bytes, cudaStream_t s, Allocator* used = nullptr);  // throws Fail{NO_MEMORY}
 void dfree(void* p, cudaStream_t s, const Allocator& a);
 

@@ -170,10 +170,12 @@ __global__ void __launch_bounds__(kScanBlock, 4)
 }
 
 __global__ void __launch_bounds__(kScanBlock)
-    expand_k(const uint64_t* __restrict__ pkey, const uint32_t* __restrict__ pslot, uint64_t npres, uint32_t q,
+    expand_k(const uint64_t* __restrict__ pkey, const uint32_t* __restrict__ pslot,
+             const unsigned long long* __restrict__ d_npres, uint64_t pcap, uint32_t q,
              const uint32_t* __restrict__ Sp, const uint32_t* __restrict__ O, const uint8_t* __restrict__ len,
              uint64_t* __restrict__ hits, uint64_t cap, unsigned long long* n_hits, uint32_t* __restrict__ rcount) {
     __shared__ uint64_t stage[kScanBlock / 32][kStageCap];
+    const uint64_t npres = *d_npres < pcap ? *d_npres : pcap;  // present positions (counted on the device)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t* st = stage[wid];
     uint32_t scnt = 0;
@@ -1987,77 +1989,87 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     int per_sm = 0;
     PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k, kScanBlock, 0));
     const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
+    const unsigned gexp = (unsigned)sm_count() * 8;  // persistent: the count of present positions is on the device
+    // Sync-free stretches run as CUDA graphs on threads that allocate from the stream-ordered pool
+    // (an engine's executors); elsewhere the same launches run one by one.
+    const bool graphs = pool_on_this_thread();
     DBuf<uint64_t> pkey;
     DBuf<uint32_t> pslot;
-    uint64_t NP = 0;
-    PN_CUDA(cudaEventRecord(kev[0], s));
-    const RefIndex* RX = R->rindex.get();
-    for (int attempt = 0; !RX; ++attempt) {
-        pkey.alloc(pcap, s);
-        pslot.alloc(pcap, s);
-        nh.zero();
-        probe_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->bloom.p, R->bloom_mask, pkey.p,
-                                                 pslot.p, pcap, nh.p);
-        PN_CHECK_LAUNCH();
-        NP = to_host(nh.p, s);
-        if (NP <= pcap) break;
-        st.scan_retries++;
-        pcap = NP + (NP >> 4) + 1024;
-        PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "present-position buffer kept overflowing");
-    }
-    st.present_probes = RX ? R->n_indexed : NP;
-    PN_CUDA(cudaEventRecord(kev[7], s));
     DBuf<uint64_t> hits;
-    uint64_t H = 0;
-    const unsigned gexp = grid_for(NP * 32 / 32, kScanBlock, (unsigned)sm_count() * 8);
+    uint64_t NP = 0, H = 0;
+    const RefIndex* RX = R->rindex.get();
     for (int attempt = 0;; ++attempt) {
+        // capacity-sized buffers; the kernels count past the capacity, so an overflow is seen once
+        // afterwards and the scan runs again with the exact sizes
+        if (!RX) {
+            pkey.alloc(pcap, s);
+            pslot.alloc(pcap, s);
+        }
         hits.alloc(cap, s);
+        GraphSegment seg(s, graphs);
+        PN_CUDA(cudaEventRecord(kev[0], s));
+        nh.zero();
         rcount.zero();
-        PN_CUDA(cudaMemsetAsync(nh.p + 1, 0, sizeof(unsigned long long), s));
+        if (!RX) {
+            probe_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->bloom.p, R->bloom_mask, pkey.p,
+                                                     pslot.p, pcap, nh.p);
+            PN_CHECK_LAUNCH();
+        }
+        PN_CUDA(cudaEventRecord(kev[7], s));
         if (RX) {
             refprobe_k<<<grid_for(R->n_indexed, kScanBlock, (unsigned)sm_count() * 8), kScanBlock, 0, s>>>(
                 R->O.p, R->n_indexed, q, R->codes.p, R->base_off.p, R->len.p, RX->IS.p, RX->Sp.p, RX->O.p,
                 RX->orient.p, hits.p, cap, nh.p + 1, rcount.p);
         } else {
-            expand_k<<<gexp, kScanBlock, 0, s>>>(pkey.p, pslot.p, NP, q, R->Sp.p, R->O.p, R->len.p, hits.p, cap,
-                                                  nh.p + 1, rcount.p);
+            expand_k<<<gexp, kScanBlock, 0, s>>>(pkey.p, pslot.p, nh.p, pcap, q, R->Sp.p, R->O.p, R->len.p, hits.p,
+                                                  cap, nh.p + 1, rcount.p);
         }
         PN_CHECK_LAUNCH();
-        H = to_host(nh.p + 1, s);
-        if (H <= cap) break;
+        PN_CUDA(cudaEventRecord(kev[1], s));
+        st.graph_segments += seg.run() ? 1 : 0;
+        unsigned long long c[2];
+        PN_CUDA(cudaMemcpyAsync(c, nh.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+        NP = c[0];
+        H = c[1];
+        if ((RX || NP <= pcap) && H <= cap) break;
         st.scan_retries++;
-        cap = H + (H >> 4) + 1024;
-        PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "hit buffer kept overflowing");
+        if (!RX && NP > pcap) pcap = NP + (NP >> 4) + 1024;
+        if (H > cap) cap = H + (H >> 4) + 1024;
+        PN_REQUIRE(attempt < 3, PEANUT_NO_MEMORY, "present-position or hit buffer kept overflowing");
     }
-    PN_CUDA(cudaEventRecord(kev[1], s));
+    st.present_probes = RX ? R->n_indexed : NP;
     pkey.reset();
     pslot.reset();
     st.hits = H;
     tm.mark();  // 1
 
-    // 2. bin by read
+    // 2. bin by read, 3. windows of reads with few hits (one graph)
     DBuf<uint64_t> roff((uint64_t)n_reads + 1, s), tot(1, s);
-    exclusive_scan(ArrayIn<uint32_t>{rcount.p}, ArrayOut<uint64_t>{roff.p}, n_reads, tot.p, s);
-    PN_CUDA(cudaMemcpyAsync(roff.p + n_reads, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     DBuf<uint64_t> binned(H ? H : 1, s);
-    rcount.zero();
-    bin_hits_k<<<grid_for(H, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(hits.p, H, roff.p, rcount.p, binned.p);
-    PN_CHECK_LAUNCH();
-    hits.reset();
-    tm.mark();  // 2
-
-    // 3. windows
     DBuf<uint64_t> wlo(H ? H : 1, s), whi(H ? H : 1, s);
     DBuf<uint32_t> wcnt(2 * (uint64_t)n_reads, s);
     DBuf<uint32_t> big_list(n_reads, s), med_list(n_reads, s), nbig(3, s);  // big, medium, cursor
-    nbig.zero();
     WinParams WP{roff.p, R->len.p, R->kk.p, R->thr.p, n, wlo.p, whi.p, wcnt.p};
-    windows_k<<<grid_for((uint64_t)n_reads * 32, kWinWarps * 32, (unsigned)sm_count() * 16), kWinWarps * 32, 0, s>>>(
-        binned.p, n_reads, WP, big_list.p, nbig.p, med_list.p);
-    PN_CHECK_LAUNCH();
     uint32_t nbm[2];
-    PN_CUDA(cudaMemcpyAsync(nbm, nbig.p, sizeof(nbm), cudaMemcpyDeviceToHost, s));
-    PN_CUDA(cudaStreamSynchronize(s));
+    {
+        GraphSegment seg(s, graphs);
+        exclusive_scan(ArrayIn<uint32_t>{rcount.p}, ArrayOut<uint64_t>{roff.p}, n_reads, tot.p, s);
+        PN_CUDA(cudaMemcpyAsync(roff.p + n_reads, tot.p, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        rcount.zero();
+        bin_hits_k<<<grid_for(H, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(hits.p, H, roff.p, rcount.p,
+                                                                                binned.p);
+        PN_CHECK_LAUNCH();
+        tm.mark();  // 2
+        nbig.zero();
+        windows_k<<<grid_for((uint64_t)n_reads * 32, kWinWarps * 32, (unsigned)sm_count() * 16), kWinWarps * 32, 0,
+                    s>>>(binned.p, n_reads, WP, big_list.p, nbig.p, med_list.p);
+        PN_CHECK_LAUNCH();
+        st.graph_segments += seg.run() ? 1 : 0;
+        PN_CUDA(cudaMemcpyAsync(nbm, nbig.p, sizeof(nbm), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+    }
+    hits.reset();
     const uint32_t n_big = nbm[0], n_med = nbm[1];
     st.med_reads = n_med;
     st.big_reads = n_big;
@@ -2175,52 +2187,54 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.candidates = NC;
     tm.mark();  // 3
 
-    // 4. verification: q'-gram filter, count + inline pass, offsets, write pass
+    // 4. verification: q'-gram filter, count + inline pass, offsets (one graph), write pass (one graph)
     DBuf<uint32_t> vcnt(NC ? NC : 1, s);
-    vcnt.zero();  // ranges the filter removes report no tuples
     DBuf<uint64_t> inl(2 * (NC ? NC : 1), s), toff(NC ? NC : 1, s);
     DBuf<unsigned long long> cols(3, s), fst(3, s);  // fst: filter positions, surviving ranges, columns before
-    cols.zero();
-    fst.zero();
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
     const unsigned gv = grid_for(NC, kVerifyThreads, (unsigned)sm_count() * 32);
     DBuf<uint64_t> okey(NC ? NC : 1, s), order(NC ? NC : 1, s);
-    PN_CUDA(cudaEventRecord(kev[10], s));
-    PN_CUDA(cudaEventRecord(kev[11], s));
-    if (NC) {
-        DBuf<uint64_t> t1(NC, s), t2(NC, s);
-        order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
-            R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
-        PN_CHECK_LAUNCH();
-        radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
-        DBuf<uint32_t> qset((uint64_t)n_reads * 16, s);
-        DBuf<uint2> qtop((uint64_t)n_reads * 2, s);
-        qset_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
-            R->codes.p, R->base_off.p, n_reads, qset.p, qtop.p);
-        PN_CHECK_LAUNCH();
-        PN_CUDA(cudaEventRecord(kev[10], s));
-        qfilter_k<<<grid_for(NC, kFilterThreads, (unsigned)sm_count() * 32), kFilterThreads, 0, s>>>(
-            R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, qtop.p, fst.p);
-        PN_CHECK_LAUNCH();
-        PN_CUDA(cudaEventRecord(kev[11], s));
-        // verification order over the narrowed ranges; removed ones last
-        order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
-            R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
-        PN_CHECK_LAUNCH();
-        radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
-    }
-    okey.reset();
-    PN_CUDA(cudaEventRecord(kev[2], s));
-    if (NC) {
-        verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
-        PN_CHECK_LAUNCH();
-    }
-    PN_CUDA(cudaEventRecord(kev[3], s));
-    exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
-    const uint64_t NT = to_host(tot.p, s);
+    uint64_t NT = 0;
     {
+        GraphSegment seg(s, graphs);
+        vcnt.zero();  // ranges the filter removes report no tuples
+        cols.zero();
+        fst.zero();
+        PN_CUDA(cudaEventRecord(kev[10], s));
+        PN_CUDA(cudaEventRecord(kev[11], s));
+        if (NC) {
+            DBuf<uint64_t> t1(NC, s), t2(NC, s);
+            order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+                R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
+            PN_CHECK_LAUNCH();
+            radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
+            DBuf<uint32_t> qset((uint64_t)n_reads * 16, s);
+            DBuf<uint2> qtop((uint64_t)n_reads * 2, s);
+            qset_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+                R->codes.p, R->base_off.p, n_reads, qset.p, qtop.p);
+            PN_CHECK_LAUNCH();
+            PN_CUDA(cudaEventRecord(kev[10], s));
+            qfilter_k<<<grid_for(NC, kFilterThreads, (unsigned)sm_count() * 32), kFilterThreads, 0, s>>>(
+                R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, qtop.p, fst.p);
+            PN_CHECK_LAUNCH();
+            PN_CUDA(cudaEventRecord(kev[11], s));
+            // verification order over the narrowed ranges; removed ones last
+            order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+                R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
+            PN_CHECK_LAUNCH();
+            radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
+        }
+        PN_CUDA(cudaEventRecord(kev[2], s));
+        if (NC) {
+            verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
+            PN_CHECK_LAUNCH();
+        }
+        PN_CUDA(cudaEventRecord(kev[3], s));
+        exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
+        st.graph_segments += seg.run() ? 1 : 0;
         unsigned long long cv[3], fv[3];
+        PN_CUDA(cudaMemcpyAsync(&NT, tot.p, sizeof(NT), cudaMemcpyDeviceToHost, s));
         PN_CUDA(cudaMemcpyAsync(cv, cols.p, sizeof(cv), cudaMemcpyDeviceToHost, s));
         PN_CUDA(cudaMemcpyAsync(fv, fst.p, sizeof(fv), cudaMemcpyDeviceToHost, s));
         PN_CUDA(cudaStreamSynchronize(s));
@@ -2232,6 +2246,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         st.prefilter_columns = fv[2];
         R->n_live = fv[1];
     }
+    okey.reset();
     DeviceHits* out = new DeviceHits();
     try {
         DeviceHits all;
@@ -2240,12 +2255,14 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         V.out_strand = all.h.strand;
         V.out_end = all.h.end_pos;
         V.out_dist = all.h.dist;
+        GraphSegment seg(s, graphs && NC);
         if (NC) {
             inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
             PN_CHECK_LAUNCH();
             verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
             PN_CHECK_LAUNCH();
         }
+        st.graph_segments += seg.run() ? 1 : 0;
         tm.mark();  // 4
         // 5. best stratum
         if (mode == 1 && NT) {

@@ -57,7 +57,7 @@ class MapStats(Structure):
                 ("med_reads", c_uint64), ("big_reads", c_uint64), ("lowcx_rest_segments", c_uint64),
                 ("lowcx_serial_segments", c_uint64), ("useful_columns", c_uint64),
                 ("prefilter_columns", c_uint64), ("filter_positions", c_uint64), ("filter_live", c_uint64),
-                ("ms_filter_kernel", c_float)]
+                ("ms_filter_kernel", c_float), ("graph_segments", c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -85,7 +85,8 @@ class EngineStats(Structure):
                 ("ms_admit", ctypes.c_double), ("ms_launch", ctypes.c_double), ("ms_assemble", ctypes.c_double),
                 ("ms_download", ctypes.c_double), ("pageable_result_blocks", c_uint64),
                 ("candidate_columns", c_uint64), ("useful_columns", c_uint64),
-                ("filter_positions", c_uint64), ("ms_filter_kernel", ctypes.c_double)]
+                ("filter_positions", c_uint64), ("ms_filter_kernel", ctypes.c_double),
+                ("graph_segments", c_uint64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)

@@ -240,6 +240,9 @@ def test_engine_autotune_records(gpu, world, expected):
     for c in classes.values():
         assert c["tune_candidates"] >= 1 and c["q"] in (c["q_class"], c["q_class"] - 1)
         assert 1 <= c["stride"] <= c["q"] and c["launches"] >= 1
+    # the engine's launches run their sync-free stretches (scan, binning + windows, filter +
+    # verification count pass, write pass) as CUDA graphs: four per mapping run
+    assert st["graph_segments"] >= 3 * st["map_runs"]
 
 
 @pytest.mark.parametrize("stride", [2, 3, 4])
