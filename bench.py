@@ -90,6 +90,7 @@ def parse_args():
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
     ap.add_argument("--no-check", action="store_true", help="batched: skip the identical-output check")
     ap.add_argument("--no-serve", action="store_true", help="plain: skip the short serving leg")
+    ap.add_argument("--no-graph-arm", action="store_true", help="plain: skip the engine-with-graphs arm")
     ap.add_argument("--no-refindex", action="store_true",
                     help="plain: skip the reference-side q-group index comparison arm")
     ap.add_argument("--serve-requests", type=int, default=30, help="plain: requests of the serving leg")
@@ -764,6 +765,31 @@ def main():
     est = E.stats()
     E.free()
 
+    # the same engine with each launch's sync-free stretches run as CUDA graphs (graphs = 1)
+    engine_graphs = None
+    if not args.no_graph_arm:
+        EG = peanut.Engine(R, **kw, executors=args.executors, max_reads=B, autotune=True, graphs=True)
+
+        def step_engine_graphs():
+            tickets = [EG.submit_device(bt["d_seq"], bt["d_off"], "all", result_on_device=True) for bt in batches]
+            n = 0
+            for t in tickets:
+                h = EG.wait_device(t)
+                n += h.n
+                h.free()
+            return n
+        n_g = step_engine_graphs()  # warm-up (tunes the engine's class)
+        step_engine_graphs()
+        ms_g, n_g2, launches_g, _, _ = timed(step_engine_graphs, engine=False)
+        gst = EG.stats()
+        EG.free()
+        engine_graphs = {"value": units / (ms_g / 1e3), "ms_per_step": ms_g, "gpu_launches": int(launches_g),
+                         "graph_segments": gst["graph_segments"], "map_runs": gst["map_runs"],
+                         "results_per_step": int(n_g2), "same_result_count": int(n_g2) == int(n_eng),
+                         "note": "peanut_engine_params.graphs = 1: the scan, binning + short-read windows, filter "
+                                 "+ verification count pass and write pass of every launch captured as CUDA "
+                                 "graphs (instantiated per launch)"}
+
     # the plain path at the engine's tuned setting: isolates what batching and overlap add
     tuned = next((c for c in est["classes"] if c["q_class"] == q), None)
     plain_tuned = None
@@ -914,6 +940,7 @@ def main():
             "plain": plain, "plain_tuned": plain_tuned, "vs_plain": ms_p / ms,
             "vs_plain_tuned": plain_tuned["ms_per_step"] / ms if plain_tuned else None,
             "identical_output": identical, "serving": serving, "plain_refindex": refidx,
+            "engine_graphs": engine_graphs,
             "int_peak": {kk: {"per_s": v["ops_per_s"], "unit": v["unit"],
                               "per_sm_per_clock": (v["ops_per_s"] / (152 * clocks["sm_mhz"] * 1e6)
                                                    if clocks and clocks.get("sm_mhz") else None)}

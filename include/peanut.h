@@ -91,6 +91,13 @@ typedef struct {
                             1 = look the batch's indexed q-grams up in the reference's own q-group
                             index instead (built beforehand with peanut_index_reference at this q).
                             Same hits, same output; a comparison of the two scans */
+    uint32_t index_layout; /* storage of the batch index's I and S (Algorithm 1; the output is the
+                            same for every layout): 0 = (I, S) interleaved per group of w = 32
+                            codes, one 8-byte probe (8 B per 32 codes); 1 = I per 32 codes and S
+                            kept for every second group only, an odd group adding the population
+                            count of the even one (the sampling of S of Section "The q-group
+                            index", 6 B per 32 codes); 2 = w = 64: a 64-bit I word and S per 64
+                            codes (6 B per 32 codes) */
 } peanut_params;
 
 /* Counters of the last peanut_map() on a batch (diagnostics; all device-computed). */
@@ -223,7 +230,8 @@ peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn rele
 peanut_status peanut_index_sizes(const peanut_reads* reads, uint64_t* n_groups, uint64_t* n_distinct,
                                  uint64_t* n_indexed);
 
-/* Copies the index arrays to host buffers sized by peanut_index_sizes (any pointer may be NULL):
+/* Copies the index arrays to host buffers sized by peanut_index_sizes (any pointer may be NULL),
+ * in the w = 32 form whatever the batch's layout (S of a group not stored is recomputed from I):
  * I[n_groups] (bit j of I[i] = canonical q-gram 32 i + j occurs), S[n_groups] (exclusive
  * cumulative popcount of I), Sp[n_distinct + 1], O[n_indexed] (entries
  * (read << 9) | (orientation << 8) | offset; orientation 1 = the read holds the reverse
@@ -352,6 +360,13 @@ typedef struct {
     uint64_t hbm_budget;  /* device bytes the engine may hold (0 = 90 % of the free memory at
                              creation, less 4 GiB; give explicit budgets when several engines
                              share a device) */
+    uint32_t graphs;      /* 1 = each launch runs its sync-free stretches (the scan; binning and
+                             the windows of reads with few hits; the candidate filter and the
+                             verification count pass; the write pass) as CUDA graphs, one readback
+                             between stretches.  While such an engine has work in flight the
+                             process must not synchronize the whole device (cudaDeviceSynchronize,
+                             torch.cuda.synchronize()): a stream being captured makes that call
+                             fail.  Synchronize streams or events instead.  0 = plain launches */
 } peanut_engine_params;
 
 /* Per-class record of an engine (peanut_engine_get_stats). */

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -37,6 +38,12 @@ static void* g_ctx = nullptr;
 static thread_local bool t_pool_only = false;
 void use_pool_on_this_thread() { t_pool_only = true; }
 bool pool_on_this_thread() { return t_pool_only; }
+
+// Threads whose map calls run their sync-free stretches as CUDA graphs (engine executors whose
+// engine was created with graphs = 1; they allocate from the stream-ordered pool).
+static thread_local bool t_graphs = false;
+void use_graphs_on_this_thread(bool on) { t_graphs = on; }
+bool graphs_on_this_thread() { return t_graphs && t_pool_only; }
 
 Allocator current_allocator() {
     return t_pool_only ? Allocator{} : Allocator{g_alloc, g_release, g_ctx};
@@ -271,6 +278,7 @@ static void check_params(const peanut_params* p) {
     PN_REQUIRE(p->k_fixed != 0xFFFFFFFFu || p->k_permille <= 1000, PEANUT_INVALID_ARG, "k_permille > 1000");
     PN_REQUIRE(p->stride <= 64, PEANUT_INVALID_ARG, "stride = %u outside 0..64", p->stride);
     PN_REQUIRE(p->ref_index <= 1, PEANUT_INVALID_ARG, "ref_index = %u outside 0..1", p->ref_index);
+    PN_REQUIRE(p->index_layout <= 2, PEANUT_INVALID_ARG, "index_layout = %u outside 0..2", p->index_layout);
 }
 
 peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets, uint32_t n_reads,
@@ -302,6 +310,7 @@ peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint6
     peanut_reads* R = new peanut_reads();
     try {
         R->rindex = rindex;
+        R->layout = p->index_layout;
         R->prep = prep;
         R->ref = ref;
         R->stream = s;
@@ -477,20 +486,43 @@ peanut_status peanut_export_index(const peanut_reads* R, uint32_t* I, uint32_t* 
         PN_REQUIRE(R && R->magic == kMagicReads, PEANUT_INVALID_ARG, "bad batch");
         cudaStream_t s = R->stream;
         if (I || S) {
-            uint2* tmp = (uint2*)malloc(R->n_groups * sizeof(uint2));
-            PN_REQUIRE(tmp, PEANUT_NO_MEMORY, "host allocation failed");
-            const cudaError_t e = cudaMemcpyAsync(tmp, R->IS.p, R->n_groups * sizeof(uint2), cudaMemcpyDeviceToHost, s);
-            const cudaError_t e2 = cudaStreamSynchronize(s);
-            if (e != cudaSuccess || e2 != cudaSuccess) {
-                free(tmp);
-                set_error("copy of the index failed");
-                throw Fail{PEANUT_CUDA_ERROR};
+            // the w = 32 form: I word and S of every group of 32 codes
+            std::vector<uint32_t> wi(R->n_groups + 1), ws(R->n_groups + 1);
+            cudaError_t e = cudaSuccess;
+            if (R->layout == 0) {
+                std::vector<uint2> tmp(R->n_groups);
+                e = cudaMemcpyAsync(tmp.data(), R->IS.p, R->n_groups * sizeof(uint2), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                for (uint64_t g = 0; g < R->n_groups; ++g) {
+                    wi[g] = tmp[g].x;
+                    ws[g] = tmp[g].y;
+                }
+            } else if (R->layout == 1) {
+                const uint64_t pairs = (R->n_groups + 1) / 2;
+                std::vector<uint32_t> s2(pairs);
+                e = cudaMemcpyAsync(wi.data(), R->I32.p, R->n_groups * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(s2.data(), R->S2.p, pairs * 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                for (uint64_t g = 0; g < R->n_groups; ++g)
+                    ws[g] = s2[g >> 1] + ((g & 1) ? (uint32_t)__builtin_popcount(wi[g - 1]) : 0u);
+            } else {
+                const uint64_t g64 = (R->n_groups + 1) / 2;
+                std::vector<unsigned long long> i64(g64);
+                std::vector<uint32_t> s64(g64);
+                e = cudaMemcpyAsync(i64.data(), R->I64.p, g64 * 8, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(s64.data(), R->S64.p, g64 * 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                for (uint64_t g = 0; g < R->n_groups; ++g) {
+                    const unsigned long long w = i64[g >> 1];
+                    wi[g] = (g & 1) ? (uint32_t)(w >> 32) : (uint32_t)w;
+                    ws[g] = s64[g >> 1] + ((g & 1) ? (uint32_t)__builtin_popcount((uint32_t)w) : 0u);
+                }
             }
+            PN_REQUIRE(e == cudaSuccess, PEANUT_CUDA_ERROR, "copy of the index failed: %s", cudaGetErrorString(e));
             for (uint64_t g = 0; g < R->n_groups; ++g) {
-                if (I) I[g] = tmp[g].x;
-                if (S) S[g] = tmp[g].y;
+                if (I) I[g] = wi[g];
+                if (S) S[g] = ws[g];
             }
-            free(tmp);
         }
         if (Sp) PN_CUDA(cudaMemcpyAsync(Sp, R->Sp.p, (R->n_distinct + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         if (O && R->n_indexed)

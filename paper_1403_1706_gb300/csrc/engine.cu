@@ -662,6 +662,7 @@ static int pick_class(peanut_engine* E) {
 static void executor(peanut_engine* E, int idx) {
     cudaSetDevice(E->device);
     use_pool_on_this_thread();
+    use_graphs_on_this_thread(E->p.graphs != 0);
     cudaStream_t s = E->streams[idx];
     std::unique_lock<std::mutex> lk(E->mu);
     while (!E->stop) {

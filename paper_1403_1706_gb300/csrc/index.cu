@@ -467,6 +467,27 @@ __global__ void set_bits_k(const uint32_t* __restrict__ tcode, uint64_t n, uint2
     }
 }
 
+// GROUPBIT for the other layouts: I words of 32 codes (layout 1) or of 64 codes (layout 2).
+__global__ void set_bits_alt_k(const uint32_t* __restrict__ tcode, uint64_t n, uint32_t* I32, unsigned long long* I64) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = tcode[x];
+        if (c == kSentinel) continue;
+        if (I32) atomicOr(&I32[c >> 5], 1u << (c & 31));
+        else atomicOr(&I64[c >> 6], 1ull << (c & 63));
+    }
+}
+
+// Population counts per stored S entry: two 32-code words (layout 1) or one 64-code word (layout 2).
+struct PopcPairIn {
+    const uint32_t* I32;
+    __device__ __forceinline__ uint64_t operator()(uint64_t t) const { return __popc(I32[2 * t]) + __popc(I32[2 * t + 1]); }
+};
+struct Popc64In {
+    const unsigned long long* I64;
+    __device__ __forceinline__ uint64_t operator()(uint64_t t) const { return __popcll(I64[t]); }
+};
+
 struct PopcIn {
     const uint2* IS;
     __device__ __forceinline__ uint64_t operator()(uint64_t i) const { return __popc(IS[i].x); }
@@ -482,23 +503,30 @@ __device__ __forceinline__ uint32_t qgram_slot(const uint2* __restrict__ IS, uin
     return v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
 }
 
-__global__ void count_qgrams_k(const uint32_t* __restrict__ tcode, uint64_t n, const uint2* __restrict__ IS,
-                               uint32_t* cnt) {
+template <int L>
+__device__ __forceinline__ uint32_t view_slot(const IndexView& V, uint32_t c) {
+    const uint2 v = index_group<L>(V, c);
+    return v.y + __popc(v.x & ((1u << (c & 31)) - 1u));
+}
+
+template <int L>
+__global__ void count_qgrams_k(const uint32_t* __restrict__ tcode, uint64_t n, IndexView V, uint32_t* cnt) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t c = tcode[x];
-        if (c != kSentinel) atomicAdd(&cnt[qgram_slot(IS, c)], 1u);
+        if (c != kSentinel) atomicAdd(&cnt[view_slot<L>(V, c)], 1u);
     }
 }
 
+template <int L>
 __global__ void scatter_qgrams_k(const uint32_t* __restrict__ tcode, const uint32_t* __restrict__ tpay,
-                                 uint64_t n, const uint2* __restrict__ IS, const uint32_t* __restrict__ Sp,
-                                 uint32_t* cur, uint32_t* O) {
+                                 uint64_t n, IndexView V, const uint32_t* __restrict__ Sp, uint32_t* cur,
+                                 uint32_t* O) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t c = tcode[x];
         if (c == kSentinel) continue;
-        const uint32_t slot = qgram_slot(IS, c);
+        const uint32_t slot = view_slot<L>(V, c);
         O[Sp[slot] + atomicAdd(&cur[slot], 1u)] = tpay[x];
     }
 }
@@ -677,18 +705,41 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
         R->lowcx_list.p, nlc.p);
     PN_CHECK_LAUNCH();
 
-    // Algorithm 1 over the indexed canonical codes
+    // Algorithm 1 over the indexed canonical codes, in the batch's layout of I and S
     R->n_groups = ((1ull << (2 * q)) + 31) / 32;
-    R->IS.alloc(R->n_groups, s);
-    R->IS.zero();
     const unsigned gq = grid_for(nqg, 256, (unsigned)sm_count() * 16);
-    set_bits_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->IS.p);
-    PN_CHECK_LAUNCH();
     DBuf<uint64_t> tot2(1, s);
-    exclusive_scan(PopcIn{R->IS.p}, SOut{R->IS.p}, R->n_groups, tot2.p, s);
+    if (R->layout == 0) {
+        R->IS.alloc(R->n_groups, s);
+        R->IS.zero();
+        set_bits_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->IS.p);
+        PN_CHECK_LAUNCH();
+        exclusive_scan(PopcIn{R->IS.p}, SOut{R->IS.p}, R->n_groups, tot2.p, s);
+    } else if (R->layout == 1) {
+        const uint64_t pairs = (R->n_groups + 1) / 2;
+        R->I32.alloc(2 * pairs, s);
+        R->I32.zero();
+        R->S2.alloc(pairs, s);
+        set_bits_alt_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->I32.p, nullptr);
+        PN_CHECK_LAUNCH();
+        exclusive_scan(PopcPairIn{R->I32.p}, ArrayOut<uint32_t>{R->S2.p}, pairs, tot2.p, s);
+    } else {
+        const uint64_t g64 = ((1ull << (2 * q)) + 63) / 64;
+        R->I64.alloc(g64, s);
+        R->I64.zero();
+        R->S64.alloc(g64, s);
+        set_bits_alt_k<<<gq, 256, 0, s>>>(tcode.p, nqg, nullptr, R->I64.p);
+        PN_CHECK_LAUNCH();
+        exclusive_scan(Popc64In{R->I64.p}, ArrayOut<uint32_t>{R->S64.p}, g64, tot2.p, s);
+    }
+    const IndexView IV = index_view(R);
     DBuf<uint32_t> cnt(nqg + 1, s);
     cnt.zero();
-    count_qgrams_k<<<gq, 256, 0, s>>>(tcode.p, nqg, R->IS.p, cnt.p);
+    switch (R->layout) {
+        case 0: count_qgrams_k<0><<<gq, 256, 0, s>>>(tcode.p, nqg, IV, cnt.p); break;
+        case 1: count_qgrams_k<1><<<gq, 256, 0, s>>>(tcode.p, nqg, IV, cnt.p); break;
+        default: count_qgrams_k<2><<<gq, 256, 0, s>>>(tcode.p, nqg, IV, cnt.p); break;
+    }
     PN_CHECK_LAUNCH();
     R->Sp.alloc(nqg + 1, s);
     exclusive_scan(ArrayIn<uint32_t>{cnt.p}, ArrayOut<uint32_t>{R->Sp.p}, nqg + 1, tot.p, s);
@@ -700,7 +751,11 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     R->n_distinct = sizes[0];
     R->n_indexed = sizes[1];
     R->O.alloc(R->n_indexed ? R->n_indexed : 1, s);
-    scatter_qgrams_k<<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, R->IS.p, R->Sp.p, cnt.p, R->O.p);
+    switch (R->layout) {
+        case 0: scatter_qgrams_k<0><<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, IV, R->Sp.p, cnt.p, R->O.p); break;
+        case 1: scatter_qgrams_k<1><<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, IV, R->Sp.p, cnt.p, R->O.p); break;
+        default: scatter_qgrams_k<2><<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, IV, R->Sp.p, cnt.p, R->O.p); break;
+    }
     PN_CHECK_LAUNCH();
     // prefilter for the reference scan: about 6 bits per distinct code, at most 64 MB so that it
     // stays resident in the 129 MB L2 while the index itself is probed in HBM

@@ -79,10 +79,21 @@ struct Allocator {
 Allocator current_allocator();
 void use_pool_on_this_thread();  // this thread allocates from the stream-ordered pool
 bool pool_on_this_thread();
+void use_graphs_on_this_thread(bool on);
+bool graphs_on_this_thread();
+
+// Records ev on s; inside a stream capture as an event-record node of the graph (a plain record
+// there only orders the capture), so that the event is recorded when the graph runs.
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    return cudaEventRecord(ev, s);
+}
 
 // A sync-free stretch of work on stream s captured as a CUDA graph and launched once (when
-// enabled: the thread allocates from the stream-ordered pool, whose allocations and frees become
-// graph memory nodes).  run() ends the capture and launches the graph; the graph is released when
+// enabled: an engine created with graphs = 1, whose threads allocate from the stream-ordered
+// pool; its allocations and frees become graph memory nodes).  run() ends the capture and launches the graph; the graph is released when
 // the segment is destroyed (after the caller's next synchronization).  An exception inside the
 // captured stretch ends the capture and discards it.
 struct GraphSegment {
@@ -115,6 +126,7 @@ struct GraphSegment {
         }
         if (x) cudaGraphExecDestroy(x);
         if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
     }
 };
 void* dalloc(size_t bytes, cudaStream_t s, Allocator* used = nullptr);  // throws Fail{NO_MEMORY}
@@ -190,6 +202,16 @@ struct RefPrep {
     }
 };
 
+// ---- the batch's q-group index as the device sees it (one of three layouts) ---------------
+struct IndexView {
+    uint32_t layout;
+    const uint2* IS;
+    const uint32_t* I32;
+    const uint32_t* S2;
+    const unsigned long long* I64;
+    const uint32_t* S64;
+};
+
 // ---- the reference's own q-group index (Algorithm 1 over the reference's q-grams) -----------
 struct RefIndex {
     uint32_t q = 0;
@@ -232,7 +254,12 @@ struct peanut_reads {
     pn::DBuf<uint64_t> peq;       // [n][2 strands][4 bases][kMaxWords] match bit masks
     // q-group index
     uint64_t n_groups = 0, n_distinct = 0, n_indexed = 0, n_qgrams = 0;
-    pn::DBuf<uint2> IS;           // (I word, S) per group of 32 canonical codes
+    uint32_t layout = 0;          // 0: (I, S) interleaved per group of 32 codes; 1: I per 32 codes,
+                                  // S sampled at every second group; 2: I per 64 codes (w = 64)
+    pn::DBuf<uint2> IS;           // layout 0: (I word, S) per group of 32 canonical codes
+    pn::DBuf<uint32_t> I32, S2;   // layout 1: I per group of 32; S of the even groups
+    pn::DBuf<unsigned long long> I64;  // layout 2: I per group of 64
+    pn::DBuf<uint32_t> S64;       // layout 2: S per group of 64
     pn::DBuf<uint32_t> Sp;        // n_qgrams + 1 (first n_distinct + 1 meaningful)
     pn::DBuf<uint32_t> O;         // n_indexed entries (read << 9 | orientation << 8 | offset)
     pn::DBuf<uint64_t> bloom;     // blocked Bloom filter of the indexed canonical codes (L2-sized)
@@ -286,6 +313,9 @@ void destroy_engine(peanut_engine* E);
 // api.cu: a new batch indexed from reads in device memory (throws Fail on error)
 peanut_reads* index_batch(const peanut_ref* ref, const char* d_seqs, const uint64_t* d_offsets, uint32_t n_reads,
                           uint64_t total, const peanut_params* p);
+inline IndexView index_view(const peanut_reads* R) {
+    return IndexView{R->layout, R->IS.p, R->I32.p, R->S2.p, R->I64.p, R->S64.p};
+}
 // map.cu
 DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode);
 // keeps, per read, the results at the read's smallest distance over both strands (in: sorted)

@@ -96,8 +96,9 @@ __device__ __forceinline__ void stage_flush2(uint64_t* sk, uint32_t* ss, uint32_
     __syncwarp();
 }
 
+template <int L>
 __global__ void __launch_bounds__(kScanBlock, 4)
-    probe_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, const uint2* __restrict__ IS,
+    probe_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, IndexView V,
                 const uint64_t* __restrict__ bloom, uint64_t bloom_mask, uint64_t* __restrict__ okey,
                 uint32_t* __restrict__ oslot, uint64_t cap, unsigned long long* n_out) {
     __shared__ uint64_t sk[kScanBlock / 32][kStageCap];
@@ -143,7 +144,11 @@ __global__ void __launch_bounds__(kScanBlock, 4)
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const bool pass = (meta[u] & 1u) && (fw[u] & fb[u]) == fb[u];
-                vv[u] = pass ? ld_u32x2_policy(IS + (cc[u] >> 5), stream) : make_uint2(0, 0);
+                if constexpr (L == 0) {
+                    vv[u] = pass ? ld_u32x2_policy(V.IS + (cc[u] >> 5), stream) : make_uint2(0, 0);
+                } else {
+                    vv[u] = pass ? index_group<L>(V, cc[u]) : make_uint2(0, 0);
+                }
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -1928,6 +1933,17 @@ void best_stratum(const peanut_device_hits& in, uint32_t n_reads, DeviceHits* ou
     PN_CHECK_LAUNCH();
 }
 
+// Milliseconds between two recorded events (0, and no error left behind, if either was not
+// recorded).
+static float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        t = 0;
+    }
+    return t;
+}
+
 struct Timer {
     cudaEvent_t ev[12];
     int n = 0;
@@ -1938,13 +1954,9 @@ struct Timer {
     ~Timer() {
         for (auto& e : ev) cudaEventDestroy(e);
     }
-    void mark() { PN_CUDA(cudaEventRecord(ev[n++], s)); }
-    void mark_at(int i) { PN_CUDA(cudaEventRecord(ev[i], s)); }
-    float ms(int a, int b) {
-        float t = 0;
-        cudaEventElapsedTime(&t, ev[a], ev[b]);
-        return t;
-    }
+    void mark() { PN_CUDA(record_event(ev[n++], s)); }
+    void mark_at(int i) { PN_CUDA(record_event(ev[i], s)); }
+    float ms(int a, int b) { return elapsed(ev[a], ev[b]); }
 };
 
 static void alloc_hits(DeviceHits* H, uint64_t n, cudaStream_t s) {
@@ -1987,12 +1999,12 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     uint64_t pcap = (uint64_t)(1.5 * rand_present) + 2 * R->n_indexed + (1u << 20);
     uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
     int per_sm = 0;
-    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k, kScanBlock, 0));
+    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k<0>, kScanBlock, 0));
     const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
     const unsigned gexp = (unsigned)sm_count() * 8;  // persistent: the count of present positions is on the device
-    // Sync-free stretches run as CUDA graphs on threads that allocate from the stream-ordered pool
-    // (an engine's executors); elsewhere the same launches run one by one.
-    const bool graphs = pool_on_this_thread();
+    // Sync-free stretches run as CUDA graphs on the executors of an engine created with graphs = 1;
+    // elsewhere the same launches run one by one.
+    const bool graphs = graphs_on_this_thread();
     DBuf<uint64_t> pkey;
     DBuf<uint32_t> pslot;
     DBuf<uint64_t> hits;
@@ -2007,15 +2019,22 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         }
         hits.alloc(cap, s);
         GraphSegment seg(s, graphs);
-        PN_CUDA(cudaEventRecord(kev[0], s));
+        PN_CUDA(record_event(kev[0], s));
         nh.zero();
         rcount.zero();
         if (!RX) {
-            probe_ref_k<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, R->IS.p, R->bloom.p, R->bloom_mask, pkey.p,
-                                                     pslot.p, pcap, nh.p);
+            const IndexView IV = index_view(R);
+            switch (R->layout) {
+                case 0: probe_ref_k<0><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
+                                                                     pkey.p, pslot.p, pcap, nh.p); break;
+                case 1: probe_ref_k<1><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
+                                                                     pkey.p, pslot.p, pcap, nh.p); break;
+                default: probe_ref_k<2><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
+                                                                      pkey.p, pslot.p, pcap, nh.p); break;
+            }
             PN_CHECK_LAUNCH();
         }
-        PN_CUDA(cudaEventRecord(kev[7], s));
+        PN_CUDA(record_event(kev[7], s));
         if (RX) {
             refprobe_k<<<grid_for(R->n_indexed, kScanBlock, (unsigned)sm_count() * 8), kScanBlock, 0, s>>>(
                 R->O.p, R->n_indexed, q, R->codes.p, R->base_off.p, R->len.p, RX->IS.p, RX->Sp.p, RX->O.p,
@@ -2025,7 +2044,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
                                                   cap, nh.p + 1, rcount.p);
         }
         PN_CHECK_LAUNCH();
-        PN_CUDA(cudaEventRecord(kev[1], s));
+        PN_CUDA(record_event(kev[1], s));
         st.graph_segments += seg.run() ? 1 : 0;
         unsigned long long c[2];
         PN_CUDA(cudaMemcpyAsync(c, nh.p, sizeof(c), cudaMemcpyDeviceToHost, s));
@@ -2073,7 +2092,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     const uint32_t n_big = nbm[0], n_med = nbm[1];
     st.med_reads = n_med;
     st.big_reads = n_big;
-    PN_CUDA(cudaEventRecord(kev[8], s));
+    PN_CUDA(record_event(kev[8], s));
     if (n_med) {
         // opt in to the block path's shared memory (a per-device function attribute; cheap to repeat)
         PN_CUDA(cudaFuncSetAttribute(windows_med_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMedSmem));
@@ -2083,7 +2102,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
             binned.p, med_list.p, n_med, WP, nbig.p + 2, sbit);
         PN_CHECK_LAUNCH();
     }
-    PN_CUDA(cudaEventRecord(kev[9], s));
+    PN_CUDA(record_event(kev[9], s));
     if (n_big) {
         DBuf<uint64_t> goff((uint64_t)n_big + 1, s);
         exclusive_scan(BigSize{big_list.p, roff.p}, ArrayOut<uint64_t>{goff.p}, n_big, tot.p, s);
@@ -2201,8 +2220,8 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         vcnt.zero();  // ranges the filter removes report no tuples
         cols.zero();
         fst.zero();
-        PN_CUDA(cudaEventRecord(kev[10], s));
-        PN_CUDA(cudaEventRecord(kev[11], s));
+        PN_CUDA(record_event(kev[10], s));
+        PN_CUDA(record_event(kev[11], s));
         if (NC) {
             DBuf<uint64_t> t1(NC, s), t2(NC, s);
             order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
@@ -2214,23 +2233,23 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
             qset_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
                 R->codes.p, R->base_off.p, n_reads, qset.p, qtop.p);
             PN_CHECK_LAUNCH();
-            PN_CUDA(cudaEventRecord(kev[10], s));
+            PN_CUDA(record_event(kev[10], s));
             qfilter_k<<<grid_for(NC, kFilterThreads, (unsigned)sm_count() * 32), kFilterThreads, 0, s>>>(
                 R->cand_key.p, R->cand_hi.p, order.p, NC, ref->packed.p, R->len.p, R->kk.p, qset.p, qtop.p, fst.p);
             PN_CHECK_LAUNCH();
-            PN_CUDA(cudaEventRecord(kev[11], s));
+            PN_CUDA(record_event(kev[11], s));
             // verification order over the narrowed ranges; removed ones last
             order_key_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
                 R->cand_key.p, R->cand_hi.p, NC, R->len.p, R->kk.p, okey.p, order.p);
             PN_CHECK_LAUNCH();
             radix_sort_pairs(okey.p, order.p, t1.p, t2.p, NC, kOrderBits, s);
         }
-        PN_CUDA(cudaEventRecord(kev[2], s));
+        PN_CUDA(record_event(kev[2], s));
         if (NC) {
             verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
             PN_CHECK_LAUNCH();
         }
-        PN_CUDA(cudaEventRecord(kev[3], s));
+        PN_CUDA(record_event(kev[3], s));
         exclusive_scan(ArrayIn<uint32_t>{vcnt.p}, ArrayOut<uint64_t>{toff.p}, NC, tot.p, s);
         st.graph_segments += seg.run() ? 1 : 0;
         unsigned long long cv[3], fv[3];
@@ -2287,15 +2306,15 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     st.ms_windows = tm.ms(2, 3);
     st.ms_verify = tm.ms(3, 4);
     st.ms_output = tm.ms(4, 5);
-    cudaEventElapsedTime(&st.ms_scan_kernel, kev[0], kev[1]);
-    cudaEventElapsedTime(&st.ms_verify_kernel, kev[2], kev[3]);
-    cudaEventElapsedTime(&st.ms_probe_kernel, kev[0], kev[7]);
-    cudaEventElapsedTime(&st.ms_windows_med, kev[8], kev[9]);
-    cudaEventElapsedTime(&st.ms_windows_big, kev[9], kev[4]);
-    cudaEventElapsedTime(&st.ms_windows_sweep, tm.ev[2], kev[4]);
-    cudaEventElapsedTime(&st.ms_lowcx, kev[4], kev[5]);
-    cudaEventElapsedTime(&st.ms_compact, kev[5], kev[6]);
-    cudaEventElapsedTime(&st.ms_filter_kernel, kev[10], kev[11]);
+    st.ms_scan_kernel = elapsed(kev[0], kev[1]);
+    st.ms_verify_kernel = elapsed(kev[2], kev[3]);
+    st.ms_probe_kernel = elapsed(kev[0], kev[7]);
+    st.ms_windows_med = elapsed(kev[8], kev[9]);
+    st.ms_windows_big = elapsed(kev[9], kev[4]);
+    st.ms_windows_sweep = elapsed(tm.ev[2], kev[4]);
+    st.ms_lowcx = elapsed(kev[4], kev[5]);
+    st.ms_compact = elapsed(kev[5], kev[6]);
+    st.ms_filter_kernel = elapsed(kev[10], kev[11]);
     R->stats = st;
     return out;
 }

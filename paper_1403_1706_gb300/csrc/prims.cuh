@@ -223,6 +223,26 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return (1u << (threadIdx.x & 31)) - 1u;
 }
 
+// The 32-code group of canonical code c as (I word, S: the number of distinct codes before the
+// group) for any layout of the batch's q-group index: interleaved; I per 32 codes with S kept for
+// the even groups only (an odd group adds the population count of the even one before it, the
+// sampling of S of Section "The q-group index"); or I per 64 codes (w = 64) with S per 64 codes.
+template <int L>
+__device__ __forceinline__ uint2 index_group(const IndexView& V, uint32_t c) {
+    if constexpr (L == 0) {
+        return V.IS[c >> 5];
+    } else if constexpr (L == 1) {
+        const uint32_t g = c >> 5;
+        const uint2 pair = *reinterpret_cast<const uint2*>(V.I32 + (g & ~1u));
+        const uint32_t base = V.S2[g >> 1];
+        return (g & 1u) ? make_uint2(pair.y, base + __popc(pair.x)) : make_uint2(pair.x, base);
+    } else {
+        const unsigned long long w = V.I64[c >> 6];
+        const uint32_t base = V.S64[c >> 6];
+        return (c & 32u) ? make_uint2((uint32_t)(w >> 32), base + __popc((uint32_t)w)) : make_uint2((uint32_t)w, base);
+    }
+}
+
 // 2-bit base code at position p of the packed reference (first base most significant).
 __device__ __forceinline__ uint32_t ref_base(const uint32_t* packed, uint64_t p) {
     return (packed[p >> 4] >> (30 - 2 * (uint32_t)(p & 15))) & 3u;

@@ -32,7 +32,7 @@ class PeanutError(RuntimeError):
 
 class Params(Structure):
     _fields_ = [("q", c_uint32), ("k_fixed", c_uint32), ("k_permille", c_uint32), ("freq_cap", c_uint32),
-                ("stride", c_uint32), ("stream", c_void_p), ("ref_index", c_uint32)]
+                ("stride", c_uint32), ("stream", c_void_p), ("ref_index", c_uint32), ("index_layout", c_uint32)]
 
 
 class Hits(Structure):
@@ -65,7 +65,7 @@ class MapStats(Structure):
 
 class EngineParams(Structure):
     _fields_ = [("k_fixed", c_uint32), ("k_permille", c_uint32), ("executors", c_uint32), ("max_reads", c_uint32),
-                ("autotune", c_uint32), ("fixed_q", c_uint32), ("hbm_budget", c_uint64)]
+                ("autotune", c_uint32), ("fixed_q", c_uint32), ("hbm_budget", c_uint64), ("graphs", c_uint32)]
 
 
 class EngineClass(Structure):
@@ -240,12 +240,15 @@ def pack_reference(seq, stream=None) -> Reference:
     return Reference(out.value)
 
 
+INDEX_LAYOUTS = {"interleaved": 0, "sampled_s": 1, "w64": 2}
+
+
 def make_params(q: int, k=None, k_permille=None, freq_cap: int = 0, stream=None, stride: int = 1,
-                ref_index: bool = False) -> Params:
+                ref_index: bool = False, layout: str = "interleaved") -> Params:
     if k is None and k_permille is None:
         raise ValueError("give k or k_permille")
     return Params(q, K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(freq_cap),
-                  int(stride), _stream_ptr(stream), 1 if ref_index else 0)
+                  int(stride), _stream_ptr(stream), 1 if ref_index else 0, INDEX_LAYOUTS[layout])
 
 
 def index_reference(ref: "Reference", q: int, stream=None) -> None:
@@ -254,11 +257,11 @@ def index_reference(ref: "Reference", q: int, stream=None) -> None:
 
 
 def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                stream=None, stride: int = 1, ref_index: bool = False) -> ReadBatch:
+                stream=None, stride: int = 1, ref_index: bool = False, layout: str = "interleaved") -> ReadBatch:
     """peanut_index_reads: host reads (concatenated ASCII + n+1 offsets) -> indexed batch."""
     s = _host_u8(seq)
     o = np.ascontiguousarray(offsets, dtype=np.uint64)
-    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index, layout)
     out = c_void_p()
     _check(load().peanut_index_reads(ref.ptr, s.ctypes.data, o.ctypes.data, o.size - 1, ctypes.byref(p),
                                      ctypes.byref(out)))
@@ -266,9 +269,10 @@ def index_reads(ref: Reference, seq, offsets, q: int, k=None, k_permille=None, f
 
 
 def index_reads_device(ref: Reference, d_seq, d_offsets, q: int, k=None, k_permille=None, freq_cap: int = 0,
-                       stream=None, stride: int = 1, ref_index: bool = False) -> ReadBatch:
+                       stream=None, stride: int = 1, ref_index: bool = False,
+                       layout: str = "interleaved") -> ReadBatch:
     """peanut_index_reads_device: reads already in device memory (torch uint8 / int64 tensors)."""
-    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index)
+    p = make_params(q, k, k_permille, freq_cap, stream, stride, ref_index, layout)
     out = c_void_p()
     n = int(d_offsets.numel()) - 1
     _check(load().peanut_index_reads_device(ref.ptr, d_seq.data_ptr(), d_offsets.data_ptr(), n,
@@ -472,11 +476,11 @@ class Engine(_Handle):
     submit() are kept referenced here until their result is taken with wait()."""
 
     def __init__(self, ref: Reference, k=None, k_permille=None, executors: int = 2, max_reads: int = 0,
-                 autotune: bool = True, fixed_q: int = 0, hbm_budget: int = 0):
+                 autotune: bool = True, fixed_q: int = 0, hbm_budget: int = 0, graphs: bool = False):
         if k is None and k_permille is None:
             raise ValueError("give k or k_permille")
         p = EngineParams(K_FROM_PERMILLE if k is None else int(k), int(k_permille or 0), int(executors),
-                         int(max_reads), int(bool(autotune)), int(fixed_q), int(hbm_budget))
+                         int(max_reads), int(bool(autotune)), int(fixed_q), int(hbm_budget), int(bool(graphs)))
         out = c_void_p()
         _check(load().peanut_engine_create(ref.ptr, ctypes.byref(p), ctypes.byref(out)))
         super().__init__(out.value)

@@ -240,9 +240,20 @@ def test_engine_autotune_records(gpu, world, expected):
     for c in classes.values():
         assert c["tune_candidates"] >= 1 and c["q"] in (c["q_class"], c["q_class"] - 1)
         assert 1 <= c["stride"] <= c["q"] and c["launches"] >= 1
-    # the engine's launches run their sync-free stretches (scan, binning + windows, filter +
-    # verification count pass, write pass) as CUDA graphs: four per mapping run
-    assert st["graph_segments"] >= 3 * st["map_runs"]
+    assert st["graph_segments"] == 0  # plain launches unless the engine asks for graphs
+
+
+@pytest.mark.parametrize("executors", [1, 2])
+def test_engine_graphs_equal_oracle(gpu, world, expected, executors):
+    """An engine created with graphs = 1 runs each launch's sync-free stretches (the scan, binning
+    and short-read windows, the filter and verification count pass, the write pass) as CUDA
+    graphs; every submission's hits still equal the oracle's, in both modes, with autotuning."""
+    ref, R, subs = world
+    modes = ["all", "best"] * 3
+    res, st = run_engine(gpu, R, subs, modes[:len(subs)], executors=executors, autotune=True, graphs=True)
+    for i, (got, m) in enumerate(zip(res, modes)):
+        assert np.array_equal(got, expected[i, m]), (i, m)
+    assert st["graph_segments"] >= 3 * st["map_runs"] > 0
 
 
 @pytest.mark.parametrize("stride", [2, 3, 4])

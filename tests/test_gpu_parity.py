@@ -93,12 +93,13 @@ def _expected_index(seq, offs, q, ref=None, cap=None):
     return oracle.qgroup_build(codes, pay, q, 32)
 
 
+@pytest.mark.parametrize("layout", ["interleaved", "sampled_s", "w64"])
 @pytest.mark.parametrize("q", [4, 7, 11])
-def test_index_equals_algorithm1(gpu, q):
+def test_index_equals_algorithm1(gpu, q, layout):
     ref = synth.make_reference(50_000, 21)
     reads = synth.make_reads(ref, 300, 5, lengths=(60, 90, 120), rate_range=(0.0, 0.03))
     R = gpu.pack_reference(ref)
-    B = gpu.index_reads(R, reads.seq, reads.offsets, q, k=1, freq_cap=1 << 30)
+    B = gpu.index_reads(R, reads.seq, reads.offsets, q, k=1, freq_cap=1 << 30, layout=layout)
     I, S, Sp, O = gpu.export_index(B)
     eI, eS, eSp, eO, d = _expected_index(reads.seq, reads.offsets, q)
     assert I.tolist() == eI.tolist()
@@ -385,3 +386,15 @@ def test_host_array_views_equal_structured_result(gpu):
         assert np.array_equal(h.read, want["read"]) and np.array_equal(h.strand, want["strand"])
         assert np.array_equal(h.end.astype(np.int64), want["end"]) and np.array_equal(h.dist, want["dist"])
         h.free()
+
+
+@pytest.mark.parametrize("layout", ["sampled_s", "w64"])
+def test_index_layouts_map_identically(gpu, layout):
+    """The sampled-S and w = 64 layouts of the batch index (Section "The q-group index") give the
+    oracle's hit set, at q = 16 with frequent q-grams and at q = 11, every q-gram and sampled."""
+    ref, reads, w = synth.make_workload("repeat_100mbp_1m", ref_len=2_000_000, n_reads=2000)
+    R = gpu.pack_reference(ref)
+    for q, stride in ((16, 1), (16, 4), (11, 1)):
+        want = oracle.map_filter(ref, reads.seq, reads.offsets, 5, q)
+        B = gpu.index_reads(R, reads.seq, reads.offsets, q, k=5, stride=stride, layout=layout)
+        assert_same_hits(gpu.map(R, B), want)
