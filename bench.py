@@ -81,10 +81,11 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slice", type=int, default=100_000_000,
                     help="reference prefix (bp) of the CPU-baseline sample")
-    ap.add_argument("--mode", choices=["plain", "batched", "serve"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batched", "serve", "qstudy"], default="plain",
                     help="plain: one batch per launch sequence (the headline); batched: uneven batches of "
                          "50-250 bp reads through the engine vs the plain path; serve: a Poisson request "
-                         "stream through the engine vs one request at a time")
+                         "stream through the engine vs one request at a time; qstudy: index variants and the "
+                         "q / L2-residency trade-off on one batch")
     ap.add_argument("--requests", type=int, default=None, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=None, help="serve: mean arrivals per second")
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
@@ -449,6 +450,72 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+def run_qstudy(args, rank, world, local):
+    """The index variants and the q / L2-residency trade-off on one 2^20-read batch of the 3.1 Gbp
+    workload (100 bp, k = 5): for each q, sampling stride and layout of the batch index, the plain
+    path's index and map times, its stage times and the index size.  At q <= 14 the (I, S) table
+    (4^q / 4 bytes) fits the 129 MB L2; every lower q multiplies the random q-gram hits by 4.  Every
+    setting must give the same hits (checked against the first)."""
+    import torch
+    import synth
+    from paper_1403_1706_gb300 import peanut
+    torch.cuda.set_device(local)
+    peanut.load()
+    w = synth.WORKLOADS["human_3g1_10m"]
+    n_ref = args.ref_len or w["ref_len"]
+    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
+    seed = 1706 + list(synth.WORKLOADS).index("human_3g1_10m")
+    reads = synth.make_reads(ref, args.reads or (1 << 20), seed, lengths=w["lengths"], rate_range=w["rate_range"],
+                             random_frac=w["random_frac"])
+    stream = torch.cuda.current_stream()
+    R = peanut.pack_reference(ref, stream=stream)
+    d_seq = torch.from_numpy(reads.seq).to("cuda")
+    d_off = torch.from_numpy(reads.offsets.astype(np.int64)).to("cuda")
+    configs = [(16, 1, "interleaved"), (16, 1, "sampled_s"), (16, 1, "w64"), (16, 16, "interleaved"),
+               (16, 16, "sampled_s"), (16, 16, "w64"), (16, 4, "interleaved"), (15, 1, "interleaved"),
+               (15, 3, "interleaved"), (15, 15, "interleaved"), (14, 4, "interleaved"), (14, 14, "interleaved"),
+               (13, 13, "interleaved")]
+    rows, ref_hits = [], None
+    for q, stride, layout in configs:
+        def once():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B = peanut.index_reads_device(R, d_seq, d_off, q, k=5, stride=stride, layout=layout, stream=stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            H = peanut.map_device(R, B)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            st = peanut.get_map_stats(B)
+            h = H.to_numpy()
+            H.free()
+            B.free()
+            return t1 - t0, t2 - t1, st, h
+        once()  # warm-up (builds the reference's frequent-q-gram table for this q)
+        ti, tm, st, h = once()
+        if ref_hits is None:
+            ref_hits = h
+        groups = (1 << (2 * q)) // 32
+        rows.append({"q": q, "stride": stride, "layout": layout,
+                     "index_table_bytes": groups * (8 if layout == "interleaved" else 6),
+                     "index_ms": 1e3 * ti, "map_ms": 1e3 * tm, "ms_probe_kernel": st["ms_probe_kernel"],
+                     "ms_scan_kernel": st["ms_scan_kernel"], "ms_windows": st["ms_windows"],
+                     "ms_filter_kernel": st["ms_filter_kernel"], "ms_verify_kernel": st["ms_verify_kernel"],
+                     "hits": st["hits"], "present_probes": st["present_probes"], "candidates": st["candidates"],
+                     "results": st["results"], "identical": bool(np.array_equal(h, ref_hits))})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    if rank == 0:
+        best = min(rows, key=lambda r: r["index_ms"] + r["map_ms"])
+        line = {"metric": METRIC, "mode": "qstudy", "value": reads.n / ((best["index_ms"] + best["map_ms"]) / 1e3),
+                "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "human_3g1_10m (one batch)", "reference_bp": int(n_ref), "reads": int(reads.n),
+                           "k": 5, "l2_bytes": 129 << 20},
+                "study": rows, "identical_output": all(r["identical"] for r in rows)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def serve_stream(peanut, R, ref, n_req, rate, seed, executors, warmup, clock_gpu=None, log=None):
     """A Poisson request stream (sizes log-uniform in 10^3..10^6 reads, lengths 75-250 bp, 1-4 %
     errors, k = ceil(0.05 L), half the requests in best-stratum mode) on a resident reference.
@@ -602,6 +669,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "batched":
         rc = run_batched(args, rank, world, local)
+    elif args.mode == "qstudy":
+        rc = run_qstudy(args, rank, world, local)
     elif args.mode == "serve":
         rc = run_serve(args, rank, world, local)
     else:
