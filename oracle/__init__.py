@@ -47,11 +47,19 @@ def _load():
         vp = c.c_void_p
         lib.oracle_semiglobal_column.restype = c.c_int
         lib.oracle_semiglobal_column.argtypes = [vp, c.c_int64, vp, c.c_int64, vp]
-        for f in (lib.oracle_map_bruteforce,):
-            f.restype = vp
-            f.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int]
+        lib.oracle_map_bruteforce.restype = vp
+        lib.oracle_map_bruteforce.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int, vp, c.c_int64]
         lib.oracle_map_filter.restype = vp
-        lib.oracle_map_filter.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int, c.c_int]
+        lib.oracle_map_filter.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, c.c_int, c.c_int, vp, c.c_int64]
+        lib.oracle_splitmix64.restype = c.c_uint64
+        lib.oracle_splitmix64.argtypes = [c.c_uint64, c.c_uint64]
+        lib.oracle_fnv1a64.restype = c.c_uint64
+        lib.oracle_fnv1a64.argtypes = [vp, c.c_int64]
+        lib.oracle_prepare_reference.restype = c.c_int64
+        lib.oracle_prepare_reference.argtypes = [vp, c.c_int64, vp, c.c_int64, c.c_int64, c.c_uint64, vp, vp,
+                                                 c.c_int64]
+        lib.oracle_prepare_reads.restype = c.c_int
+        lib.oracle_prepare_reads.argtypes = [vp, vp, c.c_int64, c.c_uint64, vp]
         lib.oracle_hits_count.restype = c.c_int64
         lib.oracle_hits_count.argtypes = [vp]
         lib.oracle_hits_copy.argtypes = [vp, vp, vp, vp, vp]
@@ -64,7 +72,8 @@ def _load():
         lib.oracle_frequent_qgrams.restype = c.c_int64
         lib.oracle_frequent_qgrams.argtypes = [vp, c.c_int64, c.c_int, c.c_int64, vp, vp, c.c_int64]
         lib.oracle_annotate.restype = c.c_int
-        lib.oracle_annotate.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, vp, vp, vp, c.c_int64, vp, vp, vp]
+        lib.oracle_annotate.argtypes = [vp, c.c_int64, vp, vp, c.c_int64, vp, vp, vp, vp, c.c_int64, vp, vp, vp,
+                                        vp, c.c_int64]
         _lib = lib
     return _lib
 
@@ -124,27 +133,78 @@ def _kvec(k, n):
     return np.ascontiguousarray(k)
 
 
-def map_bruteforce(ref, seq, offsets, k, mode: str = "all") -> np.ndarray:
-    """Hit set by the definition: full semiglobal DP of every read and strand over `ref`."""
+def _segs(segments):
+    """Segments as a contiguous int64 (start, end) array and their count; None = the whole text."""
+    if segments is None:
+        return None, 0
+    sg = np.ascontiguousarray(np.asarray(segments, dtype=np.int64).reshape(-1, 2))
+    return sg, sg.shape[0]
+
+
+def map_bruteforce(ref, seq, offsets, k, mode: str = "all", segments=None) -> np.ndarray:
+    """Hit set by the definition: full semiglobal DP of every read and strand over `ref` (over each
+    segment separately, the matrix restarting at its start, when `segments` is given)."""
     R = _bytes(ref)
     S, offs = _reads_args(seq, offsets)
     n = offs.size - 1
     kv = _kvec(k, n)
+    sg, ns = _segs(segments)
     return _collect(_load().oracle_map_bruteforce(_p(R), len(R), _p(S), offs.ctypes.data, n, kv.ctypes.data,
-                                                  MODES[mode]))
+                                                  MODES[mode], sg.ctypes.data if ns else None, ns))
 
 
-def map_filter(ref, seq, offsets, k, q: int, mode: str = "all") -> np.ndarray:
+def map_filter(ref, seq, offsets, k, q: int, mode: str = "all", segments=None) -> np.ndarray:
     """Hit set by the q-gram filter + windowed DP (equal to map_bruteforce when every t >= 1)."""
     R = _bytes(ref)
     S, offs = _reads_args(seq, offsets)
     n = offs.size - 1
     kv = _kvec(k, n)
+    sg, ns = _segs(segments)
     return _collect(_load().oracle_map_filter(_p(R), len(R), _p(S), offs.ctypes.data, n, kv.ctypes.data,
-                                              int(q), MODES[mode]))
+                                              int(q), MODES[mode], sg.ctypes.data if ns else None, ns))
 
 
-def annotate(ref, seq, offsets, hits: np.ndarray):
+def splitmix64(seed: int, i: int) -> int:
+    """Output number i (i >= 1) of SplitMix64 seeded with `seed`."""
+    return int(_load().oracle_splitmix64(seed & (2 ** 64 - 1), i))
+
+
+def fnv1a64(data) -> int:
+    """FNV-1a 64 of a byte string."""
+    b = _bytes(data)
+    return int(_load().oracle_fnv1a64(_p(b), b.size))
+
+
+def prepare_reference(seq, contig_starts=(0,), gap_min: int = 16, seed: int = 0):
+    """(text, segments): the reference with every N replaced by its seeded base, and its
+    segments as an (s, 2) int64 array of [start, end) (contigs cut at runs of >= gap_min Ns)."""
+    R = _bytes(seq)
+    cs = np.ascontiguousarray(np.asarray(contig_starts, dtype=np.int64))
+    text = np.empty(max(R.size, 1), np.uint8)
+    cap = 16
+    while True:
+        sg = np.empty((cap, 2), np.int64)
+        ns = _load().oracle_prepare_reference(_p(R), R.size, _p(cs), cs.size, gap_min, seed & (2 ** 64 - 1),
+                                              text.ctypes.data, sg.ctypes.data, cap)
+        if ns == -2:
+            cap *= 4
+            continue
+        if ns < 0:
+            raise ValueError("bad reference byte or contig list")
+        return text[:R.size], sg[:ns].copy()
+
+
+def prepare_reads(seq, offsets, seed: int = 0) -> np.ndarray:
+    """The reads upper-cased with every N replaced by its seeded base."""
+    S, offs = _reads_args(seq, offsets)
+    out = np.empty(max(S.size, 1), np.uint8)
+    if _load().oracle_prepare_reads(_p(S), offs.ctypes.data, offs.size - 1, seed & (2 ** 64 - 1),
+                                    out.ctypes.data) != 0:
+        raise ValueError("bad read byte")
+    return out[:S.size]
+
+
+def annotate(ref, seq, offsets, hits: np.ndarray, segments=None):
     """Per hit (a hit set grouped by read): the leftmost alignment start (backward DP, Section
     "Validation"), the hit-rank and the mapping quality (Section "Postprocessing").  Returns
     (start int64, rank uint32, mapq int32)."""
@@ -159,8 +219,10 @@ def annotate(ref, seq, offsets, hits: np.ndarray):
     start = np.empty(max(nh, 1), np.int64)
     rank = np.empty(max(nh, 1), np.uint32)
     mapq = np.empty(max(nh, 1), np.int32)
+    sg, ns = _segs(segments)
     if _load().oracle_annotate(_p(R), len(R), _p(S), offs.ctypes.data, n, _p(hr), _p(hs), _p(he), _p(hd), nh,
-                               start.ctypes.data, rank.ctypes.data, mapq.ctypes.data) != 0:
+                               start.ctypes.data, rank.ctypes.data, mapq.ctypes.data,
+                               sg.ctypes.data if ns else None, ns) != 0:
         raise ValueError("bad input to annotate")
     return start[:nh], rank[:nh], mapq[:nh]
 

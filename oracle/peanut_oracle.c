@@ -10,7 +10,9 @@
  *   prefix of length i and any reference substring ending at j.  Boundary: E[0][j] = 0 (the
  *   alignment may start anywhere), E[i][-1] = i.  Recurrence:
  *       E[i][j] = min(E[i-1][j-1] + [P[i-1] != R[j]], E[i-1][j] + 1, E[i][j-1] + 1).
- *   D[j] = E[m][j] for j in [0, n).
+ *   D[j] = E[m][j] for j in [0, n).  A reference of several contigs, or with long runs of N, is
+ *   a list of segments (below, "unknown bases and contigs"); the matrix then restarts at every
+ *   segment start (E[i][a-1] = i for segment [a, b)) and only ends inside a segment count.
  *
  *   Hit set (the reading adopted for the paper's "duplicate removal" and strata, Section
  *   "Postprocessing"): for read r, strand s (s = 1 aligns the reverse complement of the read to
@@ -69,6 +71,155 @@ static int check_acgt(const char* s, int64_t n) {
     for (int64_t i = 0; i < n; i++)
         if (base_code(s[i]) < 0) return -1;
     return 0;
+}
+
+/* ---- unknown bases and contigs ----
+ *
+ * Section "The q-group index" (encoding paragraph): an unknown base N becomes a random base, and
+ * long runs of N stay out of the index.  Section "Overview": every step runs per chromosome, so
+ * no hit spans two contigs.  Readings:
+ *   - the random base is drawn from a counter-based generator, so that a run is reproducible:
+ *     reference position p takes the top two bits of output p + 1 of SplitMix64 started at the
+ *     reference's seed; offset i of a read takes the top two bits of output i + 1 of SplitMix64
+ *     started at (seed XOR the FNV-1a 64 hash of the read's bytes, upper-cased), so a read's
+ *     bases do not depend on the batch it arrives in;
+ *   - a run of at least gap_min Ns inside one contig is a gap: like a contig boundary, no
+ *     alignment enters it and none spans it.  The reference is then a list of segments (the
+ *     stretches of each contig between gaps), and the semiglobal matrix restarts at every
+ *     segment start: D[j] for j in segment [a, b) is computed over R[a..j] only;
+ *   - lower-case a, c, g, t, n mean their upper-case bases (soft-masked input). */
+
+/* SplitMix64 (G. L. Steele, D. Lea, C. H. Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): the state advances by the odd constant 0x9E3779B97F4A7C15 and each
+ * output is the state passed through the generator's finalizer (xor-shift 30, multiply
+ * 0xBF58476D1CE4E5B9, xor-shift 27, multiply 0x94D049BB133111EB, xor-shift 31).  Returns output
+ * number i (i >= 1) of the generator seeded with `seed`. */
+uint64_t oracle_splitmix64(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* FNV-1a, 64 bits (G. Fowler, L. C. Noll, K.-P. Vo): start from the offset basis
+ * 0xcbf29ce484222325; per byte, xor it in, then multiply by the prime 0x100000001b3. */
+uint64_t oracle_fnv1a64(const char* s, int64_t n) {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    for (int64_t i = 0; i < n; i++) {
+        h ^= (uint8_t)s[i];
+        h *= 0x100000001b3ULL;
+    }
+    return h;
+}
+
+static char upper_base(char c) {
+    switch (c) {
+        case 'a': return 'A';
+        case 'c': return 'C';
+        case 'g': return 'G';
+        case 't': return 'T';
+        case 'n': return 'N';
+        default: return c;
+    }
+}
+
+/* Replaces the unknown bases of a reference and lists its segments.
+ *   seq[0..n): A/C/G/T/N in either case.  contig_starts[0..ncontig): 0 first, strictly
+ *   ascending, each < n (contig c spans [contig_starts[c], contig_starts[c + 1]) and the last
+ *   ends at n).  gap_min >= 1.
+ *   text[0..n) receives the reference with every N replaced (gap bases too, although no
+ *   alignment uses them).  seg[2 s], seg[2 s + 1] receive segment s as [start, end).
+ * Returns the number of segments, -1 on a bad byte or contig list, -2 if more than seg_cap. */
+int64_t oracle_prepare_reference(const char* seq, int64_t n, const int64_t* contig_starts, int64_t ncontig,
+                                 int64_t gap_min, uint64_t seed, char* text, int64_t* seg, int64_t seg_cap) {
+    if (ncontig < 1 || contig_starts[0] != 0 || gap_min < 1) return -1;
+    for (int64_t c = 1; c < ncontig; c++)
+        if (contig_starts[c] <= contig_starts[c - 1] || contig_starts[c] >= n) return -1;
+    for (int64_t p = 0; p < n; p++) {
+        char u = upper_base(seq[p]);
+        if (u == 'N') {
+            text[p] = "ACGT"[oracle_splitmix64(seed, (uint64_t)p + 1) >> 62];
+        } else if (base_code(u) >= 0) {
+            text[p] = u;
+        } else {
+            return -1;
+        }
+    }
+    int64_t ns = 0;
+    for (int64_t c = 0; c < ncontig; c++) {
+        const int64_t a = contig_starts[c], b = c + 1 < ncontig ? contig_starts[c + 1] : n;
+        int64_t open = a; /* start of the current segment */
+        int64_t p = a;
+        while (p < b) {
+            if (upper_base(seq[p]) != 'N') {
+                p++;
+                continue;
+            }
+            int64_t e = p;
+            while (e < b && upper_base(seq[e]) == 'N') e++;
+            if (e - p >= gap_min) { /* a gap: close the segment before it */
+                if (p > open) {
+                    if (ns == seg_cap) return -2;
+                    seg[2 * ns] = open;
+                    seg[2 * ns + 1] = p;
+                    ns++;
+                }
+                open = e;
+            }
+            p = e;
+        }
+        if (b > open) {
+            if (ns == seg_cap) return -2;
+            seg[2 * ns] = open;
+            seg[2 * ns + 1] = b;
+            ns++;
+        }
+    }
+    return ns;
+}
+
+/* Replaces the unknown bases of a batch of reads (bytes A/C/G/T/N in either case) into out,
+ * upper-cased.  Returns 0, or -1 on a bad byte. */
+int oracle_prepare_reads(const char* reads, const int64_t* offs, int64_t nreads, uint64_t seed, char* out) {
+    for (int64_t r = 0; r < nreads; r++) {
+        const int64_t a = offs[r], m = offs[r + 1] - offs[r];
+        for (int64_t i = 0; i < m; i++) {
+            out[a + i] = upper_base(reads[a + i]);
+            if (out[a + i] != 'N' && base_code(out[a + i]) < 0) return -1;
+        }
+        const uint64_t h = oracle_fnv1a64(out + a, m);
+        for (int64_t i = 0; i < m; i++)
+            if (out[a + i] == 'N') out[a + i] = "ACGT"[oracle_splitmix64(seed ^ h, (uint64_t)i + 1) >> 62];
+    }
+    return 0;
+}
+
+/* The segments a call maps against: seg[0..2 nseg) when given, else one segment [0, n). */
+typedef struct {
+    const int64_t* v;
+    int64_t n;
+    int64_t whole[2];
+} segs_t;
+
+static void segs_init(segs_t* S, const int64_t* seg, int64_t nseg, int64_t n) {
+    S->whole[0] = 0;
+    S->whole[1] = n;
+    if (seg && nseg > 0) {
+        S->v = seg;
+        S->n = nseg;
+    } else {
+        S->v = S->whole;
+        S->n = n > 0 ? 1 : 0;
+    }
+}
+
+/* Segments must be non-empty, ascending, disjoint and inside [0, n). */
+static int segs_valid(const segs_t* S, int64_t n) {
+    for (int64_t x = 0; x < S->n; x++) {
+        if (S->v[2 * x] < 0 || S->v[2 * x] >= S->v[2 * x + 1] || S->v[2 * x + 1] > n) return 0;
+        if (x > 0 && S->v[2 * x] < S->v[2 * x - 1]) return 0;
+    }
+    return 1;
 }
 
 /* ---- semiglobal DP (Section "Validation") ---- */
@@ -204,28 +355,36 @@ static char* revcomp_copy(const char* s, int64_t m) {
 /* ---- brute force: the definition over the whole reference ---- */
 
 oracle_hits* oracle_map_bruteforce(const char* R, int64_t n, const char* reads, const int64_t* offs,
-                                   int64_t nreads, const int32_t* k, int mode) {
+                                   int64_t nreads, const int32_t* k, int mode, const int64_t* seg, int64_t nseg) {
     if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return NULL;
+    segs_t S;
+    segs_init(&S, seg, nseg, n);
+    if (!segs_valid(&S, n)) return NULL;
     oracle_hits* h = (oracle_hits*)calloc(1, sizeof(oracle_hits));
     int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int64_t* js = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int32_t* ds = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     for (int64_t r = 0; r < nreads; r++) {
         int64_t m = offs[r + 1] - offs[r];
+        int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
         for (int s = 0; s < 2; s++) {
             char* P = s == 0 ? NULL : revcomp_copy(reads + offs[r], m);
             const char* pat = s == 0 ? reads + offs[r] : P;
-            oracle_semiglobal_column(pat, m, R, n, D);
-            int64_t cnt = 0;
-            for (int64_t j = 0; j < n; j++)
-                if (D[j] <= k[r]) {
-                    js[cnt] = j;
-                    ds[cnt] = D[j];
-                    cnt++;
-                }
-            emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
+            for (int64_t x = 0; x < S.n; x++) { /* the matrix restarts at every segment start */
+                const int64_t a = S.v[2 * x], b = S.v[2 * x + 1];
+                dp_columns(pat, m, R, a, b - 1, col, D);
+                int64_t cnt = 0;
+                for (int64_t j = a; j < b; j++)
+                    if (D[j - a] <= k[r]) {
+                        js[cnt] = j;
+                        ds[cnt] = D[j - a];
+                        cnt++;
+                    }
+                emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
+            }
             free(P);
         }
+        free(col);
     }
     free(D);
     free(js);
@@ -290,9 +449,12 @@ static uint64_t qgram_code(const char* s, int q) {
 /* Returns NULL if q is out of range [1, 31], a character is not ACGT, or some read has a
  * lemma threshold t = m + 1 - q(k + 1) below 1 (the filter would not be lossless). */
 oracle_hits* oracle_map_filter(const char* R, int64_t n, const char* reads, const int64_t* offs,
-                               int64_t nreads, const int32_t* k, int q, int mode) {
+                               int64_t nreads, const int32_t* k, int q, int mode, const int64_t* seg, int64_t nseg) {
     if (q < 1 || q > 31) return NULL;
     if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return NULL;
+    segs_t S;
+    segs_init(&S, seg, nseg, n);
+    if (!segs_valid(&S, n)) return NULL;
     for (int64_t r = 0; r < nreads; r++) {
         int64_t m = offs[r + 1] - offs[r];
         if (m + 1 - (int64_t)q * (k[r] + 1) < 1) return NULL;
@@ -383,26 +545,32 @@ oracle_hits* oracle_map_filter(const char* R, int64_t n, const char* reads, cons
                 }
                 if (lo < 0) lo = 0;
                 if (hi > n - 1) hi = n - 1;
-                if (lo > hi) continue;
-                int64_t a = lo - (m + kk) + 1;
-                if (a < 0) a = 0;
-                int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(hi - a + 1));
-                dp_columns(pats[2 * r + s], m, R, a, hi, col, D);
-                for (int64_t j = lo; j <= hi; j++) {
-                    if (D[j - a] > kk) continue;
-                    if (cnt == cj) {
-                        cj = cj ? 2 * cj : 64;
-                        js = (int64_t*)realloc(js, sizeof(int64_t) * (size_t)cj);
-                        ds = (int32_t*)realloc(ds, sizeof(int32_t) * (size_t)cj);
+                /* the range's piece in each segment; the matrix restarts at the segment start */
+                for (int64_t y = 0; y < S.n; y++) {
+                    const int64_t sa = S.v[2 * y], sb = S.v[2 * y + 1];
+                    const int64_t plo = lo > sa ? lo : sa, phi = hi < sb - 1 ? hi : sb - 1;
+                    if (plo > phi) continue;
+                    int64_t a = plo - (m + kk) + 1;
+                    if (a < sa) a = sa;
+                    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(phi - a + 1));
+                    dp_columns(pats[2 * r + s], m, R, a, phi, col, D);
+                    cnt = 0;
+                    for (int64_t j = plo; j <= phi; j++) {
+                        if (D[j - a] > kk) continue;
+                        if (cnt == cj) {
+                            cj = cj ? 2 * cj : 64;
+                            js = (int64_t*)realloc(js, sizeof(int64_t) * (size_t)cj);
+                            ds = (int32_t*)realloc(ds, sizeof(int32_t) * (size_t)cj);
+                        }
+                        js[cnt] = j;
+                        ds[cnt] = D[j - a];
+                        cnt++;
                     }
-                    js[cnt] = j;
-                    ds[cnt] = D[j - a];
-                    cnt++;
+                    free(D);
+                    /* 6. canonical tuple per maximal run (a run ends at its piece's edges) */
+                    emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
                 }
-                free(D);
             }
-            /* 6. canonical tuple per maximal run */
-            emit_runs(h, (uint32_t)r, (uint8_t)s, js, ds, cnt, mode);
             free(js);
             free(ds);
             free(iv);
@@ -576,9 +744,9 @@ int64_t oracle_frequent_qgrams(const char* R, int64_t n, int q, int64_t cap, uin
  * Reading (the paper does not say which start when several give d): the leftmost one,
  * start = j - c + 1 for the largest c with G[c] = d; an alignment of cost d spans at most m + d
  * reference bases, so c <= min(j + 1, m + d).  Returns -1 if no c reaches d (not a hit). */
-static int64_t hit_start(const char* P, int64_t m, const char* R, int64_t j, int32_t d) {
+static int64_t hit_start(const char* P, int64_t m, const char* R, int64_t seg_start, int64_t j, int32_t d) {
     int64_t C = m + d;
-    if (C > j + 1) C = j + 1;
+    if (C > j + 1 - seg_start) C = j + 1 - seg_start; /* the alignment stays in j's segment */
     int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(m + 1));
     for (int64_t i = 0; i <= m; i++) col[i] = (int32_t)i; /* c = 0: the whole pattern deleted */
     int64_t best = (col[m] == d) ? 0 : -1;
@@ -611,8 +779,11 @@ static int64_t hit_start(const char* P, int64_t m, const char* R, int64_t j, int
  * Returns 0, or -1 on bad input (non-ACGT base, a hit whose start cannot be found). */
 int oracle_annotate(const char* R, int64_t n, const char* reads, const int64_t* offs, int64_t nreads,
                     const uint32_t* hr, const uint8_t* hs, const int64_t* he, const int32_t* hd, int64_t nh,
-                    int64_t* start, uint32_t* rank, int32_t* mapq) {
+                    int64_t* start, uint32_t* rank, int32_t* mapq, const int64_t* seg, int64_t nseg) {
     if (check_acgt(R, n) || check_acgt(reads, offs[nreads] - offs[0])) return -1;
+    segs_t S;
+    segs_init(&S, seg, nseg, n);
+    if (!segs_valid(&S, n)) return -1;
     int64_t x = 0;
     while (x < nh) {
         int64_t y = x;
@@ -625,7 +796,10 @@ int oracle_annotate(const char* R, int64_t n, const char* reads, const int64_t* 
         char* rc = revcomp_copy(reads + offs[r], m);
         for (int64_t z = x; z < y; z++) {
             if (he[z] < 0 || he[z] >= n) return -1;
-            start[z] = hit_start(hs[z] ? rc : fw, m, R, he[z], hd[z]);
+            int64_t sx = 0; /* the segment holding the end */
+            while (sx < S.n && S.v[2 * sx + 1] <= he[z]) sx++;
+            if (sx == S.n || S.v[2 * sx] > he[z]) return -1; /* an end in a gap */
+            start[z] = hit_start(hs[z] ? rc : fw, m, R, S.v[2 * sx], he[z], hd[z]);
             if (start[z] < 0) return -1;
             uint32_t c = 0;
             for (int64_t u = x; u < y; u++) c += hd[u] <= hd[z] ? 1u : 0u;
