@@ -138,10 +138,45 @@ typedef struct {
 
 /* Packs an ASCII reference into 2 bits per base on the device (A=00, C=01, G=10, T=11, first
  * base most significant; Section "The q-group index", encoding paragraph) and keeps it resident.
- *   seq: host, len bytes of 'A'/'C'/'G'/'T'.  len: 1 .. 2^39.  stream: see conventions.
+ * One contig; the same as peanut_pack_reference_contigs with contig_starts = {0}, gap_min =
+ * PEANUT_DEFAULT_GAP_MIN and n_seed = 0.
+ *   seq: host, len bytes of A/C/G/T/N in either case.  len: 1 .. 2^39.  stream: see conventions.
  *   out: receives the new reference object.
- * Errors: INVALID_ARG (NULL pointer, len out of range, non-ACGT byte), NO_MEMORY, CUDA_ERROR. */
+ * Errors: INVALID_ARG (NULL pointer, len out of range, another byte), NO_MEMORY, CUDA_ERROR. */
 peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream, peanut_ref** out);
+
+#define PEANUT_DEFAULT_GAP_MIN 16u
+
+/* Packs a reference made of one or more contigs (chromosomes) laid end to end.
+ * Section "Overview": every step runs per chromosome, so no hit spans two contigs.  Section "The
+ * q-group index" (encoding paragraph): an unknown base N becomes a random base, and long runs of
+ * N stay out of the index.  Here:
+ *   - N at reference position p becomes base (SplitMix64 output number p + 1 of the generator
+ *     seeded with n_seed) >> 62 (Steele, Lea & Flood 2014), so packing is reproducible; N in a
+ *     read at offset i becomes (output i + 1 of SplitMix64 seeded with n_seed XOR the FNV-1a 64
+ *     hash of the read's upper-cased bytes) >> 62, in every batch indexed against this reference;
+ *   - a run of at least gap_min Ns inside one contig is a gap.  Contig boundaries and gaps cut the
+ *     reference into segments: every alignment lies inside one segment (the semiglobal matrix
+ *     restarts at each segment start), so no hit ends in a gap or spans a boundary;
+ *   - lower-case a, c, g, t, n are read as their upper-case bases (soft-masked input).
+ * Hits keep global coordinates (positions in the concatenated sequence, gaps included); the
+ * caller maps them to (contig, offset) with its own contig_starts.
+ *   seq: host, len bytes.  len: 1 .. 2^39.
+ *   contig_starts: host, n_contigs ascending start positions, the first 0, each < len (contig c
+ *     spans [contig_starts[c], contig_starts[c + 1]), the last ends at len); NULL or
+ *     n_contigs = 0 means one contig.
+ *   gap_min: 1 .. 2^32 - 1 (PEANUT_DEFAULT_GAP_MIN = the paper's q, a run long enough to hold a
+ *     whole q-gram of Ns).  n_seed: any value.  stream: see conventions.
+ * Errors: INVALID_ARG (NULL pointer, len out of range, a byte other than A/C/G/T/N, a bad contig
+ *         list, gap_min = 0), UNSUPPORTED (more than 2^26 runs of N), NO_MEMORY, CUDA_ERROR. */
+peanut_status peanut_pack_reference_contigs(const char* seq, uint64_t len, const uint64_t* contig_starts,
+                                            uint32_t n_contigs, uint32_t gap_min, uint64_t n_seed, void* stream,
+                                            peanut_ref** out);
+
+/* The reference's segments (see peanut_pack_reference_contigs): count, then the [start, end)
+ * pairs into caller-owned host arrays of that many entries each (either may be NULL).
+ * peanut_ref_segments returns INVALID_ARG for a bad reference or a NULL count. */
+peanut_status peanut_ref_segments(const peanut_ref* ref, uint64_t* count, uint64_t* starts, uint64_t* ends);
 
 /* Reference length in bases. */
 uint64_t peanut_ref_length(const peanut_ref* ref);

@@ -245,7 +245,9 @@ peanut_status peanut_set_allocator(peanut_alloc_fn alloc, peanut_release_fn rele
     });
 }
 
-peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream, peanut_ref** out) {
+peanut_status peanut_pack_reference_contigs(const char* seq, uint64_t len, const uint64_t* contig_starts,
+                                            uint32_t n_contigs, uint32_t gap_min, uint64_t n_seed, void* stream,
+                                            peanut_ref** out) {
     return guarded([&] {
         PN_REQUIRE(seq && out, PEANUT_INVALID_ARG, "NULL argument");
         PN_REQUIRE(len >= 1 && len < kMaxRefLen, PEANUT_INVALID_ARG, "reference length %llu outside 1..2^39",
@@ -254,12 +256,27 @@ peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream,
         peanut_ref* ref = new peanut_ref();
         ref->stream = (cudaStream_t)stream;
         try {
-            pack_reference(ref, seq, len, ref->stream);
+            pack_reference(ref, seq, len, contig_starts, n_contigs, gap_min, n_seed, ref->stream);
         } catch (...) {
             delete ref;
             throw;
         }
         *out = ref;
+    });
+}
+
+peanut_status peanut_pack_reference(const char* seq, uint64_t len, void* stream, peanut_ref** out) {
+    return peanut_pack_reference_contigs(seq, len, nullptr, 0, PEANUT_DEFAULT_GAP_MIN, 0, stream, out);
+}
+
+peanut_status peanut_ref_segments(const peanut_ref* ref, uint64_t* count, uint64_t* starts, uint64_t* ends) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && count, PEANUT_INVALID_ARG, "bad reference or NULL count");
+        *count = ref->n_seg;
+        for (uint32_t x = 0; x < ref->n_seg; ++x) {
+            if (starts) starts[x] = ref->hseg[2 * x];
+            if (ends) ends[x] = ref->hseg[2 * x + 1];
+        }
     });
 }
 

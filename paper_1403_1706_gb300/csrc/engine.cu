@@ -69,7 +69,8 @@ __global__ void check_bases_k(const uint8_t* __restrict__ s, uint64_t n, uint32_
     bool bad = false;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
         const uint8_t c = s[x];
-        bad |= !(c == 'A' || c == 'C' || c == 'G' || c == 'T');
+        const uint8_t u = (c >= 'a' && c <= 'z') ? (uint8_t)(c - 32) : c;  // either case
+        bad |= !(u == 'A' || u == 'C' || u == 'G' || u == 'T' || u == 'N');
     }
     if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStBadBase);
 }
@@ -383,7 +384,7 @@ static void admit(peanut_engine* E, Submission* S, cudaStream_t s) {
     PN_CUDA(cudaStreamSynchronize(s));
     PN_REQUIRE(!(h[0] & kStBadLength), PEANUT_INVALID_ARG,
                "read offsets must ascend within the submission and give lengths 1..%d", kMaxReadLen);
-    PN_REQUIRE(!(h[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T");
+    PN_REQUIRE(!(h[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T/N (either case)");
     PN_REQUIRE(!(h[0] & kStBadThreshold), PEANUT_INVALID_ARG,
                "a read admits no q with m + 1 - q(k + 1) >= 1%s", E->p.fixed_q ? " at the engine's fixed q" : "");
     for (int c = 1; c < kQSlots; ++c) {

@@ -4,6 +4,7 @@
 // with its first base most significant.  The index is Algorithm 1 run over the CANONICAL code
 // c = min(g, revcomp(g)) of every read q-gram, so one index serves both strands; each
 // occurrence records whether the read holds c itself or its reverse complement.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -12,7 +13,7 @@
 
 namespace pn {
 
-__constant__ uint8_t kCodeLut[256];
+__constant__ uint8_t kCodeLut[256];  // A/C/G/T (either case) -> 0..3, N/n -> 4, else 0xFF
 
 static void init_lut() {
     static std::mutex mu;
@@ -22,19 +23,42 @@ static void init_lut() {
     if (done.load()) return;
     uint8_t lut[256];
     for (int i = 0; i < 256; ++i) lut[i] = 0xFF;
-    lut['A'] = 0;
-    lut['C'] = 1;
-    lut['G'] = 2;
-    lut['T'] = 3;
+    const char* up = "ACGT";
+    const char* lo = "acgt";
+    for (int c = 0; c < 4; ++c) {
+        lut[(uint8_t)up[c]] = (uint8_t)c;
+        lut[(uint8_t)lo[c]] = (uint8_t)c;
+    }
+    lut['N'] = 4;
+    lut['n'] = 4;
     PN_CUDA(cudaMemcpyToSymbol(kCodeLut, lut, sizeof(lut)));
     done = true;
+}
+
+// ---- unknown bases -----------------------------------------------------------------------
+//
+// Section "The q-group index" (encoding paragraph) turns an unknown base N into a random base.
+// Here the draw is reproducible: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014: the state steps by
+// the odd constant 0x9E3779B97F4A7C15, each output is the state through the generator's
+// finalizer).  Reference position p takes the top two bits of output p + 1 of the generator
+// seeded with the reference's seed; offset i of a read takes those of output i + 1 of the one
+// seeded with (seed XOR the FNV-1a 64 hash of the read's upper-cased bytes), so a read's bases
+// do not depend on the batch it arrives in.
+
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+    uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
 }
 
 // ---- reference packing --------------------------------------------------------------------
 
 // One packed word (16 bases) per thread; bytes at or beyond len pack as A (never read as data).
-__global__ void pack_reference_k(const uint8_t* __restrict__ ascii, uint64_t len,
-                                 uint32_t* __restrict__ words, uint32_t* status) {
+// An N takes its seeded base and sets its bit in nmask (bit t of word w = base 16 w + t), from
+// which the gaps are found.
+__global__ void pack_reference_k(const uint8_t* __restrict__ ascii, uint64_t len, uint64_t base0, uint64_t seed,
+                                 uint32_t* __restrict__ words, uint16_t* __restrict__ nmask, uint32_t* status) {
     const uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t b0 = w * 16;
     if (b0 >= len) return;
@@ -45,24 +69,73 @@ __global__ void pack_reference_k(const uint8_t* __restrict__ ascii, uint64_t len
     } else {
         for (int t = 0; t < 16; ++t) buf[t] = b0 + t < len ? ascii[b0 + t] : 'A';
     }
-    uint32_t word = 0;
+    uint32_t word = 0, nm = 0;
     bool bad = false;
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
-        const uint8_t c = kCodeLut[buf[t]];
-        bad |= c > 3;
-        word |= (uint32_t)(c & 3) << (30 - 2 * t);
+        uint32_t c = kCodeLut[buf[t]];
+        bad |= c > 4;
+        if (c == 4) {
+            c = (uint32_t)(splitmix64_at(seed, base0 + b0 + t + 1) >> 62);
+            nm |= 1u << t;
+        }
+        word |= (c & 3u) << (30 - 2 * t);
     }
     words[w] = word;
+    nmask[w] = (uint16_t)nm;
     if (bad) atomicOr(status, kStBadBase);
+    if (nm) atomicOr(status, kStHasN);
 }
 
-void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s) {
+// Boundaries of the runs of N: positions p where N-ness changes (p is N and p - 1 is not, or the
+// reverse), from the mask read as 32-bit words (bit b of word i = base 32 i + b; the mask's zero
+// padding ends a run that reaches the end).  Pass 0 counts them, pass 1 lists them (unordered).
+template <bool kList>
+__global__ void n_edges_k(const uint32_t* __restrict__ m32, uint64_t nw, unsigned long long* count,
+                          uint64_t* __restrict__ edges, uint64_t cap) {
+    uint32_t local = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t cur = m32[i], prev = i ? m32[i - 1] : 0u;
+        uint32_t t = cur ^ ((cur << 1) | (prev >> 31));
+        if (!kList) {
+            local += __popc(t);
+            continue;
+        }
+        while (t) {
+            const uint32_t b = __ffs(t) - 1;
+            t &= t - 1;
+            const unsigned long long x = atomicAdd(count, 1ull);
+            if (x < cap) edges[x] = i * 32 + b;
+        }
+    }
+    if (!kList && local) atomicAdd(count, (unsigned long long)local);
+}
+
+constexpr uint64_t kMaxNEdges = 1ull << 27;  // run boundaries of N the packing lists (2^26 runs)
+
+void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, const uint64_t* contig_starts,
+                    uint32_t n_contigs, uint32_t gap_min, uint64_t seed, cudaStream_t s) {
     init_lut();
+    std::vector<uint64_t> cs;
+    if (contig_starts && n_contigs)
+        cs.assign(contig_starts, contig_starts + n_contigs);
+    else
+        cs.push_back(0);
+    PN_REQUIRE(cs[0] == 0, PEANUT_INVALID_ARG, "the first contig must start at 0");
+    for (size_t c = 1; c < cs.size(); ++c)
+        PN_REQUIRE(cs[c] > cs[c - 1] && cs[c] < len, PEANUT_INVALID_ARG,
+                   "contig starts must ascend strictly and lie inside the reference (contig %zu)", c);
+    PN_REQUIRE(gap_min >= 1, PEANUT_INVALID_ARG, "gap_min must be at least 1");
     ref->n = len;
+    ref->n_seed = seed;
+    ref->n_contigs = (uint32_t)cs.size();
     ref->n_words = (len + 15) / 16 + 8;  // lookahead padding for the scan's 64-bit windows
     ref->packed.alloc(ref->n_words, s);
     ref->packed.zero();
+    // N mask: one 16-bit word per packed word, an even count and one zero 32-bit word past the end
+    const uint64_t nw16 = (((len + 15) / 16) + 3) & ~1ull;
+    DBuf<uint16_t> nmask(nw16, s);
+    nmask.zero();
     DBuf<uint32_t> status(1, s);
     status.zero();
     const uint64_t chunk = 1ull << 30;  // bases per upload (multiple of 16)
@@ -71,11 +144,69 @@ void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStr
         const uint64_t nb = len - b < chunk ? len - b : chunk;
         PN_CUDA(cudaMemcpyAsync(tmp.p, host_seq + b, nb, cudaMemcpyHostToDevice, s));
         const uint64_t nw = (nb + 15) / 16;
-        pack_reference_k<<<grid_for(nw, 256), 256, 0, s>>>(tmp.p, nb, ref->packed.p + b / 16, status.p);
+        pack_reference_k<<<grid_for(nw, 256), 256, 0, s>>>(tmp.p, nb, b, seed, ref->packed.p + b / 16,
+                                                            nmask.p + b / 16, status.p);
         PN_CHECK_LAUNCH();
     }
+    tmp.reset();
     const uint32_t st = to_host(status.p, s);
-    PN_REQUIRE(!(st & kStBadBase), PEANUT_INVALID_ARG, "reference contains a byte other than A/C/G/T");
+    PN_REQUIRE(!(st & kStBadBase), PEANUT_INVALID_ARG, "reference contains a byte other than A/C/G/T/N (either case)");
+    // runs of N as [start, end) pairs, ascending
+    std::vector<uint64_t> runs;
+    if (st & kStHasN) {
+        const uint64_t nw32 = nw16 / 2;
+        const unsigned g = grid_for(nw32, 256, (unsigned)sm_count() * 16);
+        DBuf<unsigned long long> cnt(1, s);
+        cnt.zero();
+        n_edges_k<false><<<g, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(nmask.p), nw32, cnt.p, nullptr, 0);
+        PN_CHECK_LAUNCH();
+        const uint64_t E = to_host(cnt.p, s);
+        PN_REQUIRE(E <= kMaxNEdges, PEANUT_UNSUPPORTED, "more than %llu runs of N",
+                   (unsigned long long)(kMaxNEdges / 2));
+        PN_REQUIRE(E % 2 == 0, PEANUT_CUDA_ERROR, "unpaired run boundary of N");
+        DBuf<uint64_t> edges(E ? E : 1, s);
+        cnt.zero();
+        n_edges_k<true><<<g, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(nmask.p), nw32, cnt.p, edges.p, E);
+        PN_CHECK_LAUNCH();
+        runs.resize(E);
+        if (E) PN_CUDA(cudaMemcpyAsync(runs.data(), edges.p, E * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
+        std::sort(runs.begin(), runs.end());
+    }
+    nmask.reset();
+    // segments: each contig cut by the pieces of runs of at least gap_min Ns inside it
+    std::vector<uint64_t> seg;
+    uint64_t gaps = 0;
+    size_t ri = 0;
+    for (size_t c = 0; c < cs.size(); ++c) {
+        const uint64_t a = cs[c], b = c + 1 < cs.size() ? cs[c + 1] : len;
+        uint64_t open = a;
+        while (ri < runs.size() / 2 && runs[2 * ri + 1] <= a) ++ri;
+        for (size_t x = ri; x < runs.size() / 2 && runs[2 * x] < b; ++x) {
+            const uint64_t ga = runs[2 * x] > a ? runs[2 * x] : a;
+            const uint64_t gb = runs[2 * x + 1] < b ? runs[2 * x + 1] : b;
+            if (gb - ga < gap_min) continue;
+            if (ga > open) {
+                seg.push_back(open);
+                seg.push_back(ga);
+            }
+            open = gb;
+            ++gaps;
+        }
+        if (b > open) {
+            seg.push_back(open);
+            seg.push_back(b);
+        }
+    }
+    ref->n_gaps = gaps;
+    ref->n_seg = (uint32_t)(seg.size() / 2);
+    PN_REQUIRE(seg.size() / 2 < (1ull << 31), PEANUT_UNSUPPORTED, "too many segments");
+    ref->hseg = seg;
+    ref->seg.alloc(seg.size() ? seg.size() : 2, s);
+    ref->seg.zero();
+    if (!seg.empty())
+        PN_CUDA(cudaMemcpyAsync(ref->seg.p, ref->hseg.data(), seg.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaStreamSynchronize(s));
 }
 
 // ---- frequent q-grams of the reference ------------------------------------------------------
@@ -353,15 +484,40 @@ __global__ void read_meta_k(const uint64_t* __restrict__ off, uint32_t n_reads, 
     atomicMax(&maxes[1], (uint32_t)k);
 }
 
+// Base codes of the batch; an N keeps code 4 until read_fix_n_k replaces it.
 __global__ void read_codes_k(const uint8_t* __restrict__ ascii, uint64_t total, uint8_t* codes, uint32_t* status) {
-    bool bad = false;
+    bool bad = false, has_n = false;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint8_t c = kCodeLut[ascii[x]];
-        bad |= c > 3;
-        codes[x] = c & 3;
+        bad |= c > 4;
+        has_n |= c == 4;
+        codes[x] = c > 4 ? 0 : c;
     }
     if (bad) atomicOr(status, kStBadBase);
+    if (has_n) atomicOr(status, kStHasN);
+}
+
+// One thread per read holding an N: FNV-1a 64 (Fowler, Noll & Vo: offset basis
+// 0xcbf29ce484222325, per byte xor then multiply by 0x100000001b3) of its upper-cased bytes, then
+// every N at offset i takes the top two bits of output i + 1 of SplitMix64 seeded with
+// (seed XOR that hash).
+__global__ void read_fix_n_k(const uint8_t* __restrict__ ascii, const uint64_t* __restrict__ off, uint32_t n,
+                             uint64_t seed, uint8_t* __restrict__ codes) {
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint64_t a = off[r], b = off[r + 1];  // offsets index the batch's bytes and codes alike
+    bool any = false;
+    for (uint64_t x = a; x < b; ++x) any |= codes[x] == 4;
+    if (!any) return;
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (uint64_t x = a; x < b; ++x) {
+        uint8_t c = ascii[x];
+        if (c >= 'a' && c <= 'z') c = (uint8_t)(c - 32);
+        h = (h ^ c) * 0x100000001b3ull;
+    }
+    for (uint64_t x = a; x < b; ++x)
+        if (codes[x] == 4) codes[x] = (uint8_t)(splitmix64_at(seed ^ h, x - a + 1) >> 62);
 }
 
 // Classifies every read q-gram (one warp per read): canonical code, orientation, whether it is
@@ -674,7 +830,12 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
     PN_CUDA(cudaStreamSynchronize(s));
     PN_REQUIRE(!(st[0] & kStBadLength), PEANUT_INVALID_ARG,
                "read offsets must ascend within the sequence buffer and give lengths 1..%d", kMaxReadLen);
-    PN_REQUIRE(!(st[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T");
+    PN_REQUIRE(!(st[0] & kStBadBase), PEANUT_INVALID_ARG, "a read contains a byte other than A/C/G/T/N (either case)");
+    if (st[0] & kStHasN) {
+        read_fix_n_k<<<grid_for(n, 128), 128, 0, s>>>((const uint8_t*)d_seqs, R->base_off.p, n, R->ref->n_seed,
+                                                       R->codes.p);
+        PN_CHECK_LAUNCH();
+    }
     PN_REQUIRE(!(st[0] & kStBadThreshold), PEANUT_INVALID_ARG,
                "a read violates the q-gram lemma threshold m + 1 - q(k + 1) >= 1 (q = %u), or keeps no "
                "guaranteed intact q-gram at sampling stride %u", q, stride);

@@ -6,6 +6,7 @@
 
 #include <memory>
 #include <mutex>
+#include <vector>
 #include <string>
 
 #include "peanut.h"
@@ -34,6 +35,7 @@ enum : uint32_t {
     kStBadLength = 2u,
     kStBadThreshold = 4u,
     kStOverflow = 8u,
+    kStHasN = 16u,  // an unknown base (N) was seen; its replacement runs afterwards
 };
 
 // ---- errors -------------------------------------------------------------------------------
@@ -234,6 +236,14 @@ struct peanut_ref {
     std::shared_ptr<pn::RefPrep> prep[17];  // per q; batches share the table they were indexed with
     std::shared_ptr<pn::RefIndex> rindex[17];  // per q, built on request (peanut_index_reference)
     std::mutex prep_mu;
+    // Segments: the stretches of each contig between gaps (runs of >= gap_min unknown bases).
+    // No alignment leaves its segment; seg holds [start, end) pairs, ascending.
+    uint64_t n_seed = 0;                 // seeds the replacement of unknown bases (reference and reads)
+    uint32_t n_contigs = 1;
+    uint64_t n_gaps = 0;
+    std::vector<uint64_t> hseg;          // host copy, 2 per segment
+    pn::DBuf<uint64_t> seg;              // device copy
+    uint32_t n_seg = 0;
 };
 
 struct peanut_reads {
@@ -301,7 +311,13 @@ HostHits* download_hits(const peanut_device_hits& dh, cudaStream_t s);  // synch
 uint64_t pageable_blocks();  // result blocks so far that fell back to pageable memory
 void free_host_hits(HostHits* H);
 // index.cu
-void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, cudaStream_t s);
+// True when the reference is more than one segment [0, n) (several contigs, or gaps).
+inline bool segmented(const peanut_ref* ref) {
+    return !(ref->n_seg == 1 && ref->hseg[0] == 0 && ref->hseg[1] == ref->n);
+}
+
+void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, const uint64_t* contig_starts,
+                    uint32_t n_contigs, uint32_t gap_min, uint64_t seed, cudaStream_t s);
 RefPrep* prepare_reference(const peanut_ref* ref, uint32_t q, uint32_t cap, cudaStream_t s);
 void free_prep(RefPrep* p);
 void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets, uint32_t k_fixed,

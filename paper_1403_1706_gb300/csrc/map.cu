@@ -1330,6 +1330,55 @@ __global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, 
     }
 }
 
+// ---- candidate ranges cut at the reference's segment edges -----------------------------------
+//
+// Section "Overview": every step runs per chromosome, and long runs of N stay out of the index
+// (Section "The q-group index").  A reference of several contigs, or with gaps, is a list of
+// segments; a candidate range of end positions is cut into its pieces inside each segment it
+// meets (a piece in no segment, i.e. in a gap, is dropped), so that verification can start the
+// matrix at the segment start and no reported run crosses a segment edge.
+
+// The first segment whose end lies after p (n_seg when none).
+__device__ __forceinline__ uint32_t first_segment_after(const uint64_t* __restrict__ seg, uint32_t n_seg, uint64_t p) {
+    uint32_t l = 0, h = n_seg;
+    while (l < h) {
+        const uint32_t mid = (l + h) >> 1;
+        if (seg[2 * mid + 1] <= p)
+            l = mid + 1;
+        else
+            h = mid;
+    }
+    return l;
+}
+
+// Number of pieces of candidate x: the segments that meet [lo, hi].
+struct PieceCount {
+    const uint64_t* key;
+    const uint64_t* hi;
+    const uint64_t* seg;
+    uint32_t n_seg;
+    __device__ uint64_t operator()(uint64_t x) const {
+        const uint64_t lo = key[x] & kPosMask40, h = hi[x];
+        uint64_t c = 0;
+        for (uint32_t i = first_segment_after(seg, n_seg, lo); i < n_seg && seg[2 * i] <= h; ++i) ++c;
+        return c;
+    }
+};
+
+__global__ void seg_split_k(PieceCount pc, uint64_t n, const uint64_t* __restrict__ off, uint64_t* __restrict__ okey,
+                            uint64_t* __restrict__ ohi) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = pc.key[x], lo = key & kPosMask40, h = pc.hi[x];
+        uint64_t o = off[x];
+        for (uint32_t i = first_segment_after(pc.seg, pc.n_seg, lo); i < pc.n_seg && pc.seg[2 * i] <= h; ++i) {
+            const uint64_t sa = pc.seg[2 * i], sb = pc.seg[2 * i + 1];
+            okey[o] = (key & ~kPosMask40) | (lo > sa ? lo : sa);
+            ohi[o] = h < sb - 1 ? h : sb - 1;
+            ++o;
+        }
+    }
+}
+
 // ---- bit-vector verification (Myers 1999 / Hyyro 2003; Section "Validation") ------------------
 //
 // Column j of the semiglobal matrix is held as vertical delta vectors Pv (+1) and Mv (-1), one
@@ -1480,18 +1529,41 @@ struct MyersShared {
     }
 };
 
+// Start of the reference segment holding position p (n_seg >= 1 segments as [start, end) pairs,
+// ascending; p inside one of them).
+__device__ __forceinline__ int64_t segment_start(const uint64_t* __restrict__ seg, uint32_t n_seg, int64_t p) {
+    uint32_t l = 0, h = n_seg;
+    while (l < h) {
+        const uint32_t mid = (l + h) >> 1;
+        if ((int64_t)__ldg(seg + 2 * mid + 1) <= p)
+            l = mid + 1;
+        else
+            h = mid;
+    }
+    return (int64_t)__ldg(seg + 2 * (l < n_seg ? l : n_seg - 1));
+}
+
 // Verifies one candidate range: columns a .. hi of the pattern's semiglobal matrix, runs of ends
 // with distance <= k, leftmost minimum of each run.  Returns the number of columns.  Columns
-// before lo only warm the recurrence up; whole packed words (16 bases) are stepped unrolled.
+// before lo only warm the recurrence up; whole packed words (16 bases) are stepped unrolled.  The
+// range lies inside one segment of the reference (contig, or stretch between runs of N): the
+// matrix starts at that segment's start at the earliest, so no alignment leaves it.
 template <int W, bool kWrite>
-__device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq, unsigned long long& useful) {
+__device__ uint64_t verify_one(const VerifyParams& V, uint64_t x, uint64_t* seq, unsigned long long& useful,
+                               const uint64_t* __restrict__ seg, uint32_t n_seg) {
     const uint64_t key = V.cand_key[x];
     const uint32_t r = (uint32_t)(key >> 41), s = (uint32_t)(key >> 40) & 1u;
     const int64_t lo = (int64_t)(key & kPosMask40), hi = (int64_t)V.cand_hi[x];
     const uint32_t m = V.len[r];
     const int32_t k = V.kk[r];
+    // the first column: m + k before lo, but not before the start of lo's segment (ranges were
+    // cut at segment edges, so the whole range lies in that segment)
     int64_t a = lo - ((int64_t)m + k) + 1;
     if (a < 0) a = 0;
+    if (seg) {
+        const int64_t sa = segment_start(seg, n_seg, lo);
+        if (a < sa) a = sa;
+    }
     const uint64_t* pq = V.peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -1825,7 +1897,8 @@ __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_
 
 template <bool kWrite>
 __global__ void __launch_bounds__(kVerifyThreads, 8)
-    verify_k(VerifyParams V, const uint64_t* __restrict__ order, const unsigned long long* __restrict__ n_live) {
+    verify_k(VerifyParams V, const uint64_t* __restrict__ order, const unsigned long long* __restrict__ n_live,
+             const uint64_t* __restrict__ seg, uint32_t n_seg) {
     __shared__ uint64_t s_eq[4 * kMaxWords * kVerifyThreads];
     uint64_t* seq = s_eq + threadIdx.x;
     unsigned long long cols = 0, wcols = 0, useful = 0;
@@ -1838,10 +1911,10 @@ __global__ void __launch_bounds__(kVerifyThreads, 8)
         const uint32_t W = (V.len[r] + 63) >> 6;
         uint64_t c = 0;
         switch (W) {
-            case 1: c = verify_one<1, kWrite>(V, x, seq, useful); break;
-            case 2: c = verify_one<2, kWrite>(V, x, seq, useful); break;
-            case 3: c = verify_one<3, kWrite>(V, x, seq, useful); break;
-            default: c = verify_one<4, kWrite>(V, x, seq, useful); break;
+            case 1: c = verify_one<1, kWrite>(V, x, seq, useful, seg, n_seg); break;
+            case 2: c = verify_one<2, kWrite>(V, x, seq, useful, seg, n_seg); break;
+            case 3: c = verify_one<3, kWrite>(V, x, seq, useful, seg, n_seg); break;
+            default: c = verify_one<4, kWrite>(V, x, seq, useful, seg, n_seg); break;
         }
         cols += c;
         wcols += c * W;
@@ -2193,15 +2266,27 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     CandCount cc{wcnt.p, nl ? R->lowcx.p : nullptr, lcpos.p, lcnt.p};
     DBuf<uint64_t> coff((uint64_t)n_reads + 1, s);
     exclusive_scan(cc, ArrayOut<uint64_t>{coff.p}, n_reads, tot.p, s);
-    const uint64_t NC = to_host(tot.p, s);
+    uint64_t NC = to_host(tot.p, s);
     R->cand_key.alloc(NC ? NC : 1, s);
     R->cand_hi.alloc(NC ? NC : 1, s);
-    R->n_cand = NC;
     compact_k<<<grid_for((uint64_t)n_reads * 32, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
         n_reads, cc, coff.p, roff.p, wlo.p, whi.p, lc_off.p, lc_keys.p, lc_vals.p, R->cand_key.p, R->cand_hi.p);
     PN_CHECK_LAUNCH();
     wlo.reset();
     whi.reset();
+    if (segmented(ref) && NC) {  // cut the ranges at segment edges (order kept)
+        const PieceCount pc{R->cand_key.p, R->cand_hi.p, ref->seg.p, ref->n_seg};
+        DBuf<uint64_t> poff(NC, s);
+        exclusive_scan(pc, ArrayOut<uint64_t>{poff.p}, NC, tot.p, s);
+        const uint64_t NP = to_host(tot.p, s);
+        DBuf<uint64_t> pkey(NP ? NP : 1, s), phi(NP ? NP : 1, s);
+        seg_split_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(pc, NC, poff.p, pkey.p, phi.p);
+        PN_CHECK_LAUNCH();
+        R->cand_key = std::move(pkey);
+        R->cand_hi = std::move(phi);
+        NC = NP;
+    }
+    R->n_cand = NC;
     ktm.mark_at(6);
     st.candidates = NC;
     tm.mark();  // 3
@@ -2212,6 +2297,9 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     DBuf<unsigned long long> cols(3, s), fst(3, s);  // fst: filter positions, surviving ranges, columns before
     VerifyParams V{R->cand_key.p, R->cand_hi.p, NC, ref->packed.p, R->len.p, R->kk.p, R->peq.p, vcnt.p, inl.p,
                    cols.p, toff.p, nullptr, nullptr, nullptr, nullptr};
+    // the reference's segments ([start, end) pairs), or none when it is one segment [0, n)
+    const uint64_t* vseg = segmented(ref) ? ref->seg.p : nullptr;
+    const uint32_t vnseg = segmented(ref) ? ref->n_seg : 0u;
     const unsigned gv = grid_for(NC, kVerifyThreads, (unsigned)sm_count() * 32);
     DBuf<uint64_t> okey(NC ? NC : 1, s), order(NC ? NC : 1, s);
     uint64_t NT = 0;
@@ -2246,7 +2334,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         }
         PN_CUDA(record_event(kev[2], s));
         if (NC) {
-            verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
+            verify_k<false><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1, vseg, vnseg);
             PN_CHECK_LAUNCH();
         }
         PN_CUDA(record_event(kev[3], s));
@@ -2278,7 +2366,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         if (NC) {
             inline_out_k<<<grid_for(NC, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(V);
             PN_CHECK_LAUNCH();
-            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1);
+            verify_k<true><<<gv, kVerifyThreads, 0, s>>>(V, order.p, fst.p + 1, vseg, vnseg);
             PN_CHECK_LAUNCH();
         }
         st.graph_segments += seg.run() ? 1 : 0;

@@ -9,7 +9,8 @@
 // exactly at j): Myers' recurrence with a horizontal delta of +1 entering at row 0, i.e. Ph
 // shifted up with a 1 instead of a 0.  min over c of G[c] is d (the definition of D[j]); the
 // start is j - c + 1 for the largest c with G[c] = d (the leftmost start; an alignment of cost d
-// spans at most m + d bases).
+// spans at most m + d bases, and stays inside the segment of the reference that holds j, so c
+// never reaches past that segment's start).
 //
 // Hit-rank and quality.  R = the number of the read's hits (both strands) whose percent identity
 // (m - d') / m is at least the hit's, i.e. d' <= d; quality = min(-10 log10((R - 1) / n), 255)
@@ -55,7 +56,7 @@ __device__ __forceinline__ int anchored_step(uint64_t (&Pv)[W], uint64_t (&Mv)[W
 }
 
 template <int W>
-__device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64_t j, int32_t d,
+__device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64_t sa, int64_t j, int32_t d,
                               const uint32_t* __restrict__ packed, bool* ok) {
     // match masks of the reversed pattern: bit i of rev = bit m - 1 - i of the forward mask
     uint64_t eq[4][W];
@@ -78,7 +79,7 @@ __device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64
     const int lastbit = (int)((m - 1) & 63);
     int32_t score = (int32_t)m;
     int64_t best = score == d ? 0 : -1;
-    const int64_t C = (int64_t)m + d < j + 1 ? (int64_t)m + d : j + 1;
+    const int64_t C = (int64_t)m + d < j + 1 - sa ? (int64_t)m + d : j + 1 - sa;
     for (int64_t c = 1; c <= C; ++c) {
         const int64_t t = j - c + 1;
         const uint32_t b = (__ldg(packed + (t >> 4)) >> (30 - 2 * (uint32_t)(t & 15))) & 3u;
@@ -95,8 +96,8 @@ __device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64
 
 __global__ void __launch_bounds__(kPostThreads)
     start_k(peanut_device_hits H, const uint8_t* __restrict__ len, const uint64_t* __restrict__ peq,
-            const uint32_t* __restrict__ packed, uint64_t n_ref, uint32_t n_reads, uint64_t* __restrict__ start,
-            uint32_t* status) {
+            const uint32_t* __restrict__ packed, uint64_t n_ref, const uint64_t* __restrict__ seg, uint32_t n_seg,
+            uint32_t n_reads, uint64_t* __restrict__ start, uint32_t* status) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < H.n; x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t r = H.read_id[x], s = H.strand[x];
         const uint64_t j = H.end_pos[x];
@@ -105,15 +106,30 @@ __global__ void __launch_bounds__(kPostThreads)
             start[x] = ~0ull;
             continue;
         }
+        // the segment holding j: the first one ending after j
+        uint32_t l = 0, h = n_seg;
+        while (l < h) {
+            const uint32_t mid = (l + h) >> 1;
+            if (seg[2 * mid + 1] <= j)
+                l = mid + 1;
+            else
+                h = mid;
+        }
+        if (l == n_seg || seg[2 * l] > j) {  // an end in a gap
+            atomicOr(status, 1u);
+            start[x] = ~0ull;
+            continue;
+        }
+        const int64_t sa = (int64_t)seg[2 * l];
         const uint32_t m = len[r];
         const uint64_t* pq = peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords;
         bool ok = true;
         uint64_t st = 0;
         switch ((m + 63) >> 6) {
-            case 1: st = hit_start<1>(pq, m, (int64_t)j, H.dist[x], packed, &ok); break;
-            case 2: st = hit_start<2>(pq, m, (int64_t)j, H.dist[x], packed, &ok); break;
-            case 3: st = hit_start<3>(pq, m, (int64_t)j, H.dist[x], packed, &ok); break;
-            default: st = hit_start<4>(pq, m, (int64_t)j, H.dist[x], packed, &ok); break;
+            case 1: st = hit_start<1>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
+            case 2: st = hit_start<2>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
+            case 3: st = hit_start<3>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
+            default: st = hit_start<4>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
         }
         if (!ok) atomicOr(status, 2u);
         start[x] = st;
@@ -182,11 +198,11 @@ void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_de
     DBuf<uint32_t> status(1, s);
     status.zero();
     start_k<<<grid_for(n, kPostThreads, (unsigned)sm_count() * 16), kPostThreads, 0, s>>>(
-        H, R->len.p, R->peq.p, ref->packed.p, ref->n, R->n_reads, d_start, status.p);
+        H, R->len.p, R->peq.p, ref->packed.p, ref->n, ref->seg.p, ref->n_seg, R->n_reads, d_start, status.p);
     PN_CHECK_LAUNCH();
     // read ids index rb / re below: refuse the list before that if any is out of range
     PN_REQUIRE(!(to_host(status.p, s) & 1u), PEANUT_INVALID_ARG,
-               "a hit names a read, strand or end outside the batch / reference");
+               "a hit names a read, strand or end outside the batch / reference, or an end in a gap");
     DBuf<uint64_t> rb(R->n_reads, s), re(R->n_reads, s);
     rb.zero();
     re.zero();

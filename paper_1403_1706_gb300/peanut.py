@@ -108,6 +108,9 @@ def load():
         "peanut_kernel_launches": (c_uint64, []),
         "peanut_set_allocator": (st, [ALLOC_FN, RELEASE_FN, c_void_p]),
         "peanut_pack_reference": (st, [c_void_p, c_uint64, c_void_p, POINTER(c_void_p)]),
+        "peanut_pack_reference_contigs": (st, [c_void_p, c_uint64, c_void_p, c_uint32, c_uint32, c_uint64, c_void_p,
+                                               POINTER(c_void_p)]),
+        "peanut_ref_segments": (st, [c_void_p, POINTER(c_uint64), c_void_p, c_void_p]),
         "peanut_ref_length": (c_uint64, [c_void_p]),
         "peanut_index_reads": (st, [c_void_p, c_void_p, c_void_p, c_uint32, POINTER(Params), POINTER(c_void_p)]),
         "peanut_index_reads_device": (st, [c_void_p, c_void_p, c_void_p, c_uint32, c_uint64, POINTER(Params),
@@ -232,12 +235,35 @@ class ReadBatch(_Handle):
         self.n_reads = n_reads
 
 
-def pack_reference(seq, stream=None) -> Reference:
-    """peanut_pack_reference: ASCII reference (bytes or uint8 array) -> resident packed reference."""
+DEFAULT_GAP_MIN = 16
+
+
+def pack_reference(seq, stream=None, contigs=None, gap_min: int = DEFAULT_GAP_MIN, seed: int = 0) -> Reference:
+    """peanut_pack_reference (one contig) or, with `contigs` (ascending start positions, the first
+    0), peanut_pack_reference_contigs: ASCII reference (bytes or uint8 array; A/C/G/T/N in either
+    case) -> resident packed reference.  N takes a seeded base; runs of >= gap_min Ns and contig
+    boundaries cut the reference into segments no hit leaves."""
     a = _host_u8(seq)
     out = c_void_p()
-    _check(load().peanut_pack_reference(a.ctypes.data, a.size, _stream_ptr(stream), ctypes.byref(out)))
+    if contigs is None and gap_min == DEFAULT_GAP_MIN and seed == 0:
+        _check(load().peanut_pack_reference(a.ctypes.data, a.size, _stream_ptr(stream), ctypes.byref(out)))
+    else:
+        cs = np.ascontiguousarray(np.asarray([0] if contigs is None else contigs, dtype=np.uint64))
+        _check(load().peanut_pack_reference_contigs(a.ctypes.data, a.size, cs.ctypes.data, cs.size, int(gap_min),
+                                                    int(seed) & (2 ** 64 - 1), _stream_ptr(stream),
+                                                    ctypes.byref(out)))
     return Reference(out.value)
+
+
+def ref_segments(ref: Reference) -> np.ndarray:
+    """peanut_ref_segments: the reference's segments as an (s, 2) uint64 array of [start, end)."""
+    n = c_uint64()
+    _check(load().peanut_ref_segments(ref.ptr, ctypes.byref(n), None, None))
+    st = np.empty(n.value, np.uint64)
+    en = np.empty(n.value, np.uint64)
+    if n.value:
+        _check(load().peanut_ref_segments(ref.ptr, ctypes.byref(n), st.ctypes.data, en.ctypes.data))
+    return np.stack([st, en], axis=1)
 
 
 INDEX_LAYOUTS = {"interleaved": 0, "sampled_s": 1, "w64": 2}

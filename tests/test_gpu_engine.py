@@ -209,7 +209,7 @@ def test_engine_release_with_work_in_flight(gpu, world, expected):
 def test_engine_bad_submission_fails_alone(gpu, world, expected):
     ref, R, subs = world
     bad_seq = subs[2].seq.copy()
-    bad_seq[5] = ord("N")
+    bad_seq[5] = ord("X")
     E = gpu.Engine(R, k_permille=50, executors=2)
     try:
         t0 = E.submit(subs[1].seq, subs[1].offsets, "all")

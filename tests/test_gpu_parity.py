@@ -280,7 +280,7 @@ def test_edge_cases(gpu):
 def test_invalid_inputs_rejected(gpu):
     R = gpu.pack_reference(b"ACGT" * 100)
     with pytest.raises(gpu.PeanutError) as e:
-        gpu.index_reads(R, b"ACGNACGTACGTACGT", [0, 16], 4, k=0)
+        gpu.index_reads(R, b"ACGXACGTACGTACGT", [0, 16], 4, k=0)
     assert e.value.status == 1
     with pytest.raises(gpu.PeanutError) as e:  # t = 16 + 1 - 8 * 3 < 1
         gpu.index_reads(R, b"ACGTACGTACGTACGT", [0, 16], 8, k=2)
