@@ -71,6 +71,18 @@ typedef struct {
     uint8_t* dist;
 } peanut_device_hits;
 
+/* Proper pairs of a paired-end batch (peanut_pair_hits), in device memory owned by the object;
+ * release with peanut_free. */
+typedef struct {
+    uint64_t n;
+    uint64_t* i1;     /* index in the hit list of the mate-1 hit */
+    uint64_t* i2;     /* index in the hit list of the mate-2 hit */
+    uint32_t* score;  /* summed identity (m1 - d1) / m1 + (m2 - d2) / m2 as its numerator over m1 m2:
+                         (m1 - d1) m2 + (m2 - d2) m1 */
+    uint32_t* rank;   /* proper pairs of the fragment scoring at least as high (>= 1) */
+    uint8_t* mapq;    /* min(floor(-10 log10((rank - 1) / n) + 1e-9), 255), 255 at rank 1 */
+} peanut_device_pairs;
+
 /* Per-batch parameters. */
 typedef struct {
     uint32_t q;          /* q-gram length, 1..16 (Section "The q-group index"; the paper uses 16) */
@@ -357,6 +369,30 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
  *   ms: kernel time; ops: instructions executed (kinds 0-4), 64-bit word-columns (5, 6) or loads
  *   (7, 8), over all threads; grid / block: the launch shape.
  * Errors: INVALID_ARG (NULL pointer, iters = 0, unknown kind), NO_MEMORY, CUDA_ERROR. */
+/* Pairs the mates of a paired-end batch (Section "Postprocessing": mates are paired, and in
+ * paired-end mode the percent identities of properly paired hits are summed to form strata).
+ * Reads 2p and 2p + 1 of the batch are the two mates of fragment p, read from its two ends
+ * (forward-reverse).  Hit u of mate 1 and hit x of mate 2 are a proper pair when they lie on
+ * opposite strands, in the same contig, and the fragment from the strand-0 hit's start to the
+ * strand-1 hit's end is min_insert .. max_insert bases long.  Pairs are listed in (mate-1 hit,
+ * mate-2 hit) order with their score, rank and quality (peanut_device_pairs); mode 1 keeps each
+ * fragment's best-scoring pairs (the paired best stratum), mode 0 all of them.
+ *   hits: a device hit list of this batch in the order peanut_map_device gives (grouped by read,
+ *     each read's hits by strand, then end); d_start: device, hits->n alignment starts
+ *     (peanut_annotate_hits).  The batch's stream is used and synchronized.
+ *   out: receives a new pairs object.
+ * Errors: INVALID_ARG (bad object, NULL pointer, odd number of reads, min_insert = 0 or
+ *         max_insert < min_insert, hits out of order, a start after its end), NO_MEMORY,
+ *         CUDA_ERROR. */
+peanut_status peanut_pair_hits(const peanut_ref* ref, const peanut_reads* batch, const peanut_device_hits* hits,
+                               const uint64_t* d_start, uint32_t min_insert, uint32_t max_insert, int mode,
+                               peanut_device_pairs** out);
+
+/* Copies a pairs object to caller-owned host arrays of pairs->n entries each (any may be NULL).
+ * Synchronizes stream.  Errors: INVALID_ARG (bad object), CUDA_ERROR. */
+peanut_status peanut_download_pairs(const peanut_device_pairs* pairs, void* stream, uint64_t* i1, uint64_t* i2,
+                                    uint32_t* score, uint32_t* rank, uint8_t* mapq);
+
 peanut_status peanut_int_peak(uint32_t kind, uint32_t iters, void* stream, double* ms, uint64_t* ops,
                               uint32_t* grid, uint32_t* block);
 

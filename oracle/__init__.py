@@ -58,6 +58,9 @@ def _load():
         lib.oracle_prepare_reference.restype = c.c_int64
         lib.oracle_prepare_reference.argtypes = [vp, c.c_int64, vp, c.c_int64, c.c_int64, c.c_uint64, vp, vp,
                                                  c.c_int64]
+        lib.oracle_pair_hits.restype = c.c_int64
+        lib.oracle_pair_hits.argtypes = [vp, vp, vp, vp, vp, c.c_int64, vp, c.c_int64, vp, c.c_int64, c.c_int64,
+                                         c.c_int64, c.c_int64, c.c_int, vp, vp, vp, vp, vp, c.c_int64]
         lib.oracle_prepare_reads.restype = c.c_int
         lib.oracle_prepare_reads.argtypes = [vp, vp, c.c_int64, c.c_uint64, vp]
         lib.oracle_hits_count.restype = c.c_int64
@@ -304,3 +307,36 @@ def lemma_threshold(m: int, q: int, k: int) -> int:
 def sort_hits(h: np.ndarray) -> np.ndarray:
     """Hits in (read, strand, end) order."""
     return h[np.lexsort((h["end"], h["strand"], h["read"]))]
+
+
+PAIR_DTYPE = np.dtype([("i1", "<i8"), ("i2", "<i8"), ("score", "<i8"), ("rank", "<u4"), ("mapq", "<i4")])
+
+
+def pair_hits(hits: np.ndarray, starts, offsets, n_ref: int, min_insert: int, max_insert: int,
+              mode: str = "all", contig_starts=(0,)) -> np.ndarray:
+    """Proper pairs of mates 2p / 2p + 1 (Section "Postprocessing", paired-end mode; readings in
+    oracle_pair_hits): hit indices i1 (mate 1) and i2 (mate 2), summed-identity numerator score,
+    rank and quality; mode "all" or "best"."""
+    hr = np.ascontiguousarray(hits["read"], np.uint32)
+    hs = np.ascontiguousarray(hits["strand"], np.uint8)
+    he = np.ascontiguousarray(hits["end"], np.int64)
+    hd = np.ascontiguousarray(hits["dist"], np.int32)
+    st = np.ascontiguousarray(starts, np.int64)
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    cs = np.ascontiguousarray(np.asarray(contig_starts, dtype=np.int64))
+    cap = max(16, hr.size)
+    while True:
+        o1, o2, sc = (np.empty(cap, np.int64) for _ in range(3))
+        rk = np.empty(cap, np.uint32)
+        mq = np.empty(cap, np.int32)
+        got = _load().oracle_pair_hits(_p(hr), _p(hs), _p(he), _p(st), _p(hd), hr.size, offs.ctypes.data,
+                                       offs.size - 1, cs.ctypes.data, cs.size, int(n_ref), int(min_insert),
+                                       int(max_insert), {"all": 0, "best": 1}[mode], o1.ctypes.data, o2.ctypes.data,
+                                       sc.ctypes.data, rk.ctypes.data, mq.ctypes.data, cap)
+        if got < 0:
+            raise ValueError("bad input to pair_hits")
+        if got <= cap:
+            out = np.empty(got, PAIR_DTYPE)
+            out["i1"], out["i2"], out["score"], out["rank"], out["mapq"] = o1[:got], o2[:got], sc[:got], rk[:got], mq[:got]
+            return out
+        cap = int(got)

@@ -818,3 +818,97 @@ int oracle_annotate(const char* R, int64_t n, const char* reads, const int64_t* 
     }
     return 0;
 }
+
+/* ---- paired-end mates (Section "Postprocessing") ----
+ *
+ * The paper pairs mates during postprocessing and, in paired-end mode, sums the percent
+ * identities of properly paired hits when it forms strata.  Readings (the paper does not define
+ * a proper pair): reads 2p and 2p + 1 of a batch are the two mates of fragment p, sequenced from
+ * its two ends (forward-reverse); hits x of mate 1 and y of mate 2 are properly paired when they
+ * lie on opposite strands, in the same contig, and the fragment they span, from the start of
+ * the strand-0 hit to the end of the strand-1 hit, is min_insert .. max_insert bases long.  The
+ * pair's score is its summed percent identity (m1 - d1) / m1 + (m2 - d2) / m2, compared exactly
+ * through the numerator (m1 - d1) m2 + (m2 - d2) m1 over the common denominator m1 m2.  Its rank
+ * is the number of proper pairs of the fragment scoring at least as high, and its quality the
+ * formula of oracle_annotate with that rank.  mode 0 keeps every proper pair, 1 the fragment's
+ * best-scoring ones.
+ *
+ * Hits (grouped by read, ascending) with their starts; contig_starts[0..ncontig) as in
+ * oracle_prepare_reference; n = reference length.  Pairs go to the out arrays in (fragment,
+ * mate-1 hit, mate-2 hit) order.  Returns the number of pairs (filling at most cap), or -1 on
+ * bad input. */
+static int64_t contig_of(const int64_t* cs, int64_t nc, int64_t p) {
+    int64_t c = 0;
+    while (c + 1 < nc && cs[c + 1] <= p) c++;
+    return c;
+}
+
+int64_t oracle_pair_hits(const uint32_t* hr, const uint8_t* hs, const int64_t* he, const int64_t* hst,
+                         const int32_t* hd, int64_t nh, const int64_t* offs, int64_t nreads, const int64_t* cs,
+                         int64_t ncontig, int64_t n, int64_t min_insert, int64_t max_insert, int mode, int64_t* o1,
+                         int64_t* o2, int64_t* oscore, uint32_t* orank, int32_t* omapq, int64_t cap) {
+    if (nreads % 2 || min_insert < 1 || max_insert < min_insert || ncontig < 1) return -1;
+    for (int64_t x = 1; x < nh; x++)
+        if (hr[x] < hr[x - 1]) return -1;
+    int64_t np = 0, x = 0;
+    while (x < nh) {
+        const int64_t p = hr[x] / 2;
+        int64_t a1 = x, b1 = x; /* mate-1 hits [a1, b1), mate-2 hits [b1, b2) */
+        while (b1 < nh && hr[b1] == 2 * p) b1++;
+        int64_t b2 = b1;
+        while (b2 < nh && hr[b2] == 2 * p + 1) b2++;
+        if (hr[x] == 2 * p + 1) { /* no mate-1 hits */
+            a1 = b1 = x;
+        }
+        const int64_t m1 = offs[2 * p + 1] - offs[2 * p], m2 = offs[2 * p + 2] - offs[2 * p + 1];
+        const int64_t first = np;
+        int64_t best = -1;
+        for (int64_t u = a1; u < b1; u++)
+            for (int64_t v = b1; v < b2; v++) {
+                if (hs[u] == hs[v]) continue;
+                if (contig_of(cs, ncontig, he[u]) != contig_of(cs, ncontig, he[v])) continue;
+                const int64_t fwd = hs[u] == 0 ? u : v, rev = hs[u] == 0 ? v : u;
+                const int64_t ins = he[rev] - hst[fwd] + 1;
+                if (ins < min_insert || ins > max_insert) continue;
+                const int64_t sc = (m1 - hd[u]) * m2 + (m2 - hd[v]) * m1;
+                if (np < cap) {
+                    o1[np] = u;
+                    o2[np] = v;
+                    oscore[np] = sc;
+                }
+                if (sc > best) best = sc;
+                np++;
+            }
+        if (np <= cap) {
+            /* ranks and qualities over the fragment's pairs, then the best stratum */
+            int64_t w = first;
+            for (int64_t z = first; z < np; z++) {
+                uint32_t c = 0;
+                for (int64_t t = first; t < np; t++) c += oscore[t] >= oscore[z] ? 1u : 0u;
+                orank[z] = c;
+                if (c <= 1) {
+                    omapq[z] = 255;
+                } else {
+                    double qv = -10.0 * log10((double)(c - 1) / (double)n);
+                    int64_t qi = (int64_t)floor(qv + 1e-9);
+                    omapq[z] = (int32_t)(qi < 0 ? 0 : qi > 255 ? 255 : qi);
+                }
+            }
+            if (mode == 1) {
+                for (int64_t z = first; z < np; z++)
+                    if (oscore[z] == best) {
+                        o1[w] = o1[z];
+                        o2[w] = o2[z];
+                        oscore[w] = oscore[z];
+                        orank[w] = orank[z];
+                        omapq[w] = omapq[z];
+                        w++;
+                    }
+                np = w;
+            }
+        }
+        x = b2 > b1 ? b2 : b1;
+        if (x == a1) x++; /* defensive: always advance */
+    }
+    return np;
+}

@@ -486,6 +486,13 @@ void peanut_free(void* obj) {
         delete dh;
         return;
     }
+    DevicePairs* dp = reinterpret_cast<DevicePairs*>(static_cast<char*>(obj) - offsetof(DevicePairs, p));
+    if (dp->magic == kMagicDPairs) {
+        cudaStreamSynchronize(dp->stream);
+        dp->magic = 0;
+        delete dp;
+        return;
+    }
 }
 
 peanut_status peanut_index_sizes(const peanut_reads* R, uint64_t* n_groups, uint64_t* n_distinct,
@@ -636,6 +643,41 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
         PN_REQUIRE(hits->n == 0 || (hits->read_id && hits->strand && hits->end_pos && hits->dist && d_start && d_rank &&
                                     d_mapq), PEANUT_INVALID_ARG, "NULL array");
         annotate_hits(ref, reads, *hits, d_start, d_rank, d_mapq);
+    });
+}
+
+static DevicePairs* dp_of(const peanut_device_pairs* p) {
+    return reinterpret_cast<DevicePairs*>(reinterpret_cast<char*>(const_cast<peanut_device_pairs*>(p)) -
+                                          offsetof(DevicePairs, p));
+}
+
+peanut_status peanut_pair_hits(const peanut_ref* ref, const peanut_reads* reads, const peanut_device_hits* hits,
+                               const uint64_t* d_start, uint32_t min_insert, uint32_t max_insert, int mode,
+                               peanut_device_pairs** out) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && reads && reads->magic == kMagicReads && hits && out,
+                   PEANUT_INVALID_ARG, "bad reference, batch, hit list or NULL out");
+        PN_REQUIRE(reads->ref == ref, PEANUT_INVALID_ARG, "the batch was indexed against another reference");
+        PN_REQUIRE(hits->n == 0 || (hits->read_id && hits->strand && hits->end_pos && hits->dist && d_start),
+                   PEANUT_INVALID_ARG, "NULL array");
+        PN_REQUIRE(mode == 0 || mode == 1, PEANUT_INVALID_ARG, "mode must be 0 (all) or 1 (best stratum)");
+        *out = nullptr;
+        *out = &pair_hits(ref, reads, *hits, d_start, min_insert, max_insert, mode)->p;
+    });
+}
+
+peanut_status peanut_download_pairs(const peanut_device_pairs* pairs, void* stream, uint64_t* i1, uint64_t* i2,
+                                    uint32_t* score, uint32_t* rank, uint8_t* mapq) {
+    return guarded([&] {
+        PN_REQUIRE(pairs && dp_of(pairs)->magic == kMagicDPairs, PEANUT_INVALID_ARG, "bad pairs object");
+        const uint64_t n = pairs->n;
+        cudaStream_t s = (cudaStream_t)stream;
+        if (n && i1) PN_CUDA(cudaMemcpyAsync(i1, pairs->i1, n * 8, cudaMemcpyDeviceToHost, s));
+        if (n && i2) PN_CUDA(cudaMemcpyAsync(i2, pairs->i2, n * 8, cudaMemcpyDeviceToHost, s));
+        if (n && score) PN_CUDA(cudaMemcpyAsync(score, pairs->score, n * 4, cudaMemcpyDeviceToHost, s));
+        if (n && rank) PN_CUDA(cudaMemcpyAsync(rank, pairs->rank, n * 4, cudaMemcpyDeviceToHost, s));
+        if (n && mapq) PN_CUDA(cudaMemcpyAsync(mapq, pairs->mapq, n, cudaMemcpyDeviceToHost, s));
+        PN_CUDA(cudaStreamSynchronize(s));
     });
 }
 

@@ -198,6 +198,8 @@ void pack_reference(peanut_ref* ref, const char* host_seq, uint64_t len, const u
             seg.push_back(b);
         }
     }
+    ref->contig.alloc(cs.size(), s);
+    PN_CUDA(cudaMemcpyAsync(ref->contig.p, cs.data(), cs.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     ref->n_gaps = gaps;
     ref->n_seg = (uint32_t)(seg.size() / 2);
     PN_REQUIRE(seg.size() / 2 < (1ull << 31), PEANUT_UNSUPPORTED, "too many segments");

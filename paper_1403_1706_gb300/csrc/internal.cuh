@@ -28,6 +28,7 @@ constexpr uint32_t kMagicReads = 0x50524453u;  // 'PRDS'
 constexpr uint32_t kMagicHits = 0x50484954u;   // 'PHIT'
 constexpr uint32_t kMagicDHits = 0x50444854u;  // 'PDHT'
 constexpr uint32_t kMagicEngine = 0x50454E47u; // 'PENG'
+constexpr uint32_t kMagicDPairs = 0x50445052u; // 'PDPR'
 
 // device status bits (written by kernels, read at synchronization points)
 enum : uint32_t {
@@ -240,6 +241,7 @@ struct peanut_ref {
     // No alignment leaves its segment; seg holds [start, end) pairs, ascending.
     uint64_t n_seed = 0;                 // seeds the replacement of unknown bases (reference and reads)
     uint32_t n_contigs = 1;
+    pn::DBuf<uint64_t> contig;           // contig starts on the device (the first 0)
     uint64_t n_gaps = 0;
     std::vector<uint64_t> hseg;          // host copy, 2 per segment
     pn::DBuf<uint64_t> seg;              // device copy
@@ -303,6 +305,15 @@ struct DeviceHits {
     pn::Allocator a;  // made the four arrays
 };
 
+struct DevicePairs {
+    uint32_t magic = pn::kMagicDPairs;
+    peanut_device_pairs p = {};
+    cudaStream_t stream = nullptr;
+    pn::DBuf<uint64_t> i1, i2;
+    pn::DBuf<uint32_t> score, rank;
+    pn::DBuf<uint8_t> mapq;
+};
+
 namespace pn {
 // api.cu: page-locked host blocks for results, kept for reuse after they are freed
 void* host_block_alloc(size_t bytes, size_t* got, bool* pinned);
@@ -341,6 +352,8 @@ void free_device_hits(DeviceHits* H);
 void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
                        const uint64_t* txt_off, int32_t* out, cudaStream_t s);
 // post.cu: start, hit-rank and mapping quality of a batch's hits (device arrays of H.n entries)
+DevicePairs* pair_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
+                       uint32_t min_insert, uint32_t max_insert, int mode);
 void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, uint64_t* d_start,
                    uint32_t* d_rank, uint8_t* d_mapq);
 // peak.cu: integer issue-rate microbenchmark (timed with CUDA events on s)

@@ -217,4 +217,253 @@ void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_de
     PN_REQUIRE(!(st & 4u), PEANUT_INVALID_ARG, "hits are not grouped by ascending read");
 }
 
+// ---- paired-end mates (Section "Postprocessing") ------------------------------------------
+//
+// In paired-end mode the paper pairs mates and sums the percent identities of properly paired
+// hits when it forms strata.  Here reads 2p and 2p + 1 of a batch are the mates of fragment p,
+// read from its two ends (forward-reverse).  Hits u of mate 1 and x of mate 2 are properly paired
+// when they lie on opposite strands, in the same contig, and the fragment from the strand-0 hit's
+// start to the strand-1 hit's end is min_insert .. max_insert bases long.  A pair's score is the
+// numerator (m1 - d1) m2 + (m2 - d2) m1 of its summed identity over the fragment's common
+// denominator m1 m2 (exact comparison); its rank is the number of the fragment's pairs scoring at
+// least as high, its quality the hit quality formula with that rank.  Best-stratum mode keeps
+// each fragment's top-scoring pairs.  Pairs are listed in (mate-1 hit, mate-2 hit) order.
+
+constexpr int kScoreBits = 17;  // scores < 2 * 255 * 255 < 2^17
+
+struct PairIn {
+    peanut_device_hits H;
+    const uint64_t* start;
+    const uint64_t* rb;  // per read: its hits [rb, re)
+    const uint64_t* re;
+    const uint8_t* len;
+    const uint8_t* kk;
+    const uint64_t* contig;  // contig starts, ascending, the first 0
+    uint32_t n_contig;
+    uint32_t n_reads;
+    int64_t min_ins, max_ins;
+};
+
+// Index of the contig holding position p.
+__device__ __forceinline__ uint32_t contig_index(const uint64_t* __restrict__ cs, uint32_t nc, uint64_t p) {
+    uint32_t l = 0, h = nc;
+    while (h - l > 1) {
+        const uint32_t mid = (l + h) >> 1;
+        if (cs[mid] <= p)
+            l = mid;
+        else
+            h = mid;
+    }
+    return l;
+}
+
+// The proper pairs of mate-1 hit u (none for a mate-2 hit): counted, or written from slot o on.
+template <bool kWrite>
+__device__ uint32_t pairs_of(const PairIn& P, uint64_t u, uint64_t o, uint64_t* o1, uint64_t* o2, uint32_t* osc) {
+    const uint32_t r = P.H.read_id[u];
+    if ((r & 1u) || r + 1 >= P.n_reads) return 0;
+    const uint64_t a = P.rb[r + 1], b = P.re[r + 1];
+    if (b <= a) return 0;
+    const uint32_t su = P.H.strand[u];
+    // mate 2's hits: its strand-0 hits, then its strand-1 hits, each by end
+    uint64_t l = a, h = b;
+    while (l < h) {
+        const uint64_t mid = (l + h) >> 1;
+        if (P.H.strand[mid] < 1)
+            l = mid + 1;
+        else
+            h = mid;
+    }
+    const uint64_t va = su ? a : l, vb = su ? l : b;
+    const int64_t m1 = P.len[r], m2 = P.len[r + 1], k2 = P.kk[r + 1];
+    const int64_t eu = (int64_t)P.H.end_pos[u], stu = (int64_t)P.start[u];
+    // ends that can close a fragment of allowed length: u forward, the mate's end lies in
+    // [start + min - 1, start + max - 1]; u reverse, the mate's start lies in
+    // [end - max + 1, end - min + 1] and its end at most m2 + k2 - 1 after its start
+    const int64_t lo_end = su == 0 ? stu + P.min_ins - 1 : eu - P.max_ins + 1;
+    const int64_t hi_end = su == 0 ? stu + P.max_ins - 1 : eu - P.min_ins + m2 + k2;
+    l = va;
+    h = vb;
+    while (l < h) {
+        const uint64_t mid = (l + h) >> 1;
+        if ((int64_t)P.H.end_pos[mid] < lo_end)
+            l = mid + 1;
+        else
+            h = mid;
+    }
+    const uint32_t cu = contig_index(P.contig, P.n_contig, (uint64_t)eu);
+    const int64_t d1 = P.H.dist[u];
+    uint32_t c = 0;
+    for (uint64_t x = l; x < vb && (int64_t)P.H.end_pos[x] <= hi_end; ++x) {
+        const int64_t ev = (int64_t)P.H.end_pos[x];
+        const int64_t ins = su == 0 ? ev - stu + 1 : eu - (int64_t)P.start[x] + 1;
+        if (ins < P.min_ins || ins > P.max_ins) continue;
+        if (contig_index(P.contig, P.n_contig, (uint64_t)ev) != cu) continue;
+        if (kWrite) {
+            o1[o + c] = u;
+            o2[o + c] = x;
+            osc[o + c] = (uint32_t)((m1 - d1) * m2 + (m2 - (int64_t)P.H.dist[x]) * m1);
+        }
+        ++c;
+    }
+    return c;
+}
+
+struct PairCount {
+    PairIn P;
+    __device__ uint64_t operator()(uint64_t u) const { return pairs_of<false>(P, u, 0, nullptr, nullptr, nullptr); }
+};
+
+__global__ void pair_write_k(PairIn P, const uint64_t* __restrict__ off, uint64_t* o1, uint64_t* o2, uint32_t* osc) {
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < P.H.n; u += (uint64_t)gridDim.x * blockDim.x)
+        (void)pairs_of<true>(P, u, off[u], o1, o2, osc);
+}
+
+// The hit list must be grouped by read, each read's hits in (strand, end) order, every start at
+// or before its end (status bit 8 otherwise).
+__global__ void pair_check_k(peanut_device_hits H, const uint64_t* __restrict__ start, uint32_t* status) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < H.n; x += (uint64_t)gridDim.x * blockDim.x) {
+        bool bad = start[x] > H.end_pos[x];
+        if (x > 0 && H.read_id[x - 1] == H.read_id[x])
+            bad |= !(H.strand[x - 1] < H.strand[x] || (H.strand[x - 1] == H.strand[x] && H.end_pos[x - 1] < H.end_pos[x]));
+        if (bad) atomicOr(status, 8u);
+    }
+}
+
+// Sort keys: fragment, then score descending.
+__global__ void pair_keys_k(const uint32_t* __restrict__ read_id, const uint64_t* __restrict__ i1,
+                            const uint32_t* __restrict__ score, uint64_t n, uint64_t* key, uint64_t* val) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        key[t] = ((uint64_t)(read_id[i1[t]] >> 1) << kScoreBits) | (uint64_t)((1u << kScoreBits) - 1u - score[t]);
+        val[t] = t;
+    }
+}
+
+// Over the sorted keys: rank = pairs of the fragment up to the last one of equal score; keep =
+// the pair has the fragment's best score.
+__global__ void pair_rank_k(const uint64_t* __restrict__ key, const uint64_t* __restrict__ val, uint64_t n,
+                            double n_ref, uint32_t* rank, uint8_t* mapq, uint8_t* keep) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[t], f = k >> kScoreBits << kScoreBits;
+        uint64_t l = 0, h = t;  // first key of the fragment
+        while (l < h) {
+            const uint64_t mid = (l + h) >> 1;
+            if (key[mid] < f)
+                l = mid + 1;
+            else
+                h = mid;
+        }
+        const uint64_t f0 = l;
+        l = t + 1;
+        h = n;  // one past the last equal key
+        while (l < h) {
+            const uint64_t mid = (l + h) >> 1;
+            if (key[mid] <= k)
+                l = mid + 1;
+            else
+                h = mid;
+        }
+        const uint32_t R = (uint32_t)(l - f0);
+        const uint64_t x = val[t];
+        rank[x] = R;
+        uint8_t q = 255;
+        if (R > 1) {
+            const double v = floor(-10.0 * log10((double)(R - 1) / n_ref) + 1e-9);
+            q = (uint8_t)(v < 0.0 ? 0.0 : v > 255.0 ? 255.0 : v);
+        }
+        mapq[x] = q;
+        keep[x] = key[f0] == k;
+    }
+}
+
+struct PairOut {
+    uint64_t *i1, *i2;
+    uint32_t *score, *rank;
+    uint8_t* mapq;
+};
+
+__global__ void pair_keep_k(PairOut in, const uint8_t* __restrict__ keep, const uint64_t* __restrict__ off, uint64_t n,
+                            PairOut out) {
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        if (!keep[t]) continue;
+        const uint64_t o = off[t];
+        out.i1[o] = in.i1[t];
+        out.i2[o] = in.i2[t];
+        out.score[o] = in.score[t];
+        out.rank[o] = in.rank[t];
+        out.mapq[o] = in.mapq[t];
+    }
+}
+
+DevicePairs* pair_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
+                       uint32_t min_insert, uint32_t max_insert, int mode) {
+    cudaStream_t s = R->stream;
+    PN_REQUIRE(R->n_reads % 2 == 0, PEANUT_INVALID_ARG, "a paired batch holds an even number of reads (%u)",
+               R->n_reads);
+    PN_REQUIRE(min_insert >= 1 && max_insert >= min_insert, PEANUT_INVALID_ARG, "insert range %u..%u", min_insert,
+               max_insert);
+    std::unique_ptr<DevicePairs> out(new DevicePairs());
+    out->stream = s;
+    const uint64_t n = H.n;
+    const unsigned g = grid_for(n, 256, (unsigned)sm_count() * 16);
+    DBuf<uint32_t> status(1, s);
+    status.zero();
+    DBuf<uint64_t> rb(R->n_reads, s), re(R->n_reads, s);
+    rb.zero();
+    re.zero();
+    if (n) {
+        read_ranges_k<<<g, 256, 0, s>>>(H.read_id, n, rb.p, re.p, status.p);
+        PN_CHECK_LAUNCH();
+        pair_check_k<<<g, 256, 0, s>>>(H, d_start, status.p);
+        PN_CHECK_LAUNCH();
+    }
+    const uint32_t st = to_host(status.p, s);
+    PN_REQUIRE(!(st & 4u), PEANUT_INVALID_ARG, "hits are not grouped by ascending read");
+    PN_REQUIRE(!(st & 8u), PEANUT_INVALID_ARG, "a read's hits are not in (strand, end) order, or a start lies after its end");
+    const PairIn P{H, d_start, rb.p, re.p, R->len.p, R->kk.p, ref->contig.p, ref->n_contigs, R->n_reads,
+                   (int64_t)min_insert, (int64_t)max_insert};
+    DBuf<uint64_t> off(n ? n : 1, s), tot(1, s);
+    exclusive_scan(PairCount{P}, ArrayOut<uint64_t>{off.p}, n, tot.p, s);
+    const uint64_t np = to_host(tot.p, s);
+    PairOut a{};
+    DBuf<uint64_t> i1(np ? np : 1, s), i2(np ? np : 1, s);
+    DBuf<uint32_t> sc(np ? np : 1, s), rk(np ? np : 1, s);
+    DBuf<uint8_t> mq(np ? np : 1, s), keep(np ? np : 1, s);
+    a = PairOut{i1.p, i2.p, sc.p, rk.p, mq.p};
+    if (np) {
+        pair_write_k<<<g, 256, 0, s>>>(P, off.p, i1.p, i2.p, sc.p);
+        PN_CHECK_LAUNCH();
+        DBuf<uint64_t> key(np, s), val(np, s), kt(np, s), vt(np, s);
+        const unsigned gp = grid_for(np, 256, (unsigned)sm_count() * 16);
+        pair_keys_k<<<gp, 256, 0, s>>>(H.read_id, i1.p, sc.p, np, key.p, val.p);
+        PN_CHECK_LAUNCH();
+        radix_sort_pairs(key.p, val.p, kt.p, vt.p, np, kScoreBits + 23, s);
+        pair_rank_k<<<gp, 256, 0, s>>>(key.p, val.p, np, (double)ref->n, rk.p, mq.p, keep.p);
+        PN_CHECK_LAUNCH();
+    }
+    uint64_t nk = np;
+    if (mode == 1 && np) {
+        DBuf<uint64_t> koff(np, s);
+        exclusive_scan(ArrayIn<uint8_t>{keep.p}, ArrayOut<uint64_t>{koff.p}, np, tot.p, s);
+        nk = to_host(tot.p, s);
+        out->i1.alloc(nk ? nk : 1, s);
+        out->i2.alloc(nk ? nk : 1, s);
+        out->score.alloc(nk ? nk : 1, s);
+        out->rank.alloc(nk ? nk : 1, s);
+        out->mapq.alloc(nk ? nk : 1, s);
+        pair_keep_k<<<grid_for(np, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(
+            a, keep.p, koff.p, np, PairOut{out->i1.p, out->i2.p, out->score.p, out->rank.p, out->mapq.p});
+        PN_CHECK_LAUNCH();
+    } else {
+        out->i1 = std::move(i1);
+        out->i2 = std::move(i2);
+        out->score = std::move(sc);
+        out->rank = std::move(rk);
+        out->mapq = std::move(mq);
+    }
+    PN_CUDA(cudaStreamSynchronize(s));
+    out->p = peanut_device_pairs{nk, out->i1.p, out->i2.p, out->score.p, out->rank.p, out->mapq.p};
+    return out.release();
+}
+
 }  // namespace pn

@@ -45,6 +45,11 @@ class DeviceHitsStruct(Structure):
                 ("dist", c_void_p)]
 
 
+class DevicePairsStruct(Structure):
+    _fields_ = [("n", c_uint64), ("i1", c_void_p), ("i2", c_void_p), ("score", c_void_p), ("rank", c_void_p),
+                ("mapq", c_void_p)]
+
+
 class MapStats(Structure):
     _fields_ = [("hits", c_uint64), ("candidates", c_uint64), ("candidate_columns", c_uint64),
                 ("results", c_uint64), ("lowcx_reads", c_uint64), ("lowcx_ranges", c_uint64),
@@ -130,6 +135,10 @@ def load():
                                                   c_void_p]),
         "peanut_annotate_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_void_p, c_void_p]),
         "peanut_index_reference": (st, [c_void_p, c_uint32, c_void_p]),
+        "peanut_pair_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_uint32, c_uint32, c_int,
+                                  POINTER(POINTER(DevicePairsStruct))]),
+        "peanut_download_pairs": (st, [POINTER(DevicePairsStruct), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p]),
         "peanut_int_peak": (st, [c_uint32, c_uint32, c_void_p, POINTER(ctypes.c_double), POINTER(c_uint64),
                                  POINTER(c_uint32), POINTER(c_uint32)]),
         "peanut_engine_create": (st, [c_void_p, POINTER(EngineParams), POINTER(c_void_p)]),
@@ -399,6 +408,30 @@ def annotate_hits(ref: Reference, batch: ReadBatch, hits: DeviceHits):
     _check(load().peanut_annotate_hits(ref.ptr, batch.ptr, hits._hp, start.data_ptr(), rank.data_ptr(),
                                        mapq.data_ptr()))
     return start[:n], rank[:n], mapq[:n]
+
+
+PAIR_DTYPE = np.dtype([("i1", "<u8"), ("i2", "<u8"), ("score", "<u4"), ("rank", "<u4"), ("mapq", "u1")])
+
+
+def pair_hits(ref: Reference, batch: ReadBatch, hits: DeviceHits, start, min_insert: int, max_insert: int,
+              mode: str = "all", stream=None) -> np.ndarray:
+    """peanut_pair_hits + peanut_download_pairs: the proper pairs of mates 2p / 2p + 1 of a
+    paired batch, given its device hit list and their starts (a torch int64 device tensor from
+    annotate_hits), as a host structured array (i1, i2, score, rank, mapq)."""
+    hp = POINTER(DevicePairsStruct)()
+    _check(load().peanut_pair_hits(ref.ptr, batch.ptr, hits._hp, start.data_ptr() if hits.n else None,
+                                   int(min_insert), int(max_insert), MODES[mode], ctypes.byref(hp)))
+    try:
+        n = int(hp.contents.n)
+        out = np.empty(n, PAIR_DTYPE)
+        cols = [np.empty(n, out.dtype[f]) for f in out.dtype.names]
+        if n:
+            _check(load().peanut_download_pairs(hp, _stream_ptr(stream), *[c.ctypes.data for c in cols]))
+        for f, c in zip(out.dtype.names, cols):
+            out[f] = c
+        return out
+    finally:
+        load().peanut_free(ctypes.cast(hp, c_void_p))
 
 
 def kernel_launches() -> int:

@@ -12,12 +12,20 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
+def _kvec(offs, k=None, k_permille=None):
+    lens = np.diff(np.asarray(offs, np.int64))
+    return np.full(lens.size, k) if k is not None else (lens * k_permille + 999) // 1000
+
+
 def _check(gpu, R, ref, seq, offs, q, mode, **kw):
     B = gpu.index_reads(R, seq, offs, q, **kw)
     dh = gpu.map_device(R, B, mode)
     h = dh.to_numpy()
+    # the oracle annotates its own hit list, which the GPU's must equal first
+    want = oracle.map_filter(ref, seq, offs, _kvec(offs, kw.get("k"), kw.get("k_permille")), q, mode)
+    assert np.array_equal(h, want)
     start, rank, mapq = gpu.annotate_hits(R, B, dh)
-    ws, wr, wq = oracle.annotate(ref, seq, offs, h)
+    ws, wr, wq = oracle.annotate(ref, seq, offs, want)
     assert np.array_equal(start.cpu().numpy(), ws)
     assert np.array_equal(rank.cpu().numpy().astype(np.uint32), wr)
     assert np.array_equal(mapq.cpu().numpy().astype(np.int32), wq)
