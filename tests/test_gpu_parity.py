@@ -289,7 +289,7 @@ def test_invalid_inputs_rejected(gpu):
         gpu.index_reads(R, b"A" * 300, [0, 300], 8, k=2)
     assert e.value.status == 1
     with pytest.raises(gpu.PeanutError) as e:
-        gpu.pack_reference(b"ACGTN")
+        gpu.pack_reference(b"ACGTR")
     assert e.value.status == 1
     with pytest.raises(gpu.PeanutError) as e:
         gpu.index_reads(R, b"ACGT", [0, 4], 20, k=0)
