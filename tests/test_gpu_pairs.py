@@ -66,10 +66,11 @@ def _paired(seed, n_frag, lens=(100,)):
 def case(gpu):
     ref, contigs, seq, offs = _paired(7, 1500, lens=(100, 120, 150))
     R = gpu.pack_reference(ref, contigs=contigs)
+    _, seg = oracle.prepare_reference(ref, contigs)  # no alignment spans two contigs
     want = {}
     for mode in ("all", "best"):
-        h = oracle.map_filter(ref, seq, offs, K, Q, mode)  # the stratum the pairs are built from
-        st, _, _ = oracle.annotate(ref, seq, offs, h)
+        h = oracle.map_filter(ref, seq, offs, K, Q, mode, segments=seg)  # the stratum the pairs come from
+        st, _, _ = oracle.annotate(ref, seq, offs, h, segments=seg)
         want[mode] = h, st, {pm: oracle.pair_hits(h, st, offs, ref.size, MIN_INS, MAX_INS, pm, contigs)
                              for pm in ("all", "best")}
     return ref, contigs, seq, offs, R, want
