@@ -95,6 +95,8 @@ def parse_args():
     ap.add_argument("--no-refindex", action="store_true",
                     help="plain: skip the reference-side q-group index comparison arm")
     ap.add_argument("--serve-requests", type=int, default=30, help="plain: requests of the serving leg")
+    ap.add_argument("--qstudy-configs", default=None,
+                    help="qstudy: the settings to run, q:stride:layout joined by commas (default: all 13)")
     return ap.parse_args()
 
 
@@ -475,6 +477,8 @@ def run_qstudy(args, rank, world, local):
                (16, 16, "sampled_s"), (16, 16, "w64"), (16, 4, "interleaved"), (15, 1, "interleaved"),
                (15, 3, "interleaved"), (15, 15, "interleaved"), (14, 4, "interleaved"), (14, 14, "interleaved"),
                (13, 13, "interleaved")]
+    if args.qstudy_configs:
+        configs = [(int(a), int(b), c) for a, b, c in (x.split(":") for x in args.qstudy_configs.split(","))]
     rows, ref_hits = [], None
     for q, stride, layout in configs:
         def once():
