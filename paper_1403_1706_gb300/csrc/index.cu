@@ -920,10 +920,11 @@ void index_reads(peanut_reads* R, const char* d_seqs, const uint64_t* d_offsets,
         default: scatter_qgrams_k<2><<<gq, 256, 0, s>>>(tcode.p, tpay.p, nqg, IV, R->Sp.p, cnt.p, R->O.p); break;
     }
     PN_CHECK_LAUNCH();
-    // prefilter for the reference scan: about 6 bits per distinct code, at most 64 MB so that it
-    // stays resident in the 129 MB L2 while the index itself is probed in HBM
+    // prefilter for the reference scan: 16 to 32 bits per distinct code (four bits of a 64-bit
+    // word each, so that few absent codes pass on to an 8-byte probe of the index in HBM), at
+    // most 64 MB so that it stays resident in the 129 MB L2 while the index is probed in HBM
     uint64_t words = 1024;
-    while (words < (1ull << 23) && words * 64 < R->n_distinct * 6) words <<= 1;
+    while (words < (1ull << 23) && words * 64 < R->n_distinct * 16) words <<= 1;
     R->bloom.alloc(words, s);
     R->bloom.zero();
     R->bloom_mask = words - 1;

@@ -1816,14 +1816,21 @@ __global__ void __launch_bounds__(kFilterThreads)
             const uint32_t wn = __ldg(packed + w + 1);
             int32_t cnt = 0;
             uint32_t pc = 0;  // per-byte counts of the tracked codes in this block
+            // the word shifted by 0, 1, 2 and 3 bases: the 4-gram at base 4 j + q is byte 3 - j of
+            // the q-th shift
+            const uint32_t sh[4] = {wc, __funnelshift_l(wn, wc, 2), __funnelshift_l(wn, wc, 4),
+                                    __funnelshift_l(wn, wc, 6)};
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {  // the 4-gram starting at base u of this word
-                const uint32_t g = __funnelshift_l(wn, wc, 2 * u) >> 24;
-                cnt += (int32_t)((set[(g >> 5) * kFilterThreads] >> (g & 31)) & 1u);
-                const uint32_t xq = G4 ^ (g * 0x01010101u);  // zero bytes: tracked codes equal to g
-                const uint32_t zb = ~(((xq & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | xq) & 0x80808080u;
-                pc += zb >> 7;
-            }
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t g = __byte_perm(sh[q], 0u, 0x4440u | (uint32_t)(3 - j));
+                    const uint32_t sw = set[(g >> 5) * kFilterThreads];
+                    cnt += (int32_t)(__funnelshift_r(sw, sw, g) & 1u);  // bit g mod 32 (a rotation)
+                    const uint32_t xq = G4 ^ (g * 0x01010101u);  // zero bytes: tracked codes equal to g
+                    const uint32_t zb = ~(((xq & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | xq) & 0x80808080u;
+                    pc += zb >> 7;
+                }
             ring[(w & 31) * kFilterThreads] = (uint8_t)cnt;
             ring4[(w & 31) * kFilterThreads] = pc;
             sum += cnt;
