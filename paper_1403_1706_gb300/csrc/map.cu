@@ -1302,10 +1302,11 @@ __global__ void lcpos_k(const uint32_t* list, uint32_t n, uint32_t* lcpos) {
 }
 
 // One warp per read copies its ranges (strand 0 first) into the candidate arrays.
-__global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, const uint64_t* roff,
-                          const uint64_t* wlo, const uint64_t* whi, const uint64_t* lc_off,
-                          const uint64_t* lc_keys, const uint64_t* lc_vals, uint64_t* cand_key,
-                          uint64_t* cand_hi) {
+__global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* __restrict__ coff,
+                          const uint64_t* __restrict__ roff, const uint64_t* __restrict__ wlo,
+                          const uint64_t* __restrict__ whi, const uint64_t* __restrict__ lc_off,
+                          const uint64_t* __restrict__ lc_keys, const uint64_t* __restrict__ lc_vals,
+                          uint64_t* __restrict__ cand_key, uint64_t* __restrict__ cand_hi) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_reads; r += nw) {
@@ -1314,6 +1315,7 @@ __global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, 
         if (cc.lowcx && cc.lowcx[r]) {
             const uint32_t x = cc.lcpos[r];
             const uint32_t c0 = cc.lcnt[2 * x], c1 = cc.lcnt[2 * x + 1];
+#pragma unroll 4
             for (uint32_t j = lane; j < c0 + c1; j += 32) {
                 const uint32_t s = j < c0 ? 0 : 1;
                 const uint64_t src = lc_off[2 * x + s] + (s ? j - c0 : j);
@@ -1322,6 +1324,7 @@ __global__ void compact_k(uint32_t n_reads, CandCount cc, const uint64_t* coff, 
             }
         } else {
             const uint32_t c = cc.wcnt[2 * r] + cc.wcnt[2 * r + 1];
+#pragma unroll 4
             for (uint32_t j = lane; j < c; j += 32) {
                 cand_key[o + j] = rk | wlo[roff[r] + j];
                 cand_hi[o + j] = whi[roff[r] + j];
@@ -1878,16 +1881,17 @@ __global__ void __launch_bounds__(kFilterThreads)
 }
 
 // Work order of the verification: candidates grouped by words per column and by length (8-column
-// steps up to 4088), so that the 32 ranges of a warp take about the same number of steps.
-// Ranges the q'-gram filter removed sort last.
-constexpr int kOrderBits = 12;
+// steps up to 384 columns, 64-column steps up to 1344, longer ones together), so that the 32
+// ranges of a warp take about the same number of steps; one 8-bit key, one radix pass.  Ranges
+// the q'-gram filter removed sort last.
+constexpr int kOrderBits = 8;
 __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_t* __restrict__ cand_hi, uint64_t n,
                             const uint8_t* __restrict__ len, const uint8_t* __restrict__ kk, uint64_t* keys,
                             uint64_t* vals) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (uint64_t)gridDim.x * blockDim.x) {
         vals[x] = x;
         if (cand_hi[x] == kDeadRange) {
-            keys[x] = 1ull << 11;
+            keys[x] = 255;
             continue;
         }
         const uint64_t key = cand_key[x];
@@ -1896,9 +1900,10 @@ __global__ void order_key_k(const uint64_t* __restrict__ cand_key, const uint64_
         const uint32_t m = len[r];
         int64_t a = lo - ((int64_t)m + kk[r]) + 1;
         if (a < 0) a = 0;
-        const uint64_t cols = (uint64_t)(hi - a + 1) >> 3;
+        const uint64_t c8 = (uint64_t)(hi - a + 1) >> 3;
+        const uint64_t b = c8 < 48 ? c8 : 48 + ((c8 - 48) >> 3);
         const uint64_t w = (m + 63) >> 6;
-        keys[x] = ((w - 1) << 9) | (cols < 511 ? cols : 511);
+        keys[x] = ((w - 1) << 6) | (b < 62 ? b : 62);  // at most 254
     }
 }
 
