@@ -694,8 +694,8 @@ __global__ void bloom_set_k(const uint32_t* __restrict__ tcode, uint64_t n, uint
          x += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t c = tcode[x];
         if (c == kSentinel) continue;
-        const uint64_t h = bloom_hash(c);
-        atomicOr((unsigned long long*)(bloom + ((h >> 24) & mask)), (unsigned long long)bloom_bits(h));
+        const BloomKey bk = bloom_key(c, (uint32_t)(mask + 1));
+        atomicOr((unsigned long long*)(bloom + bk.word), ((unsigned long long)bk.hi << 32) | bk.lo);
     }
 }
 

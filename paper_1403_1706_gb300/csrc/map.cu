@@ -96,13 +96,16 @@ __device__ __forceinline__ void stage_flush2(uint64_t* sk, uint32_t* ss, uint32_
     __syncwarp();
 }
 
-template <int L>
+// kQ16: q = 16 known at compile time (the common case): constant shifts, no masks.
+template <int L, bool kQ16>
 __global__ void __launch_bounds__(kScanBlock, 4)
-    probe_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q, IndexView V,
+    probe_ref_k(const uint32_t* __restrict__ packed, uint64_t n, uint32_t q_arg, IndexView V,
                 const uint64_t* __restrict__ bloom, uint64_t bloom_mask, uint64_t* __restrict__ okey,
                 uint32_t* __restrict__ oslot, uint64_t cap, unsigned long long* n_out) {
     __shared__ uint64_t sk[kScanBlock / 32][kStageCap];
     __shared__ uint32_t ss[kScanBlock / 32][kStageCap];
+    const uint32_t q = kQ16 ? 16u : q_arg;
+    const uint32_t bloom_words = (uint32_t)(bloom_mask + 1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t scnt = 0;
     const uint64_t npos = n >= q ? n - q + 1 : 0;
@@ -125,7 +128,8 @@ __global__ void __launch_bounds__(kScanBlock, 4)
         for (int o0 = 0; o0 < 32; o0 += 8) {
             uint32_t cc[8];
             uint32_t meta[8];  // bit 0: valid, bit 1: orientation, bit 2: palindrome
-            uint64_t fw[8], fb[8];
+            uint64_t fw[8];
+            uint32_t flo[8], fhi[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int o = o0 + u;
@@ -136,14 +140,16 @@ __global__ void __launch_bounds__(kScanBlock, 4)
                 const bool valid = active && p0 + o < npos;
                 cc[u] = c;
                 meta[u] = (valid ? 1u : 0u) | (g > h ? 2u : 0u) | (g == h ? 4u : 0u);
-                const uint64_t hh = bloom_hash(c);
-                fb[u] = bloom_bits(hh);
-                fw[u] = valid ? ld_u64_policy(bloom + ((hh >> 24) & bloom_mask), keep) : 0;
+                const BloomKey bk = bloom_key(c, bloom_words);
+                flo[u] = bk.lo;
+                fhi[u] = bk.hi;
+                fw[u] = valid ? ld_u64_policy(bloom + bk.word, keep) : 0;
             }
             uint2 vv[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const bool pass = (meta[u] & 1u) && (fw[u] & fb[u]) == fb[u];
+                const bool pass = (meta[u] & 1u) && ((uint32_t)fw[u] & flo[u]) == flo[u] &&
+                                  ((uint32_t)(fw[u] >> 32) & fhi[u]) == fhi[u];
                 if constexpr (L == 0) {
                     vv[u] = pass ? ld_u32x2_policy(V.IS + (cc[u] >> 5), stream) : make_uint2(0, 0);
                 } else {
@@ -2084,7 +2090,7 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
     uint64_t pcap = (uint64_t)(1.5 * rand_present) + 2 * R->n_indexed + (1u << 20);
     uint64_t cap = (uint64_t)(1.5 * rand_hits) + 2 * R->n_indexed + (1u << 20);
     int per_sm = 0;
-    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k<0>, kScanBlock, 0));
+    PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_ref_k<0, true>, kScanBlock, 0));
     const unsigned gscan = (unsigned)sm_count() * (unsigned)(per_sm > 0 ? per_sm : 1);  // one resident wave
     const unsigned gexp = (unsigned)sm_count() * 8;  // persistent: the count of present positions is on the device
     // Sync-free stretches run as CUDA graphs on the executors of an engine created with graphs = 1;
@@ -2109,13 +2115,14 @@ DeviceHits* map_batch(const peanut_ref* ref, peanut_reads* R, int mode) {
         rcount.zero();
         if (!RX) {
             const IndexView IV = index_view(R);
+            auto launch = [&](auto k16, auto kq) {
+                (q == 16 ? k16 : kq)<<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p,
+                                                                  R->bloom_mask, pkey.p, pslot.p, pcap, nh.p);
+            };
             switch (R->layout) {
-                case 0: probe_ref_k<0><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
-                                                                     pkey.p, pslot.p, pcap, nh.p); break;
-                case 1: probe_ref_k<1><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
-                                                                     pkey.p, pslot.p, pcap, nh.p); break;
-                default: probe_ref_k<2><<<gscan, kScanBlock, 0, s>>>(ref->packed.p, n, q, IV, R->bloom.p, R->bloom_mask,
-                                                                      pkey.p, pslot.p, pcap, nh.p); break;
+                case 0: launch(probe_ref_k<0, true>, probe_ref_k<0, false>); break;
+                case 1: launch(probe_ref_k<1, true>, probe_ref_k<1, false>); break;
+                default: launch(probe_ref_k<2, true>, probe_ref_k<2, false>); break;
             }
             PN_CHECK_LAUNCH();
         }

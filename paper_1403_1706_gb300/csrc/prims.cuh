@@ -256,19 +256,30 @@ __device__ __forceinline__ uint32_t revcomp_code(uint32_t g, uint32_t q) {
     return q == 16 ? x : (x >> (32 - 2 * q)) & ((1u << (2 * q)) - 1u);
 }
 
-// Blocked Bloom filter over canonical q-gram codes: one 64-bit word per key (word index from
-// bits 24.. of a 64-bit hash), four bits in that word (bits 0..23 of the hash, 6 each).
-__device__ __forceinline__ uint64_t bloom_hash(uint32_t c) {
-    uint64_t h = (uint64_t)c * 0x9E3779B97F4A7C15ull;
-    h ^= h >> 32;
-    h *= 0xD6E8FEB86659FD93ull;
-    h ^= h >> 29;
-    return h;
-}
+// Blocked Bloom filter over canonical q-gram codes: one 64-bit word per key, two bits in each of
+// its 32-bit halves.  All 32-bit arithmetic: the code is mixed by the "lowbias32" multiply /
+// xor-shift sequence (C. Wellons' hash search); the high bits of the mix pick the word (its
+// product with the number of words, high half), and the top 20 bits of one more odd multiple of
+// the mix pick the four bit positions.  Keys that share a word differ in the low bits of the mix,
+// which reach every top bit of the multiple, so their bit positions are independent of the word.
+struct BloomKey {
+    uint32_t word;    // word index, < the number of words
+    uint32_t lo, hi;  // the key's bits in the low and high half of the word
+};
 
-__device__ __forceinline__ uint64_t bloom_bits(uint64_t h) {
-    return (1ull << (h & 63)) | (1ull << ((h >> 6) & 63)) | (1ull << ((h >> 12) & 63)) |
-           (1ull << ((h >> 18) & 63));
+__device__ __forceinline__ BloomKey bloom_key(uint32_t c, uint32_t words) {
+    uint32_t h = c;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    const uint32_t g = h * 0x9E3779B1u;
+    BloomKey k;
+    k.word = __umulhi(h, words);
+    k.lo = (1u << (g >> 27)) | (1u << ((g >> 22) & 31u));
+    k.hi = (1u << ((g >> 17) & 31u)) | (1u << ((g >> 12) & 31u));
+    return k;
 }
 
 }  // namespace pn
