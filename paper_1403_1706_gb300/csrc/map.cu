@@ -124,18 +124,33 @@ __global__ void __launch_bounds__(kScanBlock, 4)
             w1 = __ldcs(packed + p0 / 16 + 1);
             w2 = __ldcs(packed + p0 / 16 + 2);
         }
+        // q = 16: the reverse complement of the chunk's 48 bases as three words (r0 first), so
+        // that both the code and its reverse complement are one funnel shift per position
+        const uint32_t r0 = kQ16 ? revcomp_code(w2, 16) : 0u, r1 = kQ16 ? revcomp_code(w1, 16) : 0u,
+                       r2 = kQ16 ? revcomp_code(w0, 16) : 0u;
 #pragma unroll 1
         for (int o0 = 0; o0 < 32; o0 += 8) {
             uint32_t cc[8];
             uint32_t meta[8];  // bit 0: valid, bit 1: orientation, bit 2: palindrome
             uint64_t fw[8];
             uint32_t flo[8], fhi[8];
+            // bases o .. o + 15 (o = o0 + u) lie in (hiw, low) from bit 2 (o mod 16) on; their
+            // reverse complement starts at base 32 - o of the reversed chunk
+            const uint32_t hiw = o0 < 16 ? w0 : w1, low = o0 < 16 ? w1 : w2;
+            const uint32_t hir = o0 < 16 ? r1 : r0, lor = o0 < 16 ? r2 : r1;
+            const uint32_t sh0 = 2u * (uint32_t)(o0 & 15);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int o = o0 + u;
-                const uint64_t win = o < 16 ? (((uint64_t)w0 << 32) | w1) : (((uint64_t)w1 << 32) | w2);
-                const uint32_t g = (uint32_t)(win >> (64 - 2 * q - 2 * (o & 15))) & qm;
-                const uint32_t h = revcomp_code(g, q);
+                uint32_t g, h;
+                if constexpr (kQ16) {
+                    g = __funnelshift_l(low, hiw, sh0 + 2u * u);
+                    h = __funnelshift_lc(lor, hir, 32u - sh0 - 2u * u);
+                } else {
+                    const uint64_t win = o < 16 ? (((uint64_t)w0 << 32) | w1) : (((uint64_t)w1 << 32) | w2);
+                    g = (uint32_t)(win >> (64 - 2 * q - 2 * (o & 15))) & qm;
+                    h = revcomp_code(g, q);
+                }
                 const uint32_t c = g < h ? g : h;
                 const bool valid = active && p0 + o < npos;
                 cc[u] = c;
