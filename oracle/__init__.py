@@ -61,6 +61,8 @@ def _load():
         lib.oracle_pair_hits.restype = c.c_int64
         lib.oracle_pair_hits.argtypes = [vp, vp, vp, vp, vp, c.c_int64, vp, c.c_int64, vp, c.c_int64, c.c_int64,
                                          c.c_int64, c.c_int64, c.c_int, vp, vp, vp, vp, vp, c.c_int64]
+        lib.oracle_cigar.restype = c.c_int64
+        lib.oracle_cigar.argtypes = [vp, c.c_int64, vp, c.c_int64, c.c_int32, vp, vp, c.c_int64]
         lib.oracle_prepare_reads.restype = c.c_int
         lib.oracle_prepare_reads.argtypes = [vp, vp, c.c_int64, c.c_uint64, vp]
         lib.oracle_hits_count.restype = c.c_int64
@@ -340,3 +342,33 @@ def pair_hits(hits: np.ndarray, starts, offsets, n_ref: int, min_insert: int, ma
             out["i1"], out["i2"], out["score"], out["rank"], out["mapq"] = o1[:got], o2[:got], sc[:got], rk[:got], mq[:got]
             return out
         cap = int(got)
+
+
+_COMP = bytes.maketrans(b"ACGT", b"TGCA")
+
+
+def cigar(pattern, text, dist: int) -> str:
+    """The hit's alignment (readings in oracle_cigar) as an extended CIGAR string: runs of
+    '=' (match), 'X' (mismatch), 'I' (read base only), 'D' (reference base only)."""
+    P, T = _bytes(pattern), _bytes(text)
+    cap = P.size + T.size + 1
+    ops = np.empty(cap, np.uint8)
+    lens = np.empty(cap, np.int32)
+    n = _load().oracle_cigar(_p(P), P.size, _p(T), T.size, int(dist), ops.ctypes.data, lens.ctypes.data, cap)
+    if n < 0:
+        raise ValueError("the distance is not the edit distance of pattern and text")
+    return "".join(f"{int(l)}{chr(o)}" for o, l in zip(ops[:n], lens[:n]))
+
+
+def alignments(ref, seq, offsets, hits: np.ndarray, starts) -> list:
+    """The CIGAR string of every hit (pattern: the read, or its reverse complement for strand 1;
+    text: ref[start..end])."""
+    R = _bytes(ref)
+    S, offs = _reads_args(seq, offsets)
+    out = []
+    for h, st in zip(hits, starts):
+        r = int(h["read"])
+        read = bytes(S[offs[r]:offs[r + 1]])
+        pat = read[::-1].translate(_COMP) if h["strand"] else read
+        out.append(cigar(pat, bytes(R[int(st):int(h["end"]) + 1]), int(h["dist"])))
+    return out

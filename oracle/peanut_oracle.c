@@ -912,3 +912,70 @@ int64_t oracle_pair_hits(const uint32_t* hr, const uint8_t* hs, const int64_t* h
     }
     return np;
 }
+
+/* ---- the actual alignment of a hit (Section "Postprocessing") ----
+ *
+ * The paper's postprocessing "calculates the actual alignment of each hit".  Reading: the
+ * alignment of the pattern P (the read, or its reverse complement for strand 1; length m) with
+ * the n reference bases T = R[start..end] of the hit, both ends fixed, of cost dist = the hit's
+ * distance: E[i][c] = the edit distance between P[0..i) and T[0..c), E[i][0] = i, E[0][c] = c.
+ * Among the optimal alignments it takes the one traced back from (m, n) preferring, at every
+ * cell, the diagonal step (a match '=' or a mismatch 'X') when it is optimal, else a reference
+ * base against no read base ('D'), else a read base against no reference base ('I').  Output:
+ * the runs of equal operations in forward order, op codes '=', 'X', 'I', 'D' in ops[] and their
+ * lengths in lens[].  Returns the number of runs, -1 if E[m][n] != dist, -2 if more than cap. */
+int64_t oracle_cigar(const char* P, int64_t m, const char* T, int64_t n, int32_t d, char* ops, int32_t* lens,
+                     int64_t cap) {
+    if (m < 0 || n < 0 || m > (1 << 20) || n > (1 << 20)) return -1;
+    int32_t* E = (int32_t*)malloc(sizeof(int32_t) * (size_t)((m + 1) * (n + 1)));
+#define EE(i, c) E[(i) * (n + 1) + (c)]
+    for (int64_t i = 0; i <= m; i++) EE(i, 0) = (int32_t)i;
+    for (int64_t c = 0; c <= n; c++) EE(0, c) = (int32_t)c;
+    for (int64_t i = 1; i <= m; i++)
+        for (int64_t c = 1; c <= n; c++) {
+            int32_t v = EE(i - 1, c - 1) + (P[i - 1] != T[c - 1] ? 1 : 0);
+            if (EE(i, c - 1) + 1 < v) v = EE(i, c - 1) + 1;
+            if (EE(i - 1, c) + 1 < v) v = EE(i - 1, c) + 1;
+            EE(i, c) = v;
+        }
+    if (EE(m, n) != d) {
+        free(E);
+        return -1;
+    }
+    /* trace back, one operation per step, then run-length encode in forward order */
+    char* rev = (char*)malloc((size_t)(m + n + 1));
+    int64_t nr = 0, i = m, c = n;
+    while (i > 0 || c > 0) {
+        const int32_t e = EE(i, c);
+        if (i > 0 && c > 0 && EE(i - 1, c - 1) + (P[i - 1] != T[c - 1] ? 1 : 0) == e) {
+            rev[nr++] = P[i - 1] == T[c - 1] ? '=' : 'X';
+            i--;
+            c--;
+        } else if (c > 0 && EE(i, c - 1) + 1 == e) {
+            rev[nr++] = 'D';
+            c--;
+        } else {
+            rev[nr++] = 'I';
+            i--;
+        }
+    }
+#undef EE
+    int64_t runs = 0;
+    for (int64_t x = nr - 1; x >= 0; x--) {
+        if (runs > 0 && ops[runs - 1] == rev[x]) {
+            lens[runs - 1]++;
+            continue;
+        }
+        if (runs == cap) {
+            free(rev);
+            free(E);
+            return -2;
+        }
+        ops[runs] = rev[x];
+        lens[runs] = 1;
+        runs++;
+    }
+    free(rev);
+    free(E);
+    return runs;
+}
