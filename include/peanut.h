@@ -369,6 +369,28 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
  *   ms: kernel time; ops: instructions executed (kinds 0-4), 64-bit word-columns (5, 6) or loads
  *   (7, 8), over all threads; grid / block: the launch shape.
  * Errors: INVALID_ARG (NULL pointer, iters = 0, unknown kind), NO_MEMORY, CUDA_ERROR. */
+/* The actual alignment of every hit (Section "Postprocessing": the postprocessing calculates the
+ * actual alignment of each hit).  The pattern (the read, or its reverse complement for strand 1)
+ * is aligned with the reference bases start .. end of the hit, both ends fixed, at the hit's
+ * distance; among the optimal alignments the one traced back from the last cell preferring the
+ * diagonal step, then a reference-only step, then a read-only step.  Output per hit: up to
+ * ops_per_hit runs of equal operations in forward order, each encoded as length << 2 | code
+ * (0 '=' match, 1 'X' mismatch, 2 'I' read base only, 3 'D' reference base only: an extended
+ * CIGAR), and their number.  A hit of distance d has at most 2 d + 1 runs, so
+ * ops_per_hit = 2 k + 1 for the batch's largest k always suffices.
+ *   hits: a device hit list of this batch; d_start: device, hits->n alignment starts
+ *   (peanut_annotate_hits).  d_ops: device, hits->n * ops_per_hit words, caller-owned;
+ *   d_nops: device, hits->n entries.  Uses the batch's stream (synchronized); allocates a
+ *   transient band of (2 k + 1)(m + 1) 16-bit cells per thread for the dynamic programme.
+ * Errors: INVALID_ARG (bad object, NULL pointer, a hit outside the batch or reference, a start
+ *         after its end, a distance that is not the pattern's distance to those bases, more runs
+ *         than ops_per_hit), NO_MEMORY, CUDA_ERROR. */
+/* The largest error budget k among the batch's reads (0 for a bad batch). */
+uint32_t peanut_batch_max_k(const peanut_reads* batch);
+
+peanut_status peanut_hit_alignments(const peanut_ref* ref, const peanut_reads* batch, const peanut_device_hits* hits,
+                                    const uint64_t* d_start, uint32_t ops_per_hit, uint32_t* d_ops, uint16_t* d_nops);
+
 /* Pairs the mates of a paired-end batch (Section "Postprocessing": mates are paired, and in
  * paired-end mode the percent identities of properly paired hits are summed to form strata).
  * Reads 2p and 2p + 1 of the batch are the two mates of fragment p, read from its two ends

@@ -646,6 +646,23 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
     });
 }
 
+uint32_t peanut_batch_max_k(const peanut_reads* reads) {
+    return reads && reads->magic == kMagicReads ? reads->max_k : 0;
+}
+
+peanut_status peanut_hit_alignments(const peanut_ref* ref, const peanut_reads* reads, const peanut_device_hits* hits,
+                                    const uint64_t* d_start, uint32_t ops_per_hit, uint32_t* d_ops, uint16_t* d_nops) {
+    return guarded([&] {
+        PN_REQUIRE(ref && ref->magic == kMagicRef && reads && reads->magic == kMagicReads && hits, PEANUT_INVALID_ARG,
+                   "bad reference, batch or hit list");
+        PN_REQUIRE(reads->ref == ref, PEANUT_INVALID_ARG, "the batch was indexed against another reference");
+        PN_REQUIRE(ops_per_hit >= 1, PEANUT_INVALID_ARG, "ops_per_hit must be at least 1");
+        PN_REQUIRE(hits->n == 0 || (hits->read_id && hits->strand && hits->end_pos && hits->dist && d_start && d_ops &&
+                                    d_nops), PEANUT_INVALID_ARG, "NULL array");
+        hit_alignments(ref, reads, *hits, d_start, ops_per_hit, d_ops, d_nops);
+    });
+}
+
 static DevicePairs* dp_of(const peanut_device_pairs* p) {
     return reinterpret_cast<DevicePairs*>(reinterpret_cast<char*>(const_cast<peanut_device_pairs*>(p)) -
                                           offsetof(DevicePairs, p));

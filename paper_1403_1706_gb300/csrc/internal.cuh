@@ -352,6 +352,8 @@ void free_device_hits(DeviceHits* H);
 void bitvector_columns(const char* pat, const uint64_t* pat_off, uint32_t n_pat, const char* txt,
                        const uint64_t* txt_off, int32_t* out, cudaStream_t s);
 // post.cu: start, hit-rank and mapping quality of a batch's hits (device arrays of H.n entries)
+void hit_alignments(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
+                    uint32_t cap, uint32_t* d_ops, uint16_t* d_nops);
 DevicePairs* pair_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
                        uint32_t min_insert, uint32_t max_insert, int mode);
 void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, uint64_t* d_start,

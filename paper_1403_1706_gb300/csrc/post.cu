@@ -466,4 +466,128 @@ DevicePairs* pair_hits(const peanut_ref* ref, const peanut_reads* R, const peanu
     return out.release();
 }
 
+// ---- the actual alignment of each hit (Section "Postprocessing") ----------------------------
+//
+// The pattern P (the read, or its reverse complement for strand 1; length m) against the n
+// reference bases T = R[start..end], both ends fixed, at the hit's cost d: E[i][c] = the edit
+// distance of P[0..i) and T[0..c).  Every path of cost at most d stays within |c - i| <= d of the
+// main diagonal, so a DP over that band (2d + 1 cells per row) holds the full matrix's value at
+// every cell a traceback of the optimal alignment compares.  The traceback runs from (m, n) and
+// takes, at every cell, the diagonal step when it is optimal ('=' or 'X'), else a reference-only
+// step ('D'), else a read-only step ('I'); runs of equal operations are written in forward order
+// as len << 2 | code (0 '=', 1 'X', 2 'I', 3 'D').  The band lives in a per-thread scratch area of
+// the caller's call (cells interleaved across threads: cell e of thread t at e * T + t).
+constexpr int kCigarThreads = 128;
+
+__global__ void __launch_bounds__(kCigarThreads)
+    cigar_k(peanut_device_hits H, const uint64_t* __restrict__ start, const uint8_t* __restrict__ codes,
+            const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len,
+            const uint32_t* __restrict__ packed, uint32_t n_reads, uint64_t n_ref, uint16_t* __restrict__ band,
+            uint32_t band_cells, uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops,
+            uint32_t* status) {
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x, t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint16_t* B = band + t;
+    for (uint64_t x = t; x < H.n; x += T) {
+        nops[x] = 0;
+        const uint32_t r = H.read_id[x], s = H.strand[x];
+        const int64_t j = (int64_t)H.end_pos[x], st = (int64_t)start[x];
+        const int32_t d = H.dist[x];
+        if (r >= n_reads || s > 1 || (uint64_t)j >= n_ref || st < 0 || st > j) {
+            atomicOr(status, 1u);
+            continue;
+        }
+        const int32_t m = len[r], n = (int32_t)(j - st + 1), W = 2 * d + 1;
+        if (n - m > d || m - n > d || (uint64_t)(m + 1) * W > band_cells) {
+            atomicOr(status, 2u);
+            continue;
+        }
+        const uint8_t* rd = codes + base_off[r];
+        auto pat = [&](int32_t i) -> uint32_t { return s == 0 ? rd[i] : 3u - rd[m - 1 - i]; };
+        auto txt = [&](int32_t c) -> uint32_t { return ref_base(packed, (uint64_t)(st + c)); };
+        // E(i, c) for |c - i| <= d at cell i * W + (c - i + d)
+        auto at = [&](int32_t i, int32_t c) -> uint16_t& { return B[((uint64_t)i * W + (c - i + d)) * T]; };
+        for (int32_t i = 0; i <= m; ++i) {
+            const int32_t c0 = i - d > 0 ? i - d : 0, c1 = i + d < n ? i + d : n;
+            const uint32_t p = i > 0 ? pat(i - 1) : 0u;
+            for (int32_t c = c0; c <= c1; ++c) {
+                uint32_t v;
+                if (i == 0) {
+                    v = (uint32_t)c;
+                } else if (c == 0) {
+                    v = (uint32_t)i;
+                } else {
+                    v = at(i - 1, c - 1) + (p != txt(c - 1) ? 1u : 0u);
+                    if (c - 1 - i >= -d) v = min(v, at(i, c - 1) + 1u);
+                    if (c - i + 1 <= d) v = min(v, at(i - 1, c) + 1u);
+                }
+                at(i, c) = (uint16_t)v;
+            }
+        }
+        if (at(m, n) != d) {
+            atomicOr(status, 2u);
+            continue;
+        }
+        uint32_t* out = ops + x * cap;
+        uint32_t runs = 0, last = 4;
+        bool full = false;
+        int32_t i = m, c = n;
+        while (i > 0 || c > 0) {
+            const uint32_t e = at(i, c);
+            uint32_t code;
+            if (i > 0 && c > 0 && at(i - 1, c - 1) + (pat(i - 1) != txt(c - 1) ? 1u : 0u) == e) {
+                code = pat(i - 1) == txt(c - 1) ? 0u : 1u;
+                --i;
+                --c;
+            } else if (c > 0 && c - 1 - i >= -d && at(i, c - 1) + 1u == e) {
+                code = 3u;
+                --c;
+            } else {
+                code = 2u;
+                --i;
+            }
+            if (code == last) {
+                out[runs - 1] += 4u;
+            } else if (runs == cap) {
+                full = true;
+                break;
+            } else {
+                out[runs++] = 4u | code;
+                last = code;
+            }
+        }
+        if (full) {
+            atomicOr(status, 4u);
+            continue;
+        }
+        for (uint32_t a = 0, b = runs ? runs - 1 : 0; a < b; ++a, --b) {  // forward order
+            const uint32_t tmp = out[a];
+            out[a] = out[b];
+            out[b] = tmp;
+        }
+        nops[x] = (uint16_t)runs;
+    }
+}
+
+void hit_alignments(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
+                    uint32_t cap, uint32_t* d_ops, uint16_t* d_nops) {
+    cudaStream_t s = R->stream;
+    const uint64_t n = H.n;
+    if (!n) return;
+    const uint32_t W = 2 * R->max_k + 1;
+    const uint32_t cells = (R->max_len + 1) * W;
+    const unsigned g = grid_for(n, kCigarThreads, (unsigned)sm_count() * 4);
+    DBuf<uint16_t> band((uint64_t)cells * g * kCigarThreads, s);
+    DBuf<uint32_t> status(1, s);
+    status.zero();
+    cigar_k<<<g, kCigarThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p, R->n_reads,
+                                        ref->n, band.p, cells, d_ops, cap, d_nops, status.p);
+    PN_CHECK_LAUNCH();
+    const uint32_t st = to_host(status.p, s);
+    PN_REQUIRE(!(st & 1u), PEANUT_INVALID_ARG, "a hit names a read, strand or end outside the batch / reference, "
+               "or a start after its end");
+    PN_REQUIRE(!(st & 2u), PEANUT_INVALID_ARG, "a hit's distance is not the edit distance of its pattern and "
+               "reference bases from its start");
+    PN_REQUIRE(!(st & 4u), PEANUT_INVALID_ARG, "a hit's alignment has more than %u runs of operations", cap);
+}
+
 }  // namespace pn

@@ -135,6 +135,9 @@ def load():
                                                   c_void_p]),
         "peanut_annotate_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_void_p, c_void_p]),
         "peanut_index_reference": (st, [c_void_p, c_uint32, c_void_p]),
+        "peanut_batch_max_k": (c_uint32, [c_void_p]),
+        "peanut_hit_alignments": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_uint32, c_void_p,
+                                       c_void_p]),
         "peanut_pair_hits": (st, [c_void_p, c_void_p, POINTER(DeviceHitsStruct), c_void_p, c_uint32, c_uint32, c_int,
                                   POINTER(POINTER(DevicePairsStruct))]),
         "peanut_download_pairs": (st, [POINTER(DevicePairsStruct), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -408,6 +411,31 @@ def annotate_hits(ref: Reference, batch: ReadBatch, hits: DeviceHits):
     _check(load().peanut_annotate_hits(ref.ptr, batch.ptr, hits._hp, start.data_ptr(), rank.data_ptr(),
                                        mapq.data_ptr()))
     return start[:n], rank[:n], mapq[:n]
+
+
+CIGAR_OPS = "=XID"
+
+
+def hit_alignments(ref: Reference, batch: ReadBatch, hits: DeviceHits, start, ops_per_hit: int = 0):
+    """peanut_hit_alignments: the alignment of every hit as (ops, nops) torch device tensors
+    (int32 words len << 2 | code, ops_per_hit per hit; uint16 run counts stored in int16).
+    ops_per_hit 0 = 2 k + 1 for the batch's largest k."""
+    import torch
+    n = hits.n
+    cap = int(ops_per_hit) or 2 * int(load().peanut_batch_max_k(batch.ptr)) + 1
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ops = torch.empty(max(n, 1) * cap, dtype=torch.int32, device=dev)
+    nops = torch.empty(max(n, 1), dtype=torch.int16, device=dev)
+    _check(load().peanut_hit_alignments(ref.ptr, batch.ptr, hits._hp, start.data_ptr() if n else None, cap,
+                                        ops.data_ptr(), nops.data_ptr()))
+    return ops[:n * cap].view(n, cap), nops[:n]
+
+
+def cigars(ops, nops) -> list:
+    """The extended CIGAR strings of hit_alignments' output (host conversion of device arrays)."""
+    o = ops.cpu().numpy().view(np.uint32)
+    c = nops.cpu().numpy().view(np.uint16)
+    return ["".join(f"{w >> 2}{CIGAR_OPS[w & 3]}" for w in o[x, :c[x]]) for x in range(c.size)]
 
 
 PAIR_DTYPE = np.dtype([("i1", "<u8"), ("i2", "<u8"), ("score", "<u4"), ("rank", "<u4"), ("mapq", "u1")])
