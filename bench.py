@@ -81,11 +81,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-slice", type=int, default=100_000_000,
                     help="reference prefix (bp) of the CPU-baseline sample")
-    ap.add_argument("--mode", choices=["plain", "batched", "serve", "qstudy"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "batched", "serve", "qstudy", "post"], default="plain",
                     help="plain: one batch per launch sequence (the headline); batched: uneven batches of "
                          "50-250 bp reads through the engine vs the plain path; serve: a Poisson request "
                          "stream through the engine vs one request at a time; qstudy: index variants and the "
-                         "q / L2-residency trade-off on one batch")
+                         "q / L2-residency trade-off on one batch; post: the postprocessing of one batch's "
+                         "hits (starts, ranks, qualities, alignments)")
     ap.add_argument("--requests", type=int, default=None, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=None, help="serve: mean arrivals per second")
     ap.add_argument("--executors", type=int, default=2, help="engine: launches in flight")
@@ -520,6 +521,60 @@ def run_qstudy(args, rank, world, local):
     return 0
 
 
+def run_post(args, rank, world, local):
+    """The postprocessing of one 2^20-read batch of the 3.1 Gbp workload (100 bp, k = 5, all hits,
+    q = 16, stride 16, the engine's tuned setting): alignment start, hit-rank and quality
+    (peanut_annotate_hits), then the alignment of every hit (peanut_hit_alignments); the median
+    of three runs each, CUDA events on the batch's stream, hits per second."""
+    import torch
+    import synth
+    from paper_1403_1706_gb300 import peanut
+    torch.cuda.set_device(local)
+    peanut.load()
+    w = synth.WORKLOADS["human_3g1_10m"]
+    n_ref = args.ref_len or w["ref_len"]
+    ref = synth.make_reference(n_ref, 1403, w["repeat_frac"], w["tandem_frac"])
+    seed = 1706 + list(synth.WORKLOADS).index("human_3g1_10m")
+    reads = synth.make_reads(ref, args.reads or (1 << 20), seed, lengths=w["lengths"], rate_range=w["rate_range"],
+                             random_frac=w["random_frac"])
+    stream = torch.cuda.current_stream()
+    R = peanut.pack_reference(ref, stream=stream)
+    d_seq = torch.from_numpy(reads.seq).to("cuda")
+    d_off = torch.from_numpy(reads.offsets.astype(np.int64)).to("cuda")
+    B = peanut.index_reads_device(R, d_seq, d_off, 16, k=5, stride=16, stream=stream)
+    dh = peanut.map_device(R, B, "all")
+
+    def timed(fn, reps=3):
+        out, ts = None, []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, statistics.median(ts[1:])
+
+    (start, rank, mapq), ms_ann = timed(lambda: peanut.annotate_hits(R, B, dh))
+    (ops, nops), ms_cig = timed(lambda: peanut.hit_alignments(R, B, dh, start))
+    n = dh.n
+    runs = nops.cpu().numpy().view(np.uint16)
+    line = {"metric": METRIC, "mode": "post", "value": n / ((ms_ann + ms_cig) / 1e3), "unit": "hits/s",
+            "n_gpus": world, "steps": 3, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "human_3g1_10m (one batch)", "reference_bp": int(n_ref), "reads": int(reads.n),
+                       "k": 5, "q": 16, "stride": 16, "mode": "all"},
+            "hits": int(n), "ms_annotate": ms_ann, "ms_alignments": ms_cig,
+            "annotate_hits_per_s": n / (ms_ann / 1e3), "alignment_hits_per_s": n / (ms_cig / 1e3),
+            "mean_runs_per_hit": float(runs.mean()) if n else 0.0, "max_runs_per_hit": int(runs.max()) if n else 0}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dh.free()
+    B.free()
+    return 0
+
+
 def serve_stream(peanut, R, ref, n_req, rate, seed, executors, warmup, clock_gpu=None, log=None):
     """A Poisson request stream (sizes log-uniform in 10^3..10^6 reads, lengths 75-250 bp, 1-4 %
     errors, k = ceil(0.05 L), half the requests in best-stratum mode) on a resident reference.
@@ -677,6 +732,8 @@ def main():
         rc = run_qstudy(args, rank, world, local)
     elif args.mode == "serve":
         rc = run_serve(args, rank, world, local)
+    elif args.mode == "post":
+        rc = run_post(args, rank, world, local)
     else:
         rc = None
     if rc is not None:
