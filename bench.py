@@ -556,7 +556,7 @@ def run_post(args, rank, world, local):
             ts.append(e0.elapsed_time(e1))
         return out, statistics.median(ts[1:])
 
-    (start, rank, mapq), ms_ann = timed(lambda: peanut.annotate_hits(R, B, dh))
+    (start, _, _), ms_ann = timed(lambda: peanut.annotate_hits(R, B, dh))
     (ops, nops), ms_cig = timed(lambda: peanut.hit_alignments(R, B, dh, start))
     n = dh.n
     runs = nops.cpu().numpy().view(np.uint16)
