@@ -483,11 +483,13 @@ __global__ void __launch_bounds__(kCigarThreads)
     cigar_k(peanut_device_hits H, const uint64_t* __restrict__ start, const uint8_t* __restrict__ codes,
             const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len,
             const uint32_t* __restrict__ packed, uint32_t n_reads, uint64_t n_ref, uint16_t* __restrict__ band,
-            uint32_t band_cells, uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops,
-            uint32_t* status) {
+            uint32_t band_cells, const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
+            uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops, uint32_t* status) {
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x, t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint16_t* B = band + t;
-    for (uint64_t x = t; x < H.n; x += T) {
+    const uint64_t nl = *count;
+    for (uint64_t li = t; li < nl; li += T) {
+        const uint64_t x = list[li];
         nops[x] = 0;
         const uint32_t r = H.read_id[x], s = H.strand[x];
         const int64_t j = (int64_t)H.end_pos[x], st = (int64_t)start[x];
@@ -568,26 +570,215 @@ __global__ void __launch_bounds__(kCigarThreads)
     }
 }
 
+// Hits by distance class (0: d <= 3, 1: 4 <= d <= 7, 2: d >= 8), one list per class, so that
+// the lanes of a warp all work: one atomic per class and warp.
+__global__ void cigar_classify_k(const uint8_t* __restrict__ dist, uint64_t n, uint32_t* l0, uint32_t* l1, uint32_t* l2,
+                                 unsigned long long* cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; b < n;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = b + lane;
+        const int cls = x < n ? (dist[x] <= 3 ? 0 : dist[x] <= 7 ? 1 : 2) : 3;
+        uint32_t* lists[3] = {l0, l1, l2};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const unsigned bal = __ballot_sync(kFull, cls == c);
+            if (!bal) continue;
+            unsigned long long base = 0;
+            if (lane == (uint32_t)(__ffs(bal) - 1)) base = atomicAdd(cnt + c, (unsigned long long)__popc(bal));
+            base = __shfl_sync(kFull, base, __ffs(bal) - 1);
+            if (cls == c) lists[c][base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)x;
+        }
+    }
+}
+
+// The same alignment for hits of distance d with 2 d + 1 <= WB (WB = 8 or 16): the band's previous
+// and current rows live in registers (WB cells each, one per diagonal offset o = c - i + d), and
+// only the traceback direction of every cell is kept, two bits per cell, one word per row: 0 the
+// diagonal step on a match, 3 on a mismatch, 1 the reference-only step, 2 the read-only step,
+// chosen by the traceback's own preference from the final values, so the walk back reads the
+// same decisions (and needs no bases).  The direction words live in a scratch
+// area of the call, interleaved across threads (row i of thread t at i * T + t), which leaves the
+// occupancy to the registers.  Hits of other distances are left to the other kernels.
+constexpr int kBandThreads = 64;
+
+template <int WB>
+__global__ void __launch_bounds__(kBandThreads)
+    cigar_band_k(peanut_device_hits H, const uint64_t* __restrict__ start, const uint8_t* __restrict__ codes,
+                 const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len,
+                 const uint32_t* __restrict__ packed, uint32_t n_reads, uint64_t n_ref,
+                 const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
+                 uint32_t* __restrict__ dirs_all, uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops,
+                 uint32_t* status) {
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t* dirs = dirs_all + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nl = *count;
+    for (uint64_t li = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = list[li];
+        const int32_t d = H.dist[x];
+        nops[x] = 0;
+        const uint32_t r = H.read_id[x], s = H.strand[x];
+        const int64_t j = (int64_t)H.end_pos[x], st = (int64_t)start[x];
+        if (r >= n_reads || s > 1 || (uint64_t)j >= n_ref || st < 0 || st > j) {
+            atomicOr(status, 1u);
+            continue;
+        }
+        const int32_t m = len[r], n = (int32_t)(j - st + 1);
+        if (n - m > d || m - n > d) {
+            atomicOr(status, 2u);
+            continue;
+        }
+        const uint8_t* rd = codes + base_off[r];
+        auto pat = [&](int32_t i) -> uint32_t { return s == 0 ? rd[i] : 3u - rd[m - 1 - i]; };
+        // 16 reference bases starting at position p, first base most significant (a window that
+        // starts before position 0 is shifted so that its bases keep their places; those before
+        // 0, and those past the hit's end, are never used)
+        auto bases16 = [&](int64_t p) -> uint32_t {
+            const uint64_t q = p < 0 ? 0 : (uint64_t)p;
+            const uint32_t w0 = __ldg(packed + (q >> 4)), w1 = __ldg(packed + (q >> 4) + 1);
+            const uint32_t w = __funnelshift_l(w1, w0, 2u * (uint32_t)(q & 15));
+            return p < 0 ? w >> (2 * (uint32_t)(-p)) : w;
+        };
+        constexpr uint32_t kInf = 0xFFFFu;
+        uint32_t prev[WB], cur[WB];
+        // row 0: E(0, c) = c for c = o - d >= 0
+        uint32_t wdir = 0;
+#pragma unroll
+        for (int o = 0; o < WB; ++o) {
+            const int32_t c = o - d;
+            prev[o] = (o < 2 * d + 1 && c >= 0 && c <= n) ? (uint32_t)c : kInf;
+            wdir |= 1u << (2 * o);  // reference-only steps along row 0
+        }
+        dirs[0] = wdir;
+        // row i needs read base i - 1 and the text bases c - 1 = i - d - 1 + o of its cells (first
+        // base most significant); both are loaded one row ahead
+        uint32_t p_next = m > 0 ? pat(0) : 0u, tw_next = bases16(st - d);
+        for (int32_t i = 1; i <= m; ++i) {
+            const uint32_t p = p_next, tw = tw_next;
+            if (i < m) {
+                p_next = pat(i);
+                tw_next = bases16(st + i - d);
+            }
+            wdir = 0;
+#pragma unroll
+            for (int o = 0; o < WB; ++o) {
+                const int32_t c = i - d + o;
+                uint32_t v = kInf, dir = 0;
+                if (o < 2 * d + 1 && c >= 0 && c <= n) {
+                    if (c == 0) {
+                        v = (uint32_t)i;
+                        dir = 2;
+                    } else {
+                        const uint32_t mis = p != ((tw >> (30 - 2 * o)) & 3u) ? 1u : 0u;
+                        const uint32_t dg = prev[o] + mis;
+                        const uint32_t lf = o > 0 ? cur[o - 1] + 1u : kInf;
+                        const uint32_t up = o + 1 < WB ? prev[o + 1] + 1u : kInf;
+                        v = min(dg, min(lf, up));
+                        dir = dg == v ? 3u * mis : (lf == v ? 1u : 2u);
+                    }
+                }
+                cur[o] = v;
+                wdir |= dir << (2 * o);
+            }
+            dirs[(uint64_t)i * T] = wdir;
+#pragma unroll
+            for (int o = 0; o < WB; ++o) prev[o] = cur[o];
+        }
+        // E(m, n) sits at offset n - m + d of the last row
+        uint32_t em = kInf;
+#pragma unroll
+        for (int o = 0; o < WB; ++o)
+            if (o == n - m + d) em = prev[o];
+        if (em != (uint32_t)d) {
+            atomicOr(status, 2u);
+            continue;
+        }
+        uint32_t* out = ops + x * cap;
+        uint32_t runs = 0, last = 4;
+        bool full = false;
+        int32_t i = m, c = n;
+        while (i > 0 || c > 0) {
+            const uint32_t dir = (dirs[(uint64_t)i * T] >> (2 * (c - i + d))) & 3u;
+            uint32_t code;
+            if (dir == 0 || dir == 3) {  // the diagonal step: 0 a match, 3 a mismatch
+                code = dir == 0 ? 0u : 1u;
+                --i;
+                --c;
+            } else if (dir == 1) {
+                code = 3u;
+                --c;
+            } else {
+                code = 2u;
+                --i;
+            }
+            if (code == last) {
+                out[runs - 1] += 4u;
+            } else if (runs == cap) {
+                full = true;
+                break;
+            } else {
+                out[runs++] = 4u | code;
+                last = code;
+            }
+        }
+        if (full) {
+            atomicOr(status, 4u);
+            continue;
+        }
+        for (uint32_t a = 0, b = runs ? runs - 1 : 0; a < b; ++a, --b) {
+            const uint32_t tmp = out[a];
+            out[a] = out[b];
+            out[b] = tmp;
+        }
+        nops[x] = (uint16_t)runs;
+    }
+}
+
 void hit_alignments(const peanut_ref* ref, const peanut_reads* R, const peanut_device_hits& H, const uint64_t* d_start,
                     uint32_t cap, uint32_t* d_ops, uint16_t* d_nops) {
     cudaStream_t s = R->stream;
     const uint64_t n = H.n;
     if (!n) return;
-    const uint32_t W = 2 * R->max_k + 1;
-    const uint32_t cells = (R->max_len + 1) * W;
-    const unsigned g = grid_for(n, kCigarThreads, (unsigned)sm_count() * 4);
-    DBuf<uint16_t> band((uint64_t)cells * g * kCigarThreads, s);
     DBuf<uint32_t> status(1, s);
     status.zero();
-    cigar_k<<<g, kCigarThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p, R->n_reads,
-                                        ref->n, band.p, cells, d_ops, cap, d_nops, status.p);
+    // distances 0..3 and 4..7: the register band (8 and 16 diagonals); 8 and more: the scratch band
+    PN_REQUIRE(n < (1ull << 32), PEANUT_UNSUPPORTED, "more than 2^32 - 1 hits in one call");
+    DBuf<uint32_t> l0(n, s), l1(n, s), l2(n, s);
+    DBuf<unsigned long long> cnt(3, s);
+    cnt.zero();
+    cigar_classify_k<<<grid_for(n, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(H.dist, n, l0.p, l1.p, l2.p, cnt.p);
     PN_CHECK_LAUNCH();
+    const unsigned gb = grid_for(n, kBandThreads, (unsigned)sm_count() * 16);
+    DBuf<uint32_t> dirs((uint64_t)(R->max_len + 1) * gb * kBandThreads, s);
+    cigar_band_k<8><<<gb, kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
+                                                R->n_reads, ref->n, l0.p, cnt.p, dirs.p, d_ops, cap, d_nops, status.p);
+    PN_CHECK_LAUNCH();
+    if (R->max_k >= 4) {
+        cigar_band_k<16><<<gb, kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
+                                                     R->n_reads, ref->n, l1.p, cnt.p + 1, dirs.p, d_ops, cap, d_nops,
+                                                     status.p);
+        PN_CHECK_LAUNCH();
+    }
+    if (R->max_k >= 8) {
+        const uint32_t W = 2 * R->max_k + 1;
+        const uint32_t cells = (R->max_len + 1) * W;
+        const unsigned g = grid_for(n, kCigarThreads, (unsigned)sm_count() * 4);
+        DBuf<uint16_t> band((uint64_t)cells * g * kCigarThreads, s);
+        cigar_k<<<g, kCigarThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p, R->n_reads,
+                                            ref->n, band.p, cells, l2.p, cnt.p + 2, d_ops, cap, d_nops, status.p);
+        PN_CHECK_LAUNCH();
+    }
     const uint32_t st = to_host(status.p, s);
+    unsigned long long nc[3];
+    PN_CUDA(cudaMemcpyAsync(nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
     PN_REQUIRE(!(st & 1u), PEANUT_INVALID_ARG, "a hit names a read, strand or end outside the batch / reference, "
                "or a start after its end");
     PN_REQUIRE(!(st & 2u), PEANUT_INVALID_ARG, "a hit's distance is not the edit distance of its pattern and "
                "reference bases from its start");
     PN_REQUIRE(!(st & 4u), PEANUT_INVALID_ARG, "a hit's alignment has more than %u runs of operations", cap);
+    PN_REQUIRE(!((R->max_k < 4 && nc[1]) || (R->max_k < 8 && nc[2])), PEANUT_INVALID_ARG,
+               "a hit's distance exceeds the batch's largest k (%u)", R->max_k);
 }
 
 }  // namespace pn

@@ -88,3 +88,36 @@ def test_too_few_ops_per_hit_is_refused(gpu):
     o1, o2 = ops.cpu().numpy(), ops2.cpu().numpy()
     assert all(np.array_equal(o1[x, :n[x]], o2[x, :n[x]]) for x in range(n.size))
     B.free()
+
+
+def test_every_distance_class_and_the_reference_ends(gpu):
+    """Reads of 200 bases with 0 to 10 edits (k = 10), placed at the very start and end of the
+    reference as well as inside it, so that distances 0-3, 4-7 and 8-10 (the three band widths of
+    the kernels) all occur, and bands that begin before position 0 or end at the last base."""
+    rng = np.random.default_rng(31)
+    ref = synth.make_reference(20_000, 32)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    reads = []
+    for x in range(300):
+        p = 0 if x % 5 == 0 else (ref.size - 200 if x % 5 == 1 else int(rng.integers(0, ref.size - 200)))
+        r = list(ref[p:p + 200])
+        for _ in range(x % 11):
+            y = int(rng.integers(0, len(r)))
+            op = rng.random()
+            if op < 0.5:
+                r[y] = acgt[(list(acgt).index(r[y]) + 1) % 4]
+            elif op < 0.75:
+                r.insert(y, acgt[int(rng.integers(0, 4))])
+            else:
+                del r[y]
+        reads.append(np.array(r[:200], np.uint8))
+    offs = np.concatenate([[0], np.cumsum([r.size for r in reads])]).astype(np.int64)
+    seq = np.concatenate(reads)
+    R = gpu.pack_reference(ref)
+    got = _check(gpu, R, ref, seq, offs, 16, "all", k=10)
+    h = oracle.map_filter(ref, seq, offs, 10, 16, "all")
+    d = h["dist"]
+    assert (d <= 3).any() and ((d >= 4) & (d <= 7)).any() and (d >= 8).any(), np.bincount(d)
+    st, _, _ = oracle.annotate(ref, seq, offs, h)
+    assert (st == 0).any() and (h["end"] == ref.size - 1).any()
+    assert len(got) == len(h)
