@@ -17,6 +17,7 @@
 // for a reference of n positions, 255 when R = 1, the integer part taken after adding 1e-9 (so
 // that ratios at exact powers of ten give their integer), clamped at 0.
 #include "prims.cuh"
+#include <algorithm>
 
 namespace pn {
 
@@ -570,30 +571,80 @@ __global__ void __launch_bounds__(kCigarThreads)
     }
 }
 
-// Hits by distance class (0: d <= 3, 1: 4 <= d <= 7, 2: d >= 8), one list per class, so that
-// the lanes of a warp all work: one atomic per class and warp.
-__global__ void cigar_classify_k(const uint8_t* __restrict__ dist, uint64_t n, uint32_t* l0, uint32_t* l1, uint32_t* l2,
-                                 unsigned long long* cnt) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint64_t b = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~31ull; b < n;
-         b += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t x = b + lane;
-        const int cls = x < n ? (dist[x] <= 3 ? 0 : dist[x] <= 7 ? 1 : 2) : 3;
-        uint32_t* lists[3] = {l0, l1, l2};
+// Hits by distance class (d = 0 .. 7 each a class, 8 and more the last), one list per class in
+// hit order, so that the lanes of a warp all run the same band and neighbouring lanes mostly align
+// the same read.  Block b owns the hits [b * chunk, (b + 1) * chunk): a count pass writes its
+// count of every class (cnt[class * blocks + b]), the host turns them into offsets in class-major
+// order, and a fill pass writes every block's hits of each class from its offset on, tile by tile,
+// in hit order.
+constexpr int kCigarClasses = 9;
+constexpr int kClassifyThreads = 256;
+
+__device__ __forceinline__ uint32_t cigar_class(uint8_t d) {
+    return d < kCigarClasses - 1 ? d : kCigarClasses - 1;
+}
+
+__global__ void __launch_bounds__(kClassifyThreads)
+    cigar_count_k(const uint8_t* __restrict__ dist, uint64_t n, uint64_t chunk, uint32_t* __restrict__ cnt) {
+    const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    uint32_t c[kCigarClasses];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const unsigned bal = __ballot_sync(kFull, cls == c);
-            if (!bal) continue;
-            unsigned long long base = 0;
-            if (lane == (uint32_t)(__ffs(bal) - 1)) base = atomicAdd(cnt + c, (unsigned long long)__popc(bal));
-            base = __shfl_sync(kFull, base, __ffs(bal) - 1);
-            if (cls == c) lists[c][base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)x;
-        }
+    for (int z = 0; z < kCigarClasses; ++z) c[z] = 0;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += kClassifyThreads) {
+        const uint32_t k = cigar_class(dist[x]);
+#pragma unroll
+        for (int z = 0; z < kCigarClasses; ++z) c[z] += k == (uint32_t)z ? 1u : 0u;
+    }
+    __shared__ uint32_t part[kClassifyThreads / 32][kCigarClasses];
+#pragma unroll
+    for (int z = 0; z < kCigarClasses; ++z) {
+        const uint32_t t = __reduce_add_sync(kFull, c[z]);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5][z] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < kCigarClasses) {
+        uint32_t t = 0;
+        for (int w = 0; w < kClassifyThreads / 32; ++w) t += part[w][threadIdx.x];
+        cnt[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
 }
 
-// The same alignment for hits of distance d with 2 d + 1 <= WB (WB = 8 or 16): the band's previous
-// and current rows live in registers (WB cells each, one per diagonal offset o = c - i + d), and
+__global__ void __launch_bounds__(kClassifyThreads)
+    cigar_fill_k(const uint8_t* __restrict__ dist, uint64_t n, uint64_t chunk, const uint32_t* __restrict__ off,
+                 uint32_t* __restrict__ list) {
+    const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    __shared__ uint32_t base[kCigarClasses];
+    __shared__ uint32_t wcnt[kClassifyThreads / 32][kCigarClasses];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < kCigarClasses) base[threadIdx.x] = off[(uint64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    for (uint64_t t0 = lo; t0 < hi; t0 += kClassifyThreads) {
+        const uint64_t x = t0 + threadIdx.x;
+        const uint32_t k = x < hi ? cigar_class(dist[x]) : (uint32_t)kCigarClasses;
+        uint32_t rank = 0;
+#pragma unroll
+        for (int z = 0; z < kCigarClasses; ++z) {
+            const unsigned bal = __ballot_sync(kFull, k == (uint32_t)z);
+            if (lane == 0) wcnt[w][z] = __popc(bal);
+            if (k == (uint32_t)z) rank = __popc(bal & ((1u << lane) - 1u));
+        }
+        __syncthreads();
+        if (k < kCigarClasses) {
+            uint32_t at = base[k] + rank;
+            for (uint32_t v = 0; v < w; ++v) at += wcnt[v][k];
+            list[at] = (uint32_t)x;
+        }
+        __syncthreads();
+        if (threadIdx.x < kCigarClasses) {
+            uint32_t t = 0;
+            for (int v = 0; v < kClassifyThreads / 32; ++v) t += wcnt[v][threadIdx.x];
+            base[threadIdx.x] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// The same alignment for hits of distance D (0 to 7, one instance each): the band's previous and
+// current rows live in registers (2 D + 1 cells each, one per diagonal offset o = c - i + D), and
 // only the traceback direction of every cell is kept, two bits per cell, one word per row: 0 the
 // diagonal step on a match, 3 on a mismatch, 1 the reference-only step, 2 the read-only step,
 // chosen by the traceback's own preference from the final values, so the walk back reads the
@@ -602,7 +653,7 @@ __global__ void cigar_classify_k(const uint8_t* __restrict__ dist, uint64_t n, u
 // occupancy to the registers.  Hits of other distances are left to the other kernels.
 constexpr int kBandThreads = 64;
 
-template <int WB>
+template <int D>
 __global__ void __launch_bounds__(kBandThreads)
     cigar_band_k(peanut_device_hits H, const uint64_t* __restrict__ start, const uint8_t* __restrict__ codes,
                  const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len,
@@ -613,9 +664,10 @@ __global__ void __launch_bounds__(kBandThreads)
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     uint32_t* dirs = dirs_all + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nl = *count;
+    constexpr int WB = 2 * D + 1;
+    constexpr int32_t d = D;
     for (uint64_t li = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = list[li];
-        const int32_t d = H.dist[x];
         nops[x] = 0;
         const uint32_t r = H.read_id[x], s = H.strand[x];
         const int64_t j = (int64_t)H.end_pos[x], st = (int64_t)start[x];
@@ -640,55 +692,100 @@ __global__ void __launch_bounds__(kBandThreads)
             return p < 0 ? w >> (2 * (uint32_t)(-p)) : w;
         };
         constexpr uint32_t kInf = 0xFFFFu;
-        uint32_t prev[WB], cur[WB];
+        // the band's row, updated in place: before cell o of row i is written, row[o] and
+        // row[o + 1] still hold row i - 1 (the diagonal and the up neighbours) and row[o - 1]
+        // already holds row i (the left neighbour)
+        uint32_t row[WB];
         // row 0: E(0, c) = c for c = o - d >= 0
         uint32_t wdir = 0;
 #pragma unroll
         for (int o = 0; o < WB; ++o) {
             const int32_t c = o - d;
-            prev[o] = (o < 2 * d + 1 && c >= 0 && c <= n) ? (uint32_t)c : kInf;
+            row[o] = (c >= 0 && c <= n) ? (uint32_t)c : kInf;
             wdir |= 1u << (2 * o);  // reference-only steps along row 0
         }
         dirs[0] = wdir;
-        // row i needs read base i - 1 and the text bases c - 1 = i - d - 1 + o of its cells (first
-        // base most significant); both are loaded one row ahead
-        uint32_t p_next = m > 0 ? pat(0) : 0u, tw_next = bases16(st - d);
-        for (int32_t i = 1; i <= m; ++i) {
-            const uint32_t p = p_next, tw = tw_next;
-            if (i < m) {
-                p_next = pat(i);
-                tw_next = bases16(st + i - d);
-            }
-            wdir = 0;
-#pragma unroll
-            for (int o = 0; o < WB; ++o) {
-                const int32_t c = i - d + o;
-                uint32_t v = kInf, dir = 0;
-                if (o < 2 * d + 1 && c >= 0 && c <= n) {
-                    if (c == 0) {
-                        v = (uint32_t)i;
-                        dir = 2;
+        // row i needs read base i - 1 and the 2 d + 1 text bases from position st + i - 1 - d on
+        // (first base most significant).  Rows whose window starts at or after position 0 take
+        // it from a sliding pair of packed words (w0, w1) with the next word (w2) loaded 16 rows
+        // ahead; the first rows of a band that starts before position 0 load a shifted window.
+        int64_t q = st - d;  // the window start of row i (row 1 first)
+        uint32_t w0 = 0, w1 = 0, w2 = 0;
+        bool slid = false;
+        uint32_t p_next = m > 0 ? pat(0) : 0u;
+        for (int32_t i = 1; i <= m; ++i, ++q) {
+            const uint32_t p = p_next;
+            if (i < m) p_next = pat(i);
+            uint32_t tw;
+            if (q < 0) {
+                tw = bases16(q);
+            } else {
+                const uint32_t sh = (uint32_t)q & 15u;
+                if (!slid || sh == 0) {
+                    if (!slid) {
+                        const uint32_t* pw = packed + (q >> 4);
+                        w0 = __ldg(pw);
+                        w1 = __ldg(pw + 1);
+                        w2 = __ldg(pw + 2);
+                        slid = true;
                     } else {
-                        const uint32_t mis = p != ((tw >> (30 - 2 * o)) & 3u) ? 1u : 0u;
-                        const uint32_t dg = prev[o] + mis;
-                        const uint32_t lf = o > 0 ? cur[o - 1] + 1u : kInf;
-                        const uint32_t up = o + 1 < WB ? prev[o + 1] + 1u : kInf;
-                        v = min(dg, min(lf, up));
-                        dir = dg == v ? 3u * mis : (lf == v ? 1u : 2u);
+                        w0 = w1;
+                        w1 = w2;
+                        w2 = __ldg(packed + (q >> 4) + 2);
                     }
                 }
-                cur[o] = v;
-                wdir |= dir << (2 * o);
+                tw = __funnelshift_l(w1, w0, 2u * sh);
+            }
+            wdir = 0;
+            if (i > d && i + d <= n) {
+                // every cell of the row lies inside the rectangle (1 <= c <= n), so its value is
+                // its diagonal neighbour a or a + 1: a + 1 exactly when the bases differ and
+                // neither the left nor the up neighbour is below a.  The direction follows the
+                // traceback's preference: the diagonal when it is optimal (a match, or a
+                // mismatch with value a + 1), else the reference-only step when the left
+                // neighbour is a - 1, else the read-only step.
+                const uint32_t x = tw ^ (p * 0x55555555u);
+                const uint32_t mm = (x | (x >> 1)) & 0x55555555u;  // bit 30 - 2o: cell o's bases differ
+#pragma unroll
+                for (int o = 0; o < WB; ++o) {
+                    const uint32_t av = row[o];
+                    const uint32_t lf = o > 0 ? row[o - 1] : kInf;
+                    const uint32_t up = o + 1 < WB ? row[o + 1] : kInf;
+                    const bool mis = (mm >> (30 - 2 * o)) & 1u;
+                    const bool ge = lf >= av && up >= av;
+                    const uint32_t dir = !mis ? 0u : (ge ? 3u : (lf < av ? 1u : 2u));
+                    row[o] = av + (mis && ge ? 1u : 0u);
+                    wdir |= dir << (2 * o);
+                }
+            } else {
+#pragma unroll
+                for (int o = 0; o < WB; ++o) {
+                    const int32_t c = i - d + o;
+                    uint32_t v = kInf, dir = 0;
+                    if (c >= 0 && c <= n) {
+                        if (c == 0) {
+                            v = (uint32_t)i;
+                            dir = 2;
+                        } else {
+                            const uint32_t mis = p != ((tw >> (30 - 2 * o)) & 3u) ? 1u : 0u;
+                            const uint32_t dg = row[o] + mis;
+                            const uint32_t lf = o > 0 ? row[o - 1] + 1u : kInf;
+                            const uint32_t up = o + 1 < WB ? row[o + 1] + 1u : kInf;
+                            v = min(dg, min(lf, up));
+                            dir = dg == v ? 3u * mis : (lf == v ? 1u : 2u);
+                        }
+                    }
+                    row[o] = v;
+                    wdir |= dir << (2 * o);
+                }
             }
             dirs[(uint64_t)i * T] = wdir;
-#pragma unroll
-            for (int o = 0; o < WB; ++o) prev[o] = cur[o];
         }
         // E(m, n) sits at offset n - m + d of the last row
         uint32_t em = kInf;
 #pragma unroll
         for (int o = 0; o < WB; ++o)
-            if (o == n - m + d) em = prev[o];
+            if (o == n - m + d) em = row[o];
         if (em != (uint32_t)d) {
             atomicOr(status, 2u);
             continue;
@@ -741,44 +838,73 @@ void hit_alignments(const peanut_ref* ref, const peanut_reads* R, const peanut_d
     if (!n) return;
     DBuf<uint32_t> status(1, s);
     status.zero();
-    // distances 0..3 and 4..7: the register band (8 and 16 diagonals); 8 and more: the scratch band
+    // distances 0..7: the register band of exactly 2 d + 1 diagonals; 8 and more: the scratch band
     PN_REQUIRE(n < (1ull << 32), PEANUT_UNSUPPORTED, "more than 2^32 - 1 hits in one call");
-    DBuf<uint32_t> l0(n, s), l1(n, s), l2(n, s);
-    DBuf<unsigned long long> cnt(3, s);
-    cnt.zero();
-    cigar_classify_k<<<grid_for(n, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(H.dist, n, l0.p, l1.p, l2.p, cnt.p);
+    const uint32_t nb = (uint32_t)std::min<uint64_t>((n + 4095) / 4096, (uint64_t)sm_count() * 8);
+    const uint64_t chunk = (n + nb - 1) / nb;
+    DBuf<uint32_t> bcnt((uint64_t)kCigarClasses * nb, s);
+    cigar_count_k<<<nb, kClassifyThreads, 0, s>>>(H.dist, n, chunk, bcnt.p);
     PN_CHECK_LAUNCH();
-    const unsigned gb = grid_for(n, kBandThreads, (unsigned)sm_count() * 16);
-    DBuf<uint32_t> dirs((uint64_t)(R->max_len + 1) * gb * kBandThreads, s);
-    cigar_band_k<8><<<gb, kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
-                                                R->n_reads, ref->n, l0.p, cnt.p, dirs.p, d_ops, cap, d_nops, status.p);
+    std::vector<uint32_t> hoff((size_t)kCigarClasses * nb);
+    PN_CUDA(cudaMemcpyAsync(hoff.data(), bcnt.p, hoff.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    PN_CUDA(cudaStreamSynchronize(s));
+    unsigned long long nc[kCigarClasses], off[kCigarClasses];
+    uint32_t run = 0;
+    for (int c = 0; c < kCigarClasses; ++c) {
+        off[c] = run;
+        for (uint32_t b = 0; b < nb; ++b) {
+            const uint32_t t = hoff[(size_t)c * nb + b];
+            hoff[(size_t)c * nb + b] = run;
+            run += t;
+        }
+        nc[c] = run - off[c];
+        PN_REQUIRE(nc[c] == 0 || (uint32_t)c <= R->max_k, PEANUT_INVALID_ARG,
+                   "a hit's distance exceeds the batch's largest k (%u)", R->max_k);
+    }
+    DBuf<unsigned long long> len_d(kCigarClasses, s);
+    PN_CUDA(cudaMemcpyAsync(bcnt.p, hoff.data(), hoff.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaMemcpyAsync(len_d.p, nc, sizeof(nc), cudaMemcpyHostToDevice, s));
+    DBuf<uint32_t> list(n, s);
+    cigar_fill_k<<<nb, kClassifyThreads, 0, s>>>(H.dist, n, chunk, bcnt.p, list.p);
     PN_CHECK_LAUNCH();
-    if (R->max_k >= 4) {
-        cigar_band_k<16><<<gb, kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
-                                                     R->n_reads, ref->n, l1.p, cnt.p + 1, dirs.p, d_ops, cap, d_nops,
-                                                     status.p);
+    // one grid per band width, as many blocks as its registers let stay resident (and no more
+    // than its hits need); the direction scratch is sized for the largest
+    using BandKernel = decltype(&cigar_band_k<0>);
+    const BandKernel kern[kCigarClasses - 1] = {cigar_band_k<0>, cigar_band_k<1>, cigar_band_k<2>, cigar_band_k<3>,
+                                               cigar_band_k<4>, cigar_band_k<5>, cigar_band_k<6>, cigar_band_k<7>};
+    unsigned grid[kCigarClasses - 1] = {};
+    unsigned gmax = 0;
+    for (int c = 0; c < kCigarClasses - 1; ++c) {
+        if (!nc[c]) continue;
+        int per_sm = 0;
+        PN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[c], kBandThreads, 0));
+        grid[c] = grid_for(nc[c], kBandThreads, (unsigned)sm_count() * (unsigned)std::max(per_sm, 1));
+        gmax = std::max(gmax, grid[c]);
+    }
+    DBuf<uint32_t> dirs((uint64_t)(R->max_len + 1) * std::max(gmax, 1u) * kBandThreads, s);
+    for (int c = 0; c < kCigarClasses - 1; ++c) {
+        if (!nc[c]) continue;
+        kern[c]<<<grid[c], kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
+                                                 R->n_reads, ref->n, list.p + off[c], len_d.p + c, dirs.p, d_ops,
+                                                 cap, d_nops, status.p);
         PN_CHECK_LAUNCH();
     }
-    if (R->max_k >= 8) {
+    if (nc[kCigarClasses - 1]) {
         const uint32_t W = 2 * R->max_k + 1;
         const uint32_t cells = (R->max_len + 1) * W;
         const unsigned g = grid_for(n, kCigarThreads, (unsigned)sm_count() * 4);
-        DBuf<uint16_t> band((uint64_t)cells * g * kCigarThreads, s);
+        DBuf<uint16_t> bandbuf((uint64_t)cells * g * kCigarThreads, s);
         cigar_k<<<g, kCigarThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p, R->n_reads,
-                                            ref->n, band.p, cells, l2.p, cnt.p + 2, d_ops, cap, d_nops, status.p);
+                                            ref->n, bandbuf.p, cells, list.p + off[kCigarClasses - 1],
+                                            len_d.p + kCigarClasses - 1, d_ops, cap, d_nops, status.p);
         PN_CHECK_LAUNCH();
     }
     const uint32_t st = to_host(status.p, s);
-    unsigned long long nc[3];
-    PN_CUDA(cudaMemcpyAsync(nc, cnt.p, sizeof(nc), cudaMemcpyDeviceToHost, s));
-    PN_CUDA(cudaStreamSynchronize(s));
     PN_REQUIRE(!(st & 1u), PEANUT_INVALID_ARG, "a hit names a read, strand or end outside the batch / reference, "
                "or a start after its end");
     PN_REQUIRE(!(st & 2u), PEANUT_INVALID_ARG, "a hit's distance is not the edit distance of its pattern and "
                "reference bases from its start");
     PN_REQUIRE(!(st & 4u), PEANUT_INVALID_ARG, "a hit's alignment has more than %u runs of operations", cap);
-    PN_REQUIRE(!((R->max_k < 4 && nc[1]) || (R->max_k < 8 && nc[2])), PEANUT_INVALID_ARG,
-               "a hit's distance exceeds the batch's largest k (%u)", R->max_k);
 }
 
 }  // namespace pn
