@@ -643,14 +643,19 @@ __global__ void __launch_bounds__(kClassifyThreads)
     }
 }
 
-// The same alignment for hits of distance D (0 to 7, one instance each): the band's previous and
-// current rows live in registers (2 D + 1 cells each, one per diagonal offset o = c - i + D), and
-// only the traceback direction of every cell is kept, two bits per cell, one word per row: 0 the
-// diagonal step on a match, 3 on a mismatch, 1 the reference-only step, 2 the read-only step,
-// chosen by the traceback's own preference from the final values, so the walk back reads the
-// same decisions (and needs no bases).  The direction words live in a scratch
-// area of the call, interleaved across threads (row i of thread t at i * T + t), which leaves the
-// occupancy to the registers.  Hits of other distances are left to the other kernels.
+// The same alignment for hits of distance D (0 to 7, one instance each), on a narrower band: with
+// Delta = n - m, a path of cost d that visits diagonal offset delta = c - i pays at least
+// |delta| + |Delta - delta| for its gaps, so every path of cost d stays within
+// lo = ceil((Delta - d) / 2) <= delta <= floor((Delta + d) / 2), at most d + 1 diagonals; any cell a
+// traceback of an optimal path compares and could step to lies on a path of cost d, so the band's
+// values decide every step as the full matrix does (the others compare as not optimal either way).
+// The band's row lives in registers (D + 1 cells, one per o = delta - lo), and only the traceback
+// direction of every cell is kept, two bits per cell, one 16-bit word per row: 0 the diagonal step
+// on a match, 3 on a mismatch, 1 the reference-only step, 2 the read-only step, chosen by the
+// traceback's own preference from the final values, so the walk back reads the same decisions (and
+// needs no bases).  The direction words live in a scratch area of the call, interleaved across
+// threads (row i of thread t at i * T + t), which leaves the occupancy to the registers.  Hits of
+// other distances are left to the other kernels.
 constexpr int kBandThreads = 64;
 
 template <int D>
@@ -659,13 +664,14 @@ __global__ void __launch_bounds__(kBandThreads)
                  const uint64_t* __restrict__ base_off, const uint8_t* __restrict__ len,
                  const uint32_t* __restrict__ packed, uint32_t n_reads, uint64_t n_ref,
                  const uint32_t* __restrict__ list, const unsigned long long* __restrict__ count,
-                 uint32_t* __restrict__ dirs_all, uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops,
+                 uint16_t* __restrict__ dirs_all, uint32_t* __restrict__ ops, uint32_t cap, uint16_t* __restrict__ nops,
                  uint32_t* status) {
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-    uint32_t* dirs = dirs_all + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint16_t* dirs = dirs_all + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nl = *count;
-    constexpr int WB = 2 * D + 1;
+    constexpr int WB = D + 1;
     constexpr int32_t d = D;
+    static_assert(2 * WB <= 16, "a row's directions fill one 16-bit word");
     for (uint64_t li = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t x = list[li];
         nops[x] = 0;
@@ -680,6 +686,7 @@ __global__ void __launch_bounds__(kBandThreads)
             atomicOr(status, 2u);
             continue;
         }
+        const int32_t lo = -((d - (n - m)) / 2);  // ceil((Delta - d) / 2), Delta - d <= 0
         const uint8_t* rd = codes + base_off[r];
         auto pat = [&](int32_t i) -> uint32_t { return s == 0 ? rd[i] : 3u - rd[m - 1 - i]; };
         // 16 reference bases starting at position p, first base most significant (a window that
@@ -696,20 +703,20 @@ __global__ void __launch_bounds__(kBandThreads)
         // row[o + 1] still hold row i - 1 (the diagonal and the up neighbours) and row[o - 1]
         // already holds row i (the left neighbour)
         uint32_t row[WB];
-        // row 0: E(0, c) = c for c = o - d >= 0
+        // row 0: E(0, c) = c for c = lo + o >= 0
         uint32_t wdir = 0;
 #pragma unroll
         for (int o = 0; o < WB; ++o) {
-            const int32_t c = o - d;
+            const int32_t c = lo + o;
             row[o] = (c >= 0 && c <= n) ? (uint32_t)c : kInf;
             wdir |= 1u << (2 * o);  // reference-only steps along row 0
         }
-        dirs[0] = wdir;
-        // row i needs read base i - 1 and the 2 d + 1 text bases from position st + i - 1 - d on
+        dirs[0] = (uint16_t)wdir;
+        // row i needs read base i - 1 and the d + 1 text bases from position st + i - 1 + lo on
         // (first base most significant).  Rows whose window starts at or after position 0 take
         // it from a sliding pair of packed words (w0, w1) with the next word (w2) loaded 16 rows
         // ahead; the first rows of a band that starts before position 0 load a shifted window.
-        int64_t q = st - d;  // the window start of row i (row 1 first)
+        int64_t q = st + lo;  // the window start of row i (row 1 first)
         uint32_t w0 = 0, w1 = 0, w2 = 0;
         bool slid = false;
         uint32_t p_next = m > 0 ? pat(0) : 0u;
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(kBandThreads)
                 tw = __funnelshift_l(w1, w0, 2u * sh);
             }
             wdir = 0;
-            if (i > d && i + d <= n) {
+            if (i + lo >= 1 && i + lo + WB - 1 <= n) {
                 // every cell of the row lies inside the rectangle (1 <= c <= n), so its value is
                 // its diagonal neighbour a or a + 1: a + 1 exactly when the bases differ and
                 // neither the left nor the up neighbour is below a.  The direction follows the
@@ -760,7 +767,7 @@ __global__ void __launch_bounds__(kBandThreads)
             } else {
 #pragma unroll
                 for (int o = 0; o < WB; ++o) {
-                    const int32_t c = i - d + o;
+                    const int32_t c = i + lo + o;
                     uint32_t v = kInf, dir = 0;
                     if (c >= 0 && c <= n) {
                         if (c == 0) {
@@ -779,23 +786,28 @@ __global__ void __launch_bounds__(kBandThreads)
                     wdir |= dir << (2 * o);
                 }
             }
-            dirs[(uint64_t)i * T] = wdir;
+            dirs[(uint64_t)i * T] = (uint16_t)wdir;
         }
-        // E(m, n) sits at offset n - m + d of the last row
+        // E(m, n) sits at offset n - m - lo of the last row
         uint32_t em = kInf;
 #pragma unroll
         for (int o = 0; o < WB; ++o)
-            if (o == n - m + d) em = row[o];
+            if (o == n - m - lo) em = row[o];
         if (em != (uint32_t)d) {
             atomicOr(status, 2u);
             continue;
         }
         uint32_t* out = ops + x * cap;
         uint32_t runs = 0, last = 4;
-        bool full = false;
+        uint32_t fail = 0;
         int32_t i = m, c = n;
         while (i > 0 || c > 0) {
-            const uint32_t dir = (dirs[(uint64_t)i * T] >> (2 * (c - i + d))) & 3u;
+            const int32_t o = c - i - lo;
+            if (o < 0 || o >= WB) {  // an optimal path never leaves the band
+                fail = 2u;
+                break;
+            }
+            const uint32_t dir = ((uint32_t)dirs[(uint64_t)i * T] >> (2 * o)) & 3u;
             uint32_t code;
             if (dir == 0 || dir == 3) {  // the diagonal step: 0 a match, 3 a mismatch
                 code = dir == 0 ? 0u : 1u;
@@ -811,15 +823,15 @@ __global__ void __launch_bounds__(kBandThreads)
             if (code == last) {
                 out[runs - 1] += 4u;
             } else if (runs == cap) {
-                full = true;
+                fail = 4u;
                 break;
             } else {
                 out[runs++] = 4u | code;
                 last = code;
             }
         }
-        if (full) {
-            atomicOr(status, 4u);
+        if (fail) {
+            atomicOr(status, fail);
             continue;
         }
         for (uint32_t a = 0, b = runs ? runs - 1 : 0; a < b; ++a, --b) {
@@ -881,7 +893,7 @@ void hit_alignments(const peanut_ref* ref, const peanut_reads* R, const peanut_d
         grid[c] = grid_for(nc[c], kBandThreads, (unsigned)sm_count() * (unsigned)std::max(per_sm, 1));
         gmax = std::max(gmax, grid[c]);
     }
-    DBuf<uint32_t> dirs((uint64_t)(R->max_len + 1) * std::max(gmax, 1u) * kBandThreads, s);
+    DBuf<uint16_t> dirs((uint64_t)(R->max_len + 1) * std::max(gmax, 1u) * kBandThreads, s);
     for (int c = 0; c < kCigarClasses - 1; ++c) {
         if (!nc[c]) continue;
         kern[c]<<<grid[c], kBandThreads, 0, s>>>(H, d_start, R->codes.p, R->base_off.p, R->len.p, ref->packed.p,
