@@ -381,9 +381,11 @@ peanut_status peanut_annotate_hits(const peanut_ref* ref, const peanut_reads* re
  *   hits: a device hit list of this batch; d_start: device, hits->n alignment starts
  *   (peanut_annotate_hits).  d_ops: device, hits->n * ops_per_hit words, caller-owned;
  *   d_nops: device, hits->n entries.  Uses the batch's stream (synchronized); allocates transient
- *   device memory: three hit lists by distance class (4 bytes per hit each), one 32-bit word of
- *   traceback directions per read base and thread, and, when the batch's k is 8 or more, a band
- *   of (2 k + 1)(m + 1) 16-bit cells per thread for the larger distances.
+ *   device memory: the hits' indices listed by distance (4 bytes per hit), nine 32-bit counts
+ *   per classifying block, one 16-bit word of traceback directions per read base (plus one) and
+ *   thread of the widest launch, and, when a hit has distance 8 or more, a band of
+ *   (2 k + 1)(m + 1) 16-bit cells per thread for those.  A hit whose distance exceeds the
+ *   batch's largest k is refused (INVALID_ARG).
  * Errors: INVALID_ARG (bad object, NULL pointer, a hit outside the batch or reference, a start
  *         after its end, a distance that is not the pattern's distance to those bases, more runs
  *         than ops_per_hit), NO_MEMORY, CUDA_ERROR. */
