@@ -23,6 +23,21 @@ namespace pn {
 
 constexpr int kPostThreads = 128;
 
+// The quality of rank R for a reference of n positions: the integer part of
+// -10 log10((R - 1) / n) + 1e-9, clamped to 0..255, and 255 for R <= 1.  It is first taken in single
+// precision from l10n = 10 log10(n): log10f's error (2 ulp) and the roundings keep that value
+// within 1e-4 of the exact one, so when it lies more than 1e-3 from an integer its integer part is
+// the exact one; otherwise the double-precision expression decides.  (GB300's FP64 rate is a
+// small fraction of its FP32 rate, so a double log10 per hit would bound the ranking kernels.)
+__device__ __forceinline__ uint8_t hit_quality(uint32_t R, double n_ref, float l10n) {
+    if (R <= 1) return 255;
+    const float vf = l10n - 10.0f * log10f((float)(R - 1));
+    const float fl = floorf(vf), fr = vf - fl;
+    float v = fl;
+    if (!(fr > 1e-3f && fr < 1.0f - 1e-3f)) v = (float)floor(-10.0 * log10((double)(R - 1) / n_ref) + 1e-9);
+    return (uint8_t)(v < 0.0f ? 0.0f : v > 255.0f ? 255.0f : v);
+}
+
 // One column of the anchored matrix on W 64-bit words; returns the change of E[m][c].
 template <int W>
 __device__ __forceinline__ int anchored_step(uint64_t (&Pv)[W], uint64_t (&Mv)[W], const uint64_t (&e)[W],
@@ -95,11 +110,85 @@ __device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64
     return best < 0 ? ~0ull : (uint64_t)(j - best + 1);
 }
 
+// The same start for a hit of distance d <= 7, on the 2d + 1 diagonals |c - i| <= d of the reversed
+// pattern (rows i) against the reference read leftwards from j (columns c): every path of cost <= d
+// to E(m, c), c in [m - d, m + d] (the only columns that can score d), stays in them.  Cell k of
+// column c is row c - d + k, held as a 2-bit field of one word (the lower bit the value, the upper
+// bit a spacer through which the carry below crosses into the next cell).  Cells above row 0 take
+// the virtual value c - i (as row 0 takes c), which satisfies the recurrence whatever the bases.
+// Per column, the cells that exceed their diagonal neighbour (D) are those whose bases differ while
+// neither the left neighbour nor the cell above is below that neighbour; "the cell above is not
+// below" chains down the column, Z(k) = G(k) | (P(k) & Z(k - 1)) for Z = not D, and one addition
+// gives all of it: Z is the carry vector of (G | P) + G.  The column's vertical differences (UP,
+// UN: +1, -1) follow from the previous column's and D; row m's value from the top cell's (tracked)
+// and the differences above row m.
+__device__ uint64_t hit_start_band(const uint8_t* __restrict__ rd, uint32_t s, int32_t m, int64_t sa, int64_t j,
+                                   int32_t d, const uint32_t* __restrict__ packed, bool* ok) {
+    const int32_t W = 2 * d + 1;
+    const uint32_t E = 0x55555555u & ((1u << (2 * W)) - 1u), ODD = E << 1;
+    const uint32_t upper = E & ~((1u << (2 * (d + 1))) - 1u);
+    uint32_t UP = upper, UN = E & ~upper & ~1u;  // column 0: E(i, 0) = |i|
+    int32_t v0 = d;                               // the top cell's value
+    // row i's base of the reversed pattern (any base outside 1..m)
+    auto base = [&](int32_t i) -> uint32_t {
+        if (i < 1 || i > m) return 0u;
+        return s == 0 ? rd[m - i] : 3u - rd[i - 1];
+    };
+    uint32_t pw = 0;  // the band's pattern bases, cell k at bits 2k
+    for (int32_t r = 1; r <= d && r <= m; ++r) pw |= base(r) << (2 * (r + d));
+    const int64_t C = (int64_t)m + d < j + 1 - sa ? (int64_t)m + d : j + 1 - sa;
+    int64_t best = m == d ? 0 : -1;
+    // the text base of column c sits at position p = j - c + 1: the packed word holding p and the
+    // one before it (loaded 16 columns ahead)
+    int64_t p = j;
+    uint64_t wq = (uint64_t)p >> 4;
+    uint32_t wc = __ldg(packed + wq), wn = wq ? __ldg(packed + wq - 1) : 0u;
+    uint32_t b_next = base(1 + d);
+    for (int64_t c = 1; c <= C; ++c) {
+        pw = (pw >> 2) | (b_next << (2 * (W - 1)));
+        b_next = base((int32_t)c + 1 + d);
+        const uint32_t t = (wc >> (30 - 2 * (uint32_t)(p & 15))) & 3u;
+        if ((p & 15) == 0 && wq > 0) {  // position 0 ends the loop: no word before it is read
+            wc = wn;
+            --wq;
+            wn = wq ? __ldg(packed + wq - 1) : 0u;
+        }
+        --p;
+        const uint32_t x = pw ^ (t * 0x55555555u);
+        const uint32_t mis = (x | (x >> 1)) & E;
+        const uint32_t G = (~mis & E) | ((UN >> 2) & E);
+        const uint32_t X = G | UP | ODD;
+        const uint32_t Z = (((X + G) ^ X ^ G) >> 2) & E;
+        const uint32_t D = ~Z & E;
+        const uint32_t D1 = (D << 2) & E;  // D of the cell above, at each cell
+        const uint32_t same = ~(D ^ D1) & E, U0 = ~(UP | UN) & E;
+        const uint32_t up = ((UP & same) | (U0 & D & ~D1)) & E & ~1u;
+        UN = ((UN & same) | (U0 & ~D & D1)) & E & ~1u;
+        UP = up;
+        v0 += (int32_t)(D & 1u);
+        const int32_t k = m - (int32_t)c + d;  // row m's cell
+        if ((uint32_t)k < (uint32_t)W) {
+            const uint32_t low = ((1u << (2 * k + 1)) - 1u) & E;
+            const int32_t val = v0 + __popc(UP & low) - __popc(UN & low);
+            if (val == d) best = c;
+            if (val < d) *ok = false;  // d is not the minimum: not a hit of this pattern
+        }
+    }
+    if (best < 0) *ok = false;
+    return best < 0 ? ~0ull : (uint64_t)(j - best + 1);
+}
+
+// kBand: the hits of distance <= 7 (the band above); otherwise the others (Myers' columns), so that
+// the common case keeps the band's register count.
+template <bool kBand>
 __global__ void __launch_bounds__(kPostThreads)
     start_k(peanut_device_hits H, const uint8_t* __restrict__ len, const uint64_t* __restrict__ peq,
+            const uint8_t* __restrict__ codes, const uint64_t* __restrict__ base_off,
             const uint32_t* __restrict__ packed, uint64_t n_ref, const uint64_t* __restrict__ seg, uint32_t n_seg,
             uint32_t n_reads, uint64_t* __restrict__ start, uint32_t* status) {
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < H.n; x += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t d = H.dist[x];
+        if (kBand != (d <= 7)) continue;
         const uint32_t r = H.read_id[x], s = H.strand[x];
         const uint64_t j = H.end_pos[x];
         if (r >= n_reads || s > 1 || j >= n_ref) {
@@ -126,11 +215,13 @@ __global__ void __launch_bounds__(kPostThreads)
         const uint64_t* pq = peq + ((uint64_t)r * 2 + s) * 4 * kMaxWords;
         bool ok = true;
         uint64_t st = 0;
-        switch ((m + 63) >> 6) {
-            case 1: st = hit_start<1>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
-            case 2: st = hit_start<2>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
-            case 3: st = hit_start<3>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
-            default: st = hit_start<4>(pq, m, sa, (int64_t)j, H.dist[x], packed, &ok); break;
+        if (kBand) {
+            st = hit_start_band(codes + base_off[r], s, (int32_t)m, sa, (int64_t)j, d, packed, &ok);
+        } else switch ((m + 63) >> 6) {
+            case 1: st = hit_start<1>(pq, m, sa, (int64_t)j, d, packed, &ok); break;
+            case 2: st = hit_start<2>(pq, m, sa, (int64_t)j, d, packed, &ok); break;
+            case 3: st = hit_start<3>(pq, m, sa, (int64_t)j, d, packed, &ok); break;
+            default: st = hit_start<4>(pq, m, sa, (int64_t)j, d, packed, &ok); break;
         }
         if (!ok) atomicOr(status, 2u);
         start[x] = st;
@@ -152,7 +243,7 @@ __global__ void read_ranges_k(const uint32_t* __restrict__ rd, uint64_t n, uint6
 // and quality.
 __global__ void __launch_bounds__(kPostThreads)
     rank_k(const uint8_t* __restrict__ dist, const uint64_t* __restrict__ rb, const uint64_t* __restrict__ re,
-           uint32_t n_reads, double n_ref, uint32_t* __restrict__ rank, uint8_t* __restrict__ mapq) {
+           uint32_t n_reads, double n_ref, float l10n, uint32_t* __restrict__ rank, uint8_t* __restrict__ mapq) {
     __shared__ uint32_t hist[kPostThreads / 32][64];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -180,12 +271,7 @@ __global__ void __launch_bounds__(kPostThreads)
         for (uint64_t x = a + lane; x < b; x += 32) {
             const uint32_t R = h[dist[x] & 63];
             rank[x] = R;
-            uint8_t q = 255;
-            if (R > 1) {
-                const double v = floor(-10.0 * log10((double)(R - 1) / n_ref) + 1e-9);
-                q = (uint8_t)(v < 0.0 ? 0.0 : v > 255.0 ? 255.0 : v);
-            }
-            mapq[x] = q;
+            mapq[x] = hit_quality(R, n_ref, l10n);
         }
         __syncwarp();
     }
@@ -198,8 +284,15 @@ void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_de
     if (!n) return;
     DBuf<uint32_t> status(1, s);
     status.zero();
-    start_k<<<grid_for(n, kPostThreads, (unsigned)sm_count() * 16), kPostThreads, 0, s>>>(
-        H, R->len.p, R->peq.p, ref->packed.p, ref->n, ref->seg.p, ref->n_seg, R->n_reads, d_start, status.p);
+    // every hit goes to exactly one instance; the second reads only the distances when none is 8
+    // or more
+    start_k<true><<<grid_for(n, kPostThreads, (unsigned)sm_count() * 16), kPostThreads, 0, s>>>(
+        H, R->len.p, R->peq.p, R->codes.p, R->base_off.p, ref->packed.p, ref->n, ref->seg.p, ref->n_seg, R->n_reads,
+        d_start, status.p);
+    PN_CHECK_LAUNCH();
+    start_k<false><<<grid_for(n, kPostThreads, (unsigned)sm_count() * 16), kPostThreads, 0, s>>>(
+        H, R->len.p, R->peq.p, R->codes.p, R->base_off.p, ref->packed.p, ref->n, ref->seg.p, ref->n_seg, R->n_reads,
+        d_start, status.p);
     PN_CHECK_LAUNCH();
     // read ids index rb / re below: refuse the list before that if any is out of range
     PN_REQUIRE(!(to_host(status.p, s) & 1u), PEANUT_INVALID_ARG,
@@ -210,7 +303,7 @@ void annotate_hits(const peanut_ref* ref, const peanut_reads* R, const peanut_de
     read_ranges_k<<<grid_for(n, 256, (unsigned)sm_count() * 16), 256, 0, s>>>(H.read_id, n, rb.p, re.p, status.p);
     PN_CHECK_LAUNCH();
     rank_k<<<grid_for((uint64_t)R->n_reads * 32, kPostThreads, (unsigned)sm_count() * 16), kPostThreads, 0, s>>>(
-        H.dist, rb.p, re.p, R->n_reads, (double)ref->n, d_rank, d_mapq);
+        H.dist, rb.p, re.p, R->n_reads, (double)ref->n, (float)(10.0 * log10((double)ref->n)), d_rank, d_mapq);
     PN_CHECK_LAUNCH();
     const uint32_t st = to_host(status.p, s);
     PN_REQUIRE(!(st & 1u), PEANUT_INVALID_ARG, "a hit names a read, strand or end outside the batch / reference");
@@ -343,7 +436,7 @@ __global__ void pair_keys_k(const uint32_t* __restrict__ read_id, const uint64_t
 // Over the sorted keys: rank = pairs of the fragment up to the last one of equal score; keep =
 // the pair has the fragment's best score.
 __global__ void pair_rank_k(const uint64_t* __restrict__ key, const uint64_t* __restrict__ val, uint64_t n,
-                            double n_ref, uint32_t* rank, uint8_t* mapq, uint8_t* keep) {
+                            double n_ref, float l10n, uint32_t* rank, uint8_t* mapq, uint8_t* keep) {
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t k = key[t], f = k >> kScoreBits << kScoreBits;
         uint64_t l = 0, h = t;  // first key of the fragment
@@ -367,12 +460,7 @@ __global__ void pair_rank_k(const uint64_t* __restrict__ key, const uint64_t* __
         const uint32_t R = (uint32_t)(l - f0);
         const uint64_t x = val[t];
         rank[x] = R;
-        uint8_t q = 255;
-        if (R > 1) {
-            const double v = floor(-10.0 * log10((double)(R - 1) / n_ref) + 1e-9);
-            q = (uint8_t)(v < 0.0 ? 0.0 : v > 255.0 ? 255.0 : v);
-        }
-        mapq[x] = q;
+        mapq[x] = hit_quality(R, n_ref, l10n);
         keep[x] = key[f0] == k;
     }
 }
@@ -439,7 +527,8 @@ DevicePairs* pair_hits(const peanut_ref* ref, const peanut_reads* R, const peanu
         pair_keys_k<<<gp, 256, 0, s>>>(H.read_id, i1.p, sc.p, np, key.p, val.p);
         PN_CHECK_LAUNCH();
         radix_sort_pairs(key.p, val.p, kt.p, vt.p, np, kScoreBits + 23, s);
-        pair_rank_k<<<gp, 256, 0, s>>>(key.p, val.p, np, (double)ref->n, rk.p, mq.p, keep.p);
+        pair_rank_k<<<gp, 256, 0, s>>>(key.p, val.p, np, (double)ref->n, (float)(10.0 * log10((double)ref->n)), rk.p,
+                                       mq.p, keep.p);
         PN_CHECK_LAUNCH();
     }
     uint64_t nk = np;

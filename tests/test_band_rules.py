@@ -139,3 +139,111 @@ def test_band_is_never_wider_than_the_distance_plus_one():
                 assert abs(off) + abs(delta - off) <= d
             for off in (lo - 1, hi + 1):
                 assert abs(off) + abs(delta - off) > d
+
+
+# ---- the alignment start of a hit (the backward pass of Section "Validation") ----------------
+#
+# The start kernel takes a hit of distance d <= 7 ending at j through the reversed pattern against
+# the reference read leftwards from j, column c = 1 .. min(m + d, j + 1 - segment start), and needs
+# only E(m, c) for c in [m - d, m + d]; every path of cost <= d to those cells stays within
+# |c - i| <= d, so it keeps the 2d + 1 cells of that band, one per diagonal, as 2-bit fields of one
+# word (cell k: row c - d + k; the upper bit of each field a spacer that lets the carry of the
+# addition below cross into the next cell).  Cells above row 0 take the virtual value c - i (as
+# row 0 takes c), which satisfies the recurrence whatever the bases, so the band needs no edge
+# cases.  Per column: D(k) = 1 exactly when the cell exceeds its diagonal neighbour, which by the
+# unit-step rule is (bases differ) and not (the left neighbour is below it) and not (the cell above
+# in this column is below it); the last condition chains down the column and is solved for all
+# cells at once by one addition (Z(k) = G(k) | (P(k) & Z(k - 1)) is the carry vector of
+# (G | P) + G).  The vertical differences of the column then follow from the previous column's and
+# D; the value of row m comes from the tracked top cell and popcounts.
+
+
+def _u(x):
+    return x & 0xFFFFFFFF
+
+
+def _start_model(pat, ref, j, d, sa):
+    """The start kernel's rules restated: the leftmost start of the hit, or None (not a hit)."""
+    m = len(pat)
+    rev = pat[::-1]  # row i <-> rev[i - 1]
+    C = min(m + d, j + 1 - sa)
+    W = 2 * d + 1
+    E = sum(1 << (2 * k) for k in range(W))  # the cells' value bits
+    ODD = E << 1  # the spacers
+    UP = sum(1 << (2 * k) for k in range(d + 1, W))  # column 0: E(i, 0) = |i|
+    UN = sum(1 << (2 * k) for k in range(1, d + 1))
+    v0 = d  # the top cell's value
+    base = lambda i: rev[i - 1] if 1 <= i <= m else 0  # any base outside the pattern
+    pw = 0  # the band's pattern bases, cell k at bits 2k
+    for k in range(W):
+        pw |= base(k - d) << (2 * k)
+    score0 = m
+    best = 0 if score0 == d else -1
+    ok = True
+    for c in range(1, C + 1):
+        pw = (pw >> 2) | (base(c + d) << (2 * (W - 1)))
+        t = ref[j - c + 1]
+        x = pw ^ (t * 0x55555555)
+        mis = (x | (x >> 1)) & E
+        G = (~mis & E) | ((UN >> 2) & E)
+        X = G | UP | ODD
+        Y = G
+        Z = ((_u(X + Y) ^ X ^ Y) >> 2) & E
+        D = ~Z & E
+        D1 = (D << 2) & E  # D(k - 1) at cell k
+        same = ~(D ^ D1) & E
+        U0 = ~(UP | UN) & E
+        UP, UN = ((UP & same) | (U0 & D & ~D1)) & E & ~1, ((UN & same) | (U0 & ~D & D1)) & E & ~1
+        v0 += D & 1
+        k = m - c + d  # row m's cell
+        if 0 <= k < W:
+            low = ((1 << (2 * k + 1)) - 1) & E
+            val = v0 + bin(UP & low).count("1") - bin(UN & low).count("1")
+            if val == d:
+                best = c
+            if val < d:
+                ok = False
+    if best < 0 or not ok:
+        return None
+    return j - best + 1
+
+
+_CODE = {"A": 0, "C": 1, "G": 2, "T": 3}
+
+
+@pytest.mark.parametrize("alphabet", ["ACGT", "AC"])
+def test_start_rules_give_the_oracles_starts(alphabet):
+    import numpy as np
+    rng = random.Random(1706 + len(alphabet))
+    checked = set()
+    for trial in range(60):
+        n = rng.randint(40, 160)
+        ref = "".join(rng.choice(alphabet) for _ in range(n))
+        contigs = [0] if trial % 3 else [0, rng.randint(10, n - 10)]
+        text, seg = oracle.prepare_reference(ref.encode(), contigs, gap_min=16)
+        text = bytes(text).decode()
+        reads = []
+        for _ in range(6):
+            m = rng.randint(1, 30)
+            p = rng.randrange(0, n - m + 1)
+            reads.append(_mutate(rng, text[p:p + m], rng.randint(0, 4), alphabet) or "A")
+        offs = np.concatenate([[0], np.cumsum([len(r) for r in reads])]).astype(np.int64)
+        seq = "".join(reads).encode()
+        k = rng.randint(0, 7)
+        hits = oracle.map_bruteforce(text.encode(), seq, offs, k, "all", segments=seg)
+        if hits.size == 0:
+            continue
+        starts, _, _ = oracle.annotate(text.encode(), seq, offs, hits, segments=seg)
+        codes = [_CODE[b] for b in text]
+        for h, st in zip(hits, starts):
+            read = reads[int(h["read"])]
+            pat = [_CODE[b] for b in read]
+            if h["strand"]:
+                pat = [3 - b for b in pat[::-1]]
+            j, d = int(h["end"]), int(h["dist"])
+            sa = int(seg[np.searchsorted(seg[:, 1], j, side="right"), 0])
+            assert _start_model(pat, codes, j, d, sa) == int(st), (read, int(h["strand"]), j, d, sa)
+            checked.add(d)
+            if d < 7:  # a distance above the true one is refused (some column scores below it)
+                assert _start_model(pat, codes, j, d + 1, sa) is None
+    assert checked >= set(range(6))
