@@ -113,8 +113,8 @@ __device__ uint64_t hit_start(const uint64_t* __restrict__ pq, uint32_t m, int64
 // The same start for a hit of distance d <= 7, on the 2d + 1 diagonals |c - i| <= d of the reversed
 // pattern (rows i) against the reference read leftwards from j (columns c): every path of cost <= d
 // to E(m, c), c in [m - d, m + d] (the only columns that can score d), stays in them.  Cell k of
-// column c is row c - d + k, held as a 2-bit field of one word (the lower bit the value, the upper
-// bit a spacer through which the carry below crosses into the next cell).  Cells above row 0 take
+// column c is row c - d + k, held as a 2-bit field of one word (the lower bit the cell's flag, the
+// upper bit a spacer through which the carry below crosses into the next cell).  Cells above row 0 take
 // the virtual value c - i (as row 0 takes c), which satisfies the recurrence whatever the bases.
 // Per column, the cells that exceed their diagonal neighbour (D) are those whose bases differ while
 // neither the left neighbour nor the cell above is below that neighbour; "the cell above is not
