@@ -4,7 +4,9 @@ The GPU maps whole batches; the oracle checks a sample of reads one by one again
 reference (exact hit sets; a read's hits do not depend on the other reads of its batch).  On the
 3.1 Gbp workload a property that holds at any size is checked as well: every planted read's true
 end lies in a run of ends within k edits whose canonical tuple (found here by a local DP window
-of the oracle) must be in the GPU output.
+of the oracle) must be in the GPU output.  The postprocessing of that batch (starts, ranks,
+qualities, extended CIGARs) is checked hit by hit for a sample of reads, the oracle annotating and
+aligning the GPU's own hit lists of those reads.
 """
 from concurrent.futures import ThreadPoolExecutor
 
@@ -245,3 +247,51 @@ def test_reference_beyond_2_32_bases(gpu):
         assert (int(r), s, lo + a + int(np.argmin(run)), int(run.min())) in got, int(r)
         checked += 1
     assert checked > 80
+
+
+def _postprocessing_sample(gpu, ref, R, reads, n_sample=2000, max_hits=4000):
+    """Maps one batch (q = 16, stride 16, k = 5, all hits), runs the whole postprocessing on the GPU (starts,
+    ranks, qualities, extended CIGARs of every hit), and checks it against the oracle for
+    n_sample evenly spaced reads with at most max_hits hits each (the oracle's rank is quadratic
+    in a read's hits): the oracle annotates and aligns the GPU's own hit lists of those reads.
+    Returns the number of hits checked."""
+    import torch
+    B = gpu.index_reads(R, reads.seq, reads.offsets, 16, k=5, stride=16)
+    try:
+        dh = gpu.map_device(R, B, "all")
+        h = dh.to_numpy()
+        start, rank, mapq = gpu.annotate_hits(R, B, dh)
+        ops, nops = gpu.hit_alignments(R, B, dh, start)
+        per_read = np.bincount(h["read"].astype(np.int64), minlength=reads.n)
+        cand = np.flatnonzero((per_read > 0) & (per_read <= max_hits))
+        idx = cand[np.unique(np.linspace(0, cand.size - 1, n_sample).astype(np.int64))]
+        sel = np.flatnonzero(np.isin(h["read"], idx.astype(np.uint32)))
+        sub = reads.subset(idx)
+        pos = np.full(reads.n, -1, np.int64)
+        pos[idx] = np.arange(idx.size)
+        hs = h[sel].copy()
+        hs["read"] = pos[hs["read"].astype(np.int64)].astype(np.uint32)
+        ws, wr, wq = oracle.annotate(ref, sub.seq, sub.offsets, hs)
+        assert np.array_equal(start.cpu().numpy()[sel], ws)
+        assert np.array_equal(rank.cpu().numpy()[sel].astype(np.uint32), wr)
+        assert np.array_equal(mapq.cpu().numpy()[sel].astype(np.int32), wq)
+        t = torch.as_tensor(sel, dtype=torch.int64, device=ops.device)
+        got = gpu.cigars(ops[t], nops[t])
+        exp = oracle.alignments(ref, sub.seq, sub.offsets, hs, ws)
+        bad = [(int(sel[x]), g, e) for x, (g, e) in enumerate(zip(got, exp)) if g != e]
+        assert not bad, bad[:5]
+        return int(sel.size)
+    finally:
+        B.free()
+
+
+def test_human_scale_postprocessing_sampled_exact(gpu, human_ref):
+    """The postprocessing of the bench's first 2^20-read batch of the 3.1 Gbp workload, as
+    `bench.py --mode post` runs it: every hit of 2,000 evenly spaced reads among those with at
+    most 4,000 hits (starts, ranks, qualities, alignments) exact against the oracle."""
+    ref, R = human_ref
+    w = synth.WORKLOADS["human_3g1_10m"]
+    seed = 1706 + list(synth.WORKLOADS).index("human_3g1_10m")
+    reads = synth.make_reads(ref, 1 << 20, seed, lengths=w["lengths"], rate_range=w["rate_range"],
+                             random_frac=w["random_frac"])
+    assert _postprocessing_sample(gpu, ref, R, reads) > 4_000
